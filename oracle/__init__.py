@@ -1,0 +1,308 @@
+"""SF-GRASS oracle: plain FP64 CPU restatement of the method, for tests only.
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package. The CUDA library never imports,
+links or calls it, and it imports nothing from the CUDA library's package.
+
+The arithmetic lives in ``sfg_oracle.cpp`` (single-threaded, FP64, no fused multiply-add), loaded
+here through ctypes. This module adds the condition-number measurement of Sec. 2.2
+(Eq. eqn:ineq): kappa(L_G, L_P) = lambda_max / lambda_min of the pencil (L_G, L_P) on the
+complement of the common null space, from a dense generalised symmetric eigensolve (LAPACK through
+scipy, a library primitive).
+
+Parity status: pinned by ``tests/test_oracle_pins.py`` (closed-form spectra, invariants, brute
+force). The end-to-end sparsifier edge set has no worked example in the paper: "parity unpinned"
+against the paper, pinned only through kappa and the unit pins of its steps.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sfg_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle_sfg.so")
+
+# Score modes (same numbering as the CUDA library's public header, restated independently).
+RATIO, G_ONLY, P_ONLY = 0, 1, 2
+ETA = 1e-30
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with the host C++ compiler."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC",
+                               "-ffp-contract=off", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f32p = ctypes.POINTER(ctypes.c_float)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_i32, _i64, _u64, _f64, _int = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
+
+
+def _declare(L):
+    sig = {
+        "orc_canonicalize": (_int, [_i32, _i64, _i32p, _i32p, _f32p, _i32p, _i32p, _f32p, _i64p]),
+        "orc_laplacian": (None, [_i32, _i64, _i32p, _i32p, _f32p, _i64p, _i32p, _f64p, _i32p, _f64p]),
+        "orc_laplacian_apply": (None, [_i32, _i64, _i32p, _i32p, _f32p, _int, _f64p, _f64p]),
+        "orc_gaussian": (_f64, [_u64, _u64]),
+        "orc_splitmix64": (_u64, [_u64]),
+        "orc_init_vectors": (None, [_i32, _int, _u64, _f64p]),
+        "orc_jacobi": (None, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _f64, _f64p]),
+        "orc_project": (None, [_i32, _int, _f64p]),
+        "orc_smooth": (None, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _f64, _u64, _f64p]),
+        "orc_score_edges": (None, [_i32, _i64, _i32p, _i32p, _f32p, _f64p, _f64p, _int, _i32p,
+                                   _i64, _int, _f64, _f64p]),
+        "orc_topk": (None, [_f64p, _i32p, _i64, _i64, _i32p]),
+        "orc_mst": (None, [_i32, _i64, _i32p, _i32p, _f32p, _u8p, _u8p]),
+        "orc_components": (_i32, [_i32, _i64, _i32p, _i32p]),
+        "orc_affinity": (None, [_i32, _i64, _i32p, _i32p, _f32p, _f64p, _int, _f64p]),
+        "orc_aggregate": (_i32, [_i32, _i64, _i32p, _i32p, _f32p, _f64p, _i32p]),
+        "orc_galerkin": (None, [_i32, _i64, _i32p, _i32p, _f32p, _i32p, _i32, _i32p, _i32p, _f32p,
+                                _i64p, _i32p]),
+        "orc_backward_map": (None, [_i32, _i64, _i32p, _i32p, _f32p, _i32p, _i32p, _i32, _i64,
+                                    _i32p, _i32p, _f32p, _u8p, _u8p]),
+        "orc_sparsify": (_int, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _int, _f64, _u64, _int,
+                                _f64, _int, _f64, _u8p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Graph:
+    """Canonical weighted undirected edge list (u < v, sorted, merged): edge id = position."""
+
+    def __init__(self, n, u, v, w):
+        self.n = int(n)
+        self.u = _c(u, np.int32)
+        self.v = _c(v, np.int32)
+        self.w = _c(w, np.float32)
+
+    @property
+    def m(self):
+        return int(self.u.shape[0])
+
+    def args(self):
+        return (self.n, self.m, _p(self.u, _i32p), _p(self.v, _i32p), _p(self.w, _f32p))
+
+    def subgraph(self, mask):
+        mask = np.asarray(mask).astype(bool)
+        return Graph(self.n, self.u[mask], self.v[mask], self.w[mask])
+
+
+def canonicalize(n, u, v, w) -> Graph:
+    """Sec. 2.1 input convention: u < v, sorted, parallel edges summed in FP64, self-loops dropped."""
+    u, v, w = _c(u, np.int32), _c(v, np.int32), _c(w, np.float32)
+    m = u.shape[0]
+    cu, cv, cw = np.empty(m, np.int32), np.empty(m, np.int32), np.empty(m, np.float32)
+    mo = ctypes.c_int64(0)
+    rc = lib().orc_canonicalize(int(n), m, _p(u, _i32p), _p(v, _i32p), _p(w, _f32p),
+                                _p(cu, _i32p), _p(cv, _i32p), _p(cw, _f32p), ctypes.byref(mo))
+    if rc != 0:
+        raise ValueError("invalid edge list (id out of range or weight not finite and positive)")
+    k = mo.value
+    return Graph(n, cu[:k].copy(), cv[:k].copy(), cw[:k].copy())
+
+
+def laplacian_csr(g: Graph):
+    """CSR of L (Eq. formula_adjacency): row_ptr, col, A values (FP64), edge ids, degrees."""
+    rp = np.empty(g.n + 1, np.int64)
+    col = np.empty(2 * g.m, np.int32)
+    val = np.empty(2 * g.m, np.float64)
+    eid = np.empty(2 * g.m, np.int32)
+    deg = np.empty(g.n, np.float64)
+    lib().orc_laplacian(*g.args(), _p(rp, _i64p), _p(col, _i32p), _p(val, _f64p), _p(eid, _i32p),
+                        _p(deg, _f64p))
+    return rp, col, val, eid, deg
+
+
+def laplacian_apply(g: Graph, x):
+    x = _c(x, np.float64)
+    K = 1 if x.ndim == 1 else x.shape[1]
+    y = np.empty_like(x)
+    lib().orc_laplacian_apply(*g.args(), K, _p(x, _f64p), _p(y, _f64p))
+    return y
+
+
+def gaussian(seed: int, j: int) -> float:
+    return lib().orc_gaussian(seed & (2**64 - 1), j)
+
+
+def splitmix64(x: int) -> int:
+    return lib().orc_splitmix64(x & (2**64 - 1))
+
+
+def init_vectors(n, K, seed):
+    x = np.empty((n, K), np.float64)
+    lib().orc_init_vectors(n, K, seed, _p(x, _f64p))
+    return x
+
+
+def jacobi(g: Graph, x, steps, omega=0.7):
+    x = _c(x, np.float64).copy()
+    K = 1 if x.ndim == 1 else x.shape[1]
+    lib().orc_jacobi(*g.args(), K, steps, omega, _p(x, _f64p))
+    return x
+
+
+def project(x):
+    x = _c(x, np.float64).copy()
+    lib().orc_project(x.shape[0], x.shape[1], _p(x, _f64p))
+    return x
+
+
+def smooth(g: Graph, K, steps, omega=0.7, seed=0):
+    x = np.empty((g.n, K), np.float64)
+    lib().orc_smooth(*g.args(), K, steps, omega, seed, _p(x, _f64p))
+    return x
+
+
+def score_edges(g: Graph, xg, xp, ids, mode=RATIO, eta=ETA):
+    xg, xp = _c(xg, np.float64), _c(xp, np.float64)
+    ids = _c(ids, np.int32)
+    out = np.empty(ids.shape[0], np.float64)
+    lib().orc_score_edges(*g.args(), _p(xg, _f64p), _p(xp, _f64p), xg.shape[1], _p(ids, _i32p),
+                          ids.shape[0], mode, eta, _p(out, _f64p))
+    return out
+
+
+def topk(scores, ids, k):
+    scores, ids = _c(scores, np.float64), _c(ids, np.int32)
+    out = np.empty(k, np.int32)
+    lib().orc_topk(_p(scores, _f64p), _p(ids, _i32p), ids.shape[0], k, _p(out, _i32p))
+    return out
+
+
+def mst(g: Graph, allow=None):
+    """Maximum-weight spanning forest (Kruskal, order: weight desc, id asc) as a uint8 mask."""
+    mask = np.empty(g.m, np.uint8)
+    al = None if allow is None else _c(allow, np.uint8)
+    lib().orc_mst(*g.args(), None if al is None else _p(al, _u8p), _p(mask, _u8p))
+    return mask
+
+
+def components(g: Graph) -> int:
+    return lib().orc_components(g.n, g.m, _p(g.u, _i32p), _p(g.v, _i32p))
+
+
+def affinity(g: Graph, x):
+    x = _c(x, np.float64)
+    d = np.empty(g.m, np.float64)
+    lib().orc_affinity(*g.args(), _p(x, _f64p), x.shape[1], _p(d, _f64p))
+    return d
+
+
+def aggregate(g: Graph, delta):
+    delta = _c(delta, np.float64)
+    agg = np.empty(g.n, np.int32)
+    nc = lib().orc_aggregate(*g.args(), _p(delta, _f64p), _p(agg, _i32p))
+    return agg, int(nc)
+
+
+def galerkin(g: Graph, agg, nc):
+    agg = _c(agg, np.int32)
+    cu, cv, cw = np.empty(g.m, np.int32), np.empty(g.m, np.int32), np.empty(g.m, np.float32)
+    f2c = np.empty(g.m, np.int32)
+    mo = ctypes.c_int64(0)
+    lib().orc_galerkin(*g.args(), _p(agg, _i32p), nc, _p(cu, _i32p), _p(cv, _i32p), _p(cw, _f32p),
+                       ctypes.byref(mo), _p(f2c, _i32p))
+    k = mo.value
+    return Graph(nc, cu[:k].copy(), cv[:k].copy(), cw[:k].copy()), f2c
+
+
+def backward_map(g: Graph, agg, f2c, c: Graph, pmask_c):
+    agg, f2c, pm = _c(agg, np.int32), _c(f2c, np.int32), _c(pmask_c, np.uint8)
+    out = np.empty(g.m, np.uint8)
+    lib().orc_backward_map(*g.args(), _p(agg, _i32p), _p(f2c, _i32p), c.n, c.m, _p(c.u, _i32p),
+                           _p(c.v, _i32p), _p(c.w, _f32p), _p(pm, _u8p), _p(out, _u8p))
+    return out
+
+
+def sparsify(g: Graph, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=RATIO, budget_frac=0.1,
+             budget_unit=1, eta=ETA):
+    """Algorithm 1: returns (mask over G's canonical edges, number of levels built)."""
+    mask = np.empty(g.m, np.uint8)
+    lf = lib().orc_sparsify(*g.args(), K, steps, levels, omega, seed, mode, budget_frac,
+                            budget_unit, eta, _p(mask, _u8p))
+    return mask, int(lf)
+
+
+# ------------------------------------------------------------------------------------------------
+# Sec. 2.2 relative condition number (measurement, FP64 dense; tiny and small graphs only)
+# ------------------------------------------------------------------------------------------------
+def dense_laplacian(g: Graph, mask=None):
+    L = np.zeros((g.n, g.n))
+    sel = np.ones(g.m, bool) if mask is None else np.asarray(mask).astype(bool)
+    for p, q, w in zip(g.u[sel], g.v[sel], g.w[sel].astype(np.float64)):
+        L[p, q] -= w
+        L[q, p] -= w
+        L[p, p] += w
+        L[q, q] += w
+    return L
+
+
+def kappa_dense(g: Graph, mask) -> float:
+    """kappa(L_G, L_P) of Eq. eqn:ineq for P = edges of G with mask != 0, same weights.
+
+    Both pencils share the null space spanned by the component indicators of G (when P spans G),
+    so one node per component of G is grounded (its row and column removed). If P does not span
+    G's components the reduced L_P is singular and kappa is infinite.
+    """
+    import scipy.linalg as sl
+
+    LG = dense_laplacian(g)
+    LP = dense_laplacian(g, mask)
+    # ground the smallest node of each connected component of G
+    parent = list(range(g.n))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for p, q in zip(g.u, g.v):
+        a, b = find(int(p)), find(int(q))
+        if a != b:
+            parent[max(a, b)] = min(a, b)
+    keep = np.array([find(i) != i for i in range(g.n)])
+    if keep.sum() == 0:
+        return 1.0
+    A = LG[np.ix_(keep, keep)]
+    B = LP[np.ix_(keep, keep)]
+    try:
+        np.linalg.cholesky(B)
+    except np.linalg.LinAlgError:
+        return float("inf")
+    ev = sl.eigh(A, B, eigvals_only=True)
+    return float(ev[-1] / ev[0])
