@@ -1,0 +1,215 @@
+/*
+ * sfg.h - C ABI of the GB300 (sm_103a) SF-GRASS hot path.
+ *
+ * The library computes the data-parallel core of SF-GRASS (Zhang, Zhao, Feng, "SF-GRASS:
+ * Solver-Free Graph Spectral Sparsification", ICCAD 2020): the Laplacian of a weighted undirected
+ * graph, the local spectral embedding by weighted-Jacobi smoothing of K random vectors, the
+ * spectral-perturbation score of candidate edges, top-k edge selection, spanning-tree backbones,
+ * one level of spectral coarsening, the sparsifier backward mapping, and the whole flat or
+ * multilevel method (Algorithm 1).
+ *
+ * Conventions shared by every call:
+ *  - Pointers are DEVICE pointers (memory of the context's device) unless the name ends in
+ *    _host. The caller owns every buffer it passes; opaque objects (sfg_ctx, sfg_graph) are owned
+ *    by the library and released by their *_destroy call.
+ *  - Every call is ordered on the context's CUDA stream. Calls return as soon as their work is
+ *    queued, except where an argument ends in _host or the call's comment says it synchronises.
+ *  - Errors are returned as sfg_status, never thrown or aborted; sfg_last_error() holds the text
+ *    of the most recent failure on that context. Invalid arguments give SFG_EINVAL and queue no
+ *    work; a failing CUDA call gives SFG_ECUDA.
+ *  - Results are deterministic for a fixed input, parameters and seed.
+ *  - Graph sizes: 1 <= n < 2^31 nodes; at most 2^30 - 1 distinct edges (2m stored entries must
+ *    fit an int32).
+ */
+#ifndef SFG_H
+#define SFG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SFG_API __attribute__((visibility("default")))
+#else
+#define SFG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SFG_OK = 0,
+    SFG_EINVAL = 1,       /* bad argument: range, NULL, size, non-finite or non-positive weight */
+    SFG_ENOMEM = 2,       /* device allocation failed */
+    SFG_ECUDA = 3,        /* a CUDA runtime call failed */
+    SFG_ETIMEOUT = 4,     /* an iteration limit ran out before convergence */
+    SFG_ECAPACITY = 5,    /* an output buffer is too small */
+    SFG_EUNSUPPORTED = 6  /* valid but not implemented (e.g. an unsupported K / dtype pair) */
+} sfg_status;
+
+/* Storage type of the N x K vector block. Arithmetic is always FP32 with FP32 accumulation. */
+typedef enum { SFG_F32 = 0, SFG_BF16 = 1 } sfg_dtype;
+
+/* Edge score (Sec. 3.5, Eqs. formula_eig_perturb1_conclusion and ..._conclusion2, with the
+ * eigenvector block U replaced by the smoothed block X; Algorithm 1 lines 13-14).
+ * s_G = w(p,q) * ||X_G^T e_pq||^2 and s_P = w(p,q) * ||X_P^T e_pq||^2, where X_G is the block
+ * smoothed on L_G and X_P the block smoothed on L_P from the same seed.
+ * RATIO: s_P / (s_G + eta); G: s_G (Algorithm 1 embeds G); P: s_P (Sec. 3.5 perturbs L_P). */
+typedef enum { SFG_SCORE_RATIO = 0, SFG_SCORE_G = 1, SFG_SCORE_P = 2 } sfg_score_mode;
+
+typedef struct sfg_ctx sfg_ctx;     /* device, borrowed stream, last error, optional timers */
+typedef struct sfg_graph sfg_graph; /* canonical edge list + CSR Laplacian, device-resident */
+
+/* ---------------------------------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------------------------------- */
+
+/* Create a context on `device` that queues all work on `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream). The stream is borrowed: it must outlive the context and every
+ * graph created through it. */
+SFG_API sfg_status sfg_ctx_create(sfg_ctx** out, int device, void* cuda_stream);
+SFG_API void sfg_ctx_destroy(sfg_ctx* ctx);
+SFG_API sfg_status sfg_ctx_set_stream(sfg_ctx* ctx, void* cuda_stream);
+/* Text of the last error on this context ("" if none). Valid until the next call on ctx. */
+SFG_API const char* sfg_last_error(const sfg_ctx* ctx);
+
+/* Optional per-kernel timing: when on, each launch of the library's kernels is bracketed by
+ * CUDA events on the context stream. sfg_ctx_kernel_time synchronises the stream and returns,
+ * for kernels whose name starts with `prefix`, the number of timed launches and their summed
+ * duration in milliseconds. sfg_ctx_timing(ctx, 1) also clears earlier records. */
+SFG_API sfg_status sfg_ctx_timing(sfg_ctx* ctx, int on);
+SFG_API sfg_status sfg_ctx_kernel_time(sfg_ctx* ctx, const char* prefix, int64_t* launches_host,
+                               double* ms_host);
+
+/* ---------------------------------------------------------------------------------------------
+ * Graph and Laplacian (Sec. 2.1, Eq. formula_adjacency and the definition of D under it;
+ * Sec. 4 input convention: positive weights)
+ * ------------------------------------------------------------------------------------------- */
+
+/* Build the canonical form and the CSR Laplacian of the weighted undirected graph given by the
+ * m input edges (u[i], v[i], w[i]), 0 <= u, v < n, w finite and > 0 (else SFG_EINVAL).
+ * Canonical form: each edge stored once with u < v, sorted by (u, v); parallel edges merged by
+ * adding their weights (in FP64, in input order, rounded once to FP32); self-loops dropped.
+ * Edge id = position in the canonical list. The CSR holds both directions of every edge, each
+ * row sorted by column, and the FP64 degrees D(p,p) = sum of the row. Synchronises (reads back
+ * the validation flag and the canonical edge count). */
+SFG_API sfg_status sfg_laplacian(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u, const int32_t* v,
+                         const float* w, sfg_graph** out);
+SFG_API void sfg_graph_destroy(sfg_graph* g);
+SFG_API sfg_status sfg_graph_info(const sfg_graph* g, int32_t* n_host, int64_t* m_host);
+/* Copy the canonical edge list (m entries each). */
+SFG_API sfg_status sfg_graph_edges(sfg_ctx* ctx, const sfg_graph* g, int32_t* u, int32_t* v, float* w);
+/* Copy the CSR: row_ptr[n+1], col[2m], val[2m] (= w), eid[2m] (canonical edge id of each entry),
+ * deg[n] (FP64). Any pointer may be NULL to skip that array. */
+SFG_API sfg_status sfg_graph_csr(sfg_ctx* ctx, const sfg_graph* g, int32_t* row_ptr, int32_t* col,
+                         float* val, int32_t* eid, double* deg);
+/* The subgraph P of G made of the edges e with mask[e] != 0 (mask has m entries), same nodes,
+ * same weights; its canonical list is G's list filtered in order. Synchronises. */
+SFG_API sfg_status sfg_graph_subgraph(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* mask,
+                              sfg_graph** out);
+
+/* ---------------------------------------------------------------------------------------------
+ * Local spectral embedding (Sec. 3.2: K random vectors orthogonal to the all-one vector, a few
+ * relaxation sweeps on L x = 0)
+ * ------------------------------------------------------------------------------------------- */
+
+/* X_out (n x K, row-major, `storage`) <- the smoothed, projected block:
+ *  1. X0[i,k] = Gaussian draw j = i*K + k of the counter-based generator below, rounded to
+ *     `storage`; each column's mean (FP64) removed.
+ *     Generator: h = splitmix64 (Steele, Lea & Flood 2014); a = h(seed ^ h(2j)),
+ *     b = h(seed ^ h(2j+1)); u1 = ((a >> 11) + 1) 2^-53, u2 = (b >> 11) 2^-53;
+ *     X0 = sqrt(-2 ln u1) cos(2 pi u2); the uniforms are formed exactly in FP64 and the
+ *     transform is evaluated in FP32 (logf, cospif), within a few FP32 ulp of the FP64 value.
+ *  2. `steps` weighted-Jacobi sweeps X <- X - omega D^-1 L X = (1 - omega) X + omega D^-1 A X
+ *     (D^-1 formed in FP64 once per call; rows with D(p,p) = 0 are left unchanged).
+ *  3. Projection: each column's mean removed again and the column scaled to unit RMS.
+ * K must be one of 4, 8, 16, 32, 64 (SFG_F32) or 8, 16, 32, 64 (SFG_BF16), else
+ * SFG_EUNSUPPORTED. 0 < omega <= 1, steps >= 0. */
+SFG_API sfg_status sfg_smooth(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
+                      uint64_t seed, sfg_dtype storage, void* X_out);
+/* Only step 2 of sfg_smooth, in place on a caller-provided block (no init, no projection). */
+SFG_API sfg_status sfg_jacobi(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
+                      sfg_dtype storage, void* X_inout);
+
+/* ---------------------------------------------------------------------------------------------
+ * Spectrally critical edges (Sec. 3.5; Algorithm 1 lines 13-14)
+ * ------------------------------------------------------------------------------------------- */
+
+/* scores_out[i] = score of canonical edge edge_ids[i] of LG (0 <= id < m), from the two n x K
+ * blocks XG (smoothed on L_G) and XP (smoothed on L_P), both in `storage`, per `mode` with
+ * eta = 1e-30. FP32 arithmetic. */
+SFG_API sfg_status sfg_score_edges(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
+                           int K, sfg_dtype storage, const int32_t* edge_ids, int64_t ne,
+                           sfg_score_mode mode, float* scores_out);
+
+/* ids_out[0..k) = the ids of the k largest entries under the strict order (score descending,
+ * id ascending), written in ascending id order. ids must be distinct; 0 <= k <= ne else
+ * SFG_EINVAL. */
+SFG_API sfg_status sfg_select_topk(sfg_ctx* ctx, const float* scores, const int32_t* ids, int64_t ne,
+                           int64_t k, int32_t* ids_out);
+
+/* ---------------------------------------------------------------------------------------------
+ * Spanning-tree backbone (Sec. 3.1 / 3.4: low-stretch tree approximated by a maximum spanning
+ * tree). Maximum-weight spanning forest under the strict order (weight descending, edge id
+ * ascending), so the result is unique and equals Kruskal's. Only edges with allow[e] != 0 take
+ * part (allow may be NULL). mask_out[e] = 1 for forest edges, else 0. Synchronises.
+ * ------------------------------------------------------------------------------------------- */
+SFG_API sfg_status sfg_spanning_tree(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow,
+                             uint8_t* mask_out, int64_t* n_tree_host);
+
+/* ---------------------------------------------------------------------------------------------
+ * Spectral coarsening, one level (Sec. 3.2)
+ * ------------------------------------------------------------------------------------------- */
+
+/* delta_out[e] = 1 - (X_p . X_q)^2 / (||X_p||^2 ||X_q||^2) for every canonical edge e = (p, q)
+ * (the algebraic-distance affinity quoted in Sec. 3.2), evaluated in FP64 without fused
+ * multiply-add, in increasing k order, from the FP32 block X (n x K). A zero row gives 1. */
+SFG_API sfg_status sfg_affinity(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
+                        double* delta_out);
+
+/* One coarsening level from an FP32 block X (n x K): affinities as sfg_affinity; each node hooks
+ * to the neighbour with the smallest delta (ties: smaller id); aggregation sets S_i are the
+ * connected components of the hooks, numbered by increasing smallest member (agg_out[p] = i for
+ * p in S_i); the coarse Laplacian is the Galerkin product H^-T L H^+ of Sec. 3.2, i.e. the
+ * canonical form of the list (agg[u], agg[v], w) taken in fine edge-id order.
+ * fine2coarse_out[e] (may be NULL) = coarse edge id of fine edge e, or -1 inside an aggregate.
+ * Synchronises. */
+SFG_API sfg_status sfg_coarsen(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K, int32_t* agg_out,
+                       int32_t* fine2coarse_out, int32_t* n_coarse_host, sfg_graph** coarse_out);
+
+/* Backward mapping of Sec. 3.4 / Algorithm 1 lines 5-11: pmask_f[e] over the fine graph's edges =
+ * union of a maximum spanning tree of each aggregation set's induced subgraph, and, for every
+ * coarse edge (I, J) with pmask_c set, the heaviest fine edge between S_I and S_J (ties: smallest
+ * id). agg and fine2coarse as produced by sfg_coarsen. Synchronises. */
+SFG_API sfg_status sfg_backward_map(sfg_ctx* ctx, const sfg_graph* fine, const int32_t* agg,
+                            const int32_t* fine2coarse, const sfg_graph* coarse,
+                            const uint8_t* pmask_c, uint8_t* pmask_f);
+
+/* ---------------------------------------------------------------------------------------------
+ * The method (Algorithm 1)
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+    int K;              /* vectors per block */
+    int steps;          /* Jacobi sweeps per embedding */
+    int levels;         /* 0: flat (spanning tree + recovered edges); >= 1: coarsening levels */
+    double omega;       /* Jacobi weight, e.g. 0.7 */
+    uint64_t seed;      /* level l embeds with seed (l = 0) or splitmix64(seed ^ l) */
+    sfg_score_mode mode;
+    double budget_frac; /* beta: each level ends with round(beta * base) edges beyond a forest */
+    int budget_unit;    /* 0: base = N_l; 1: base = number of off-tree edges of G_l */
+    sfg_dtype storage;  /* vector block storage */
+} sfg_params;
+
+/* mask_out[e] (m entries) = 1 for the edges of the sparsifier P of G. Flat: maximum spanning
+ * forest, then the top-scored off-tree edges. Multilevel: coarsen `levels` times (stopping early
+ * if a level has no edges left), sparsify the coarsest graph flat, then at each finer level map
+ * the sparsifier back (sfg_backward_map), re-embed, score the edges outside it and add the top
+ * ones. Budget at each level: the level's sparsifier gets round-half-up(beta * base) edges beyond
+ * N_l - c_l (c_l = number of components), counting edges already mapped; none are added if it is
+ * already over. n_selected_host (may be NULL) receives the number of edges in P. Synchronises. */
+SFG_API sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* params,
+                        uint8_t* mask_out, int64_t* n_selected_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFG_H */

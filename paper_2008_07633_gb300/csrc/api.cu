@@ -1,0 +1,169 @@
+// Context, status, allocation and timing plumbing of libsfg.
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+
+#include "sfg_internal.cuh"
+
+sfg_status sfg_fail(sfg_ctx* ctx, sfg_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return st;
+}
+
+sfg_status sfg_cuda_fail(sfg_ctx* ctx, cudaError_t e, const char* where) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return sfg_fail(ctx, SFG_ENOMEM, "out of device memory in %s", where);
+    }
+    return sfg_fail(ctx, SFG_ECUDA, "CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e),
+                    where);
+}
+
+sfg_status sfg_alloc(sfg_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    ctx->alloc_count++;
+    if (ctx->fail_alloc_at >= 0 && ctx->alloc_count == ctx->fail_alloc_at)
+        return sfg_fail(ctx, SFG_ENOMEM, "injected allocation failure (allocation %lld)",
+                        (long long)ctx->alloc_count);
+    cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return sfg_fail(ctx, SFG_ENOMEM, "cudaMallocAsync(%zu bytes) failed: %s", bytes,
+                        cudaGetErrorString(e));
+    }
+    return SFG_OK;
+}
+
+void sfg_free(sfg_ctx* ctx, void* p) {
+    if (p) cudaFreeAsync(p, ctx->stream);
+}
+
+sfg_status sfg_check_dev(sfg_ctx* ctx, const void* p, const char* what) {
+    if (!p) return sfg_fail(ctx, SFG_EINVAL, "%s is NULL", what);
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return sfg_fail(ctx, SFG_EINVAL, "%s is not a CUDA pointer", what);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return sfg_fail(ctx, SFG_EINVAL, "%s is not device memory", what);
+    return SFG_OK;
+}
+
+int sfg_grid(sfg_ctx* ctx, const void* kernel, int block, size_t smem, int64_t work_items) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    int64_t full = (int64_t)per_sm * ctx->num_sms;
+    int64_t need = (work_items + block - 1) / block;
+    if (need < 1) need = 1;
+    return (int)(need < full ? need : full);
+}
+
+void sfg_tic(sfg_ctx* ctx, const char* name) {
+    if (!ctx->timing) return;
+    sfg_timer_rec r;
+    r.name = name;
+    for (int i = 0; i < 2; ++i) {
+        cudaEvent_t ev;
+        if (!ctx->event_pool.empty()) {
+            ev = ctx->event_pool.back();
+            ctx->event_pool.pop_back();
+        } else if (cudaEventCreate(&ev) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        (i == 0 ? r.start : r.stop) = ev;
+    }
+    cudaEventRecord(r.start, ctx->stream);
+    ctx->timers.push_back(r);
+}
+
+void sfg_toc(sfg_ctx* ctx) {
+    if (!ctx->timing || ctx->timers.empty()) return;
+    cudaEventRecord(ctx->timers.back().stop, ctx->stream);
+}
+
+extern "C" {
+
+sfg_status sfg_ctx_create(sfg_ctx** out, int device, void* cuda_stream) {
+    if (!out) return SFG_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return SFG_EINVAL;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return SFG_ECUDA;
+    sfg_ctx* c = new sfg_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (c->num_sms < 1) c->num_sms = 1;
+    if (const char* f = std::getenv("SFG_FAULT_ALLOC")) c->fail_alloc_at = std::atoll(f);
+    *out = c;
+    return SFG_OK;
+}
+
+void sfg_ctx_destroy(sfg_ctx* ctx) {
+    if (!ctx) return;
+    for (auto& r : ctx->timers) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+sfg_status sfg_ctx_set_stream(sfg_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return SFG_EINVAL;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return SFG_OK;
+}
+
+const char* sfg_last_error(const sfg_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+sfg_status sfg_ctx_timing(sfg_ctx* ctx, int on) {
+    if (!ctx) return SFG_EINVAL;
+    SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& r : ctx->timers) {
+        ctx->event_pool.push_back(r.start);
+        ctx->event_pool.push_back(r.stop);
+    }
+    ctx->timers.clear();
+    ctx->timing = on != 0;
+    return SFG_OK;
+}
+
+sfg_status sfg_ctx_kernel_time(sfg_ctx* ctx, const char* prefix, int64_t* launches_host,
+                               double* ms_host) {
+    if (!ctx || !prefix || !launches_host || !ms_host) return SFG_EINVAL;
+    SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    int64_t n = 0;
+    double total = 0.0;
+    size_t len = std::strlen(prefix);
+    for (auto& r : ctx->timers) {
+        if (std::strncmp(r.name, prefix, len) != 0) continue;
+        float ms = 0.f;
+        SFG_CUDA(ctx, cudaEventElapsedTime(&ms, r.start, r.stop));
+        total += ms;
+        ++n;
+    }
+    *launches_host = n;
+    *ms_host = total;
+    return SFG_OK;
+}
+
+}  // extern "C"

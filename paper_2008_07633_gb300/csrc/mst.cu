@@ -1,0 +1,200 @@
+// Maximum-weight spanning forest (the spanning-tree backbone of Sec. 3.1 / 3.4, where the paper
+// approximates a low-stretch tree by a maximum spanning tree).
+//
+// Boruvka rounds under the strict order (weight descending, edge id ascending): every edge key is
+// (FP32 weight bits << 32) | ~id, unique and ordered like that order, so the forest is unique and
+// equal to Kruskal's. A round: (1) each component takes the largest key among edges leaving it
+// (64-bit atomicMax), (2) marks that edge and hooks to the component across it, (3) the 2-cycles
+// that mutual choices create are broken toward the smaller label, (4) pointer jumping flattens the
+// hook forest, (5) nodes are relabelled. Rounds repeat until no component has an outgoing edge.
+#include "sfg_internal.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__global__ void k_mst_init(int32_t n, int32_t* __restrict__ comp) {
+    for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * kBlock)
+        comp[p] = (int32_t)p;
+}
+
+__global__ void k_mst_reset(int32_t n, unsigned long long* __restrict__ best, int* __restrict__ flag) {
+    for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * kBlock)
+        best[p] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 0;
+}
+
+__global__ void k_mst_edges(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                            const float* __restrict__ ew, const uint8_t* __restrict__ allow,
+                            const int32_t* __restrict__ comp, unsigned long long* __restrict__ best) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock) {
+        if (allow && !allow[e]) continue;
+        const int32_t a = comp[eu[e]], b = comp[ev[e]];
+        if (a == b) continue;
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(ew[e]) << 32) | (unsigned long long)(~(uint32_t)e);
+        atomicMax(&best[a], key);
+        atomicMax(&best[b], key);
+    }
+}
+
+__global__ void k_mst_hook(int32_t n, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                           const int32_t* __restrict__ comp, const unsigned long long* __restrict__ best,
+                           int32_t* __restrict__ parent, uint8_t* __restrict__ mask,
+                           int* __restrict__ flag) {
+    for (int64_t r = (int64_t)blockIdx.x * kBlock + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * kBlock) {
+        if (comp[r] != r) continue;  // only component labels act
+        const unsigned long long b = best[r];
+        if (b == 0ull) {
+            parent[r] = (int32_t)r;
+            continue;
+        }
+        const uint32_t e = ~(uint32_t)(b & 0xffffffffull);
+        mask[e] = 1;
+        const int32_t a = comp[eu[e]], c = comp[ev[e]];
+        parent[r] = (a == r) ? c : a;
+        *flag = 1;
+    }
+}
+
+__global__ void k_mst_break(int32_t n, const int32_t* __restrict__ comp, int32_t* __restrict__ parent) {
+    for (int64_t r = (int64_t)blockIdx.x * kBlock + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * kBlock) {
+        if (comp[r] != r) continue;
+        const int32_t p = parent[r];
+        // only the smaller label of a mutual pair writes, and it writes only its own entry
+        if (p != r && p > r && parent[p] == (int32_t)r) parent[r] = (int32_t)r;
+    }
+}
+
+// One synchronous pointer-jumping step on a forest: out[r] = in[in[r]]; flag set while any
+// node still moves. Only component labels take part when comp != NULL.
+__global__ void k_jump_step(int32_t n, const int32_t* __restrict__ comp,
+                            const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                            int* __restrict__ flag) {
+    for (int64_t r = (int64_t)blockIdx.x * kBlock + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * kBlock) {
+        if (comp && comp[r] != r) continue;
+        const int32_t p = in[r], pp = in[p];
+        out[r] = pp;
+        if (pp != p) *flag = 1;
+    }
+}
+
+__global__ void k_mst_relabel(int32_t n, int32_t* __restrict__ comp, const int32_t* __restrict__ parent) {
+    for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * kBlock)
+        comp[p] = parent[comp[p]];
+}
+
+__global__ void k_count_u8(int64_t m, const uint8_t* __restrict__ mask,
+                           unsigned long long* __restrict__ cnt) {
+    unsigned long long c = 0;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock)
+        c += mask[e] != 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+}  // namespace
+
+// Flatten a forest given by parent pointers (roots point to themselves) so that every entry
+// points at its root: synchronous doubling steps, convergence checked every fourth step.
+sfg_status sfg_pointer_jump(sfg_ctx* ctx, int32_t n, const int32_t* comp, int32_t* parent) {
+    if (n <= 0) return SFG_OK;
+    Scratch s(ctx);
+    int32_t* tmp;
+    int* flag;
+    SFG_TRY(s.get(&tmp, n));
+    SFG_TRY(s.get(&flag, 1));
+    const int grid = sfg_grid(ctx, (const void*)k_jump_step, kBlock, 0, n);
+    int32_t* a = parent;
+    int32_t* b = tmp;
+    for (int it = 0; it < 64; ++it) {
+        for (int k = 0; k < 4; ++k) {
+            if (k == 3) SFG_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+            k_jump_step<<<grid, kBlock, 0, ctx->stream>>>(n, comp, a, b, flag);
+            std::swap(a, b);
+        }
+        SFG_LAUNCH_CHECK(ctx, "k_jump_step");
+        int h = 0;
+        SFG_CUDA(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (!h) {
+            // after an even number of steps the result is back in `parent`
+            return SFG_OK;
+        }
+    }
+    return sfg_fail(ctx, SFG_ETIMEOUT, "pointer jumping did not converge");
+}
+
+sfg_status sfg_count_mask(sfg_ctx* ctx, const uint8_t* mask, int64_t m, int64_t* count_host) {
+    Scratch s(ctx);
+    unsigned long long* cnt;
+    SFG_TRY(s.get(&cnt, 1));
+    SFG_CUDA(ctx, cudaMemsetAsync(cnt, 0, 8, ctx->stream));
+    if (m > 0) {
+        k_count_u8<<<sfg_grid(ctx, (const void*)k_count_u8, kBlock, 0, m), kBlock, 0, ctx->stream>>>(
+            m, mask, cnt);
+        SFG_LAUNCH_CHECK(ctx, "k_count_u8");
+    }
+    return sfg_read_i64(ctx, (const int64_t*)cnt, count_host);
+}
+
+sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, uint8_t* mask,
+                        int64_t* n_tree) {
+    const int32_t n = g->n;
+    const int64_t m = g->m;
+    if (m > 0) SFG_CUDA(ctx, cudaMemsetAsync(mask, 0, m, ctx->stream));
+    if (m == 0) {
+        if (n_tree) *n_tree = 0;
+        return SFG_OK;
+    }
+    Scratch s(ctx);
+    int32_t *comp, *parent;
+    unsigned long long* best;
+    int* flag;
+    SFG_TRY(s.get(&comp, n));
+    SFG_TRY(s.get(&parent, n));
+    SFG_TRY(s.get(&best, n));
+    SFG_TRY(s.get(&flag, 1));
+    const int gn = sfg_grid(ctx, (const void*)k_mst_hook, kBlock, 0, n);
+    const int gm = sfg_grid(ctx, (const void*)k_mst_edges, kBlock, 0, m);
+    k_mst_init<<<gn, kBlock, 0, ctx->stream>>>(n, comp);
+    SFG_LAUNCH_CHECK(ctx, "k_mst_init");
+    // each round at least halves the number of components that still have outgoing edges
+    for (int round = 0; round < 64; ++round) {
+        k_mst_reset<<<gn, kBlock, 0, ctx->stream>>>(n, best, flag);
+        k_mst_edges<<<gm, kBlock, 0, ctx->stream>>>(m, g->eu, g->ev, g->ew, allow, comp, best);
+        k_mst_hook<<<gn, kBlock, 0, ctx->stream>>>(n, g->eu, g->ev, comp, best, parent, mask, flag);
+        SFG_LAUNCH_CHECK(ctx, "k_mst_round");
+        int hflag = 0;
+        SFG_CUDA(ctx, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (!hflag) {
+            if (n_tree) SFG_TRY(sfg_count_mask(ctx, mask, m, n_tree));
+            return SFG_OK;
+        }
+        k_mst_break<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent);
+        SFG_TRY(sfg_pointer_jump(ctx, n, comp, parent));
+        k_mst_relabel<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent);
+        SFG_LAUNCH_CHECK(ctx, "k_mst_relabel");
+    }
+    return sfg_fail(ctx, SFG_ETIMEOUT, "spanning forest did not converge in 64 rounds");
+}
+
+extern "C" sfg_status sfg_spanning_tree(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow,
+                                        uint8_t* mask_out, int64_t* n_tree_host) {
+    if (!ctx) return SFG_EINVAL;
+    if (!g) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
+    if (g->m > 0) {
+        SFG_TRY(sfg_check_dev(ctx, mask_out, "mask_out"));
+        if (allow) SFG_TRY(sfg_check_dev(ctx, allow, "allow"));
+    }
+    return sfg_mst_impl(ctx, g, allow, mask_out, n_tree_host);
+}

@@ -1,0 +1,178 @@
+// Edge scores. (1) Spectral-perturbation score of candidate edges (Sec. 3.5, Eqs.
+// formula_eig_perturb1_conclusion / formula_eig_perturb1_conclusion2 with U replaced by the
+// smoothed blocks; Algorithm 1 lines 13-14). (2) Algebraic-distance affinity that drives node
+// aggregation in coarsening (Sec. 3.2).
+//
+// Scorer schedule: the same LPR-lane group per item as the smoother. For each listed edge the
+// group gathers the two endpoint rows of both blocks (4 x 16 B per lane), forms the two squared
+// distances in FP32 and folds them with xor-shuffles inside the group.
+#include "sfg_internal.cuh"
+#include "vec.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int LPR>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+    if (LPR == 32) return 0xffffffffu;
+    return ((1u << LPR) - 1u) << ((lane / LPR) * LPR);
+}
+
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kBlock)
+    k_score(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
+            const int32_t* __restrict__ ev, const float* __restrict__ ew,
+            const T* __restrict__ XG, const T* __restrict__ XP, int mode, float eta,
+            float* __restrict__ out) {
+    constexpr int E = Vec<T>::E, K = LPR * E;
+    const int lane = threadIdx.x & 31, sub = lane % LPR;
+    const unsigned gm = group_mask<LPR>(lane);
+    const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
+    const int64_t ng = (int64_t)gridDim.x * kBlock / LPR;
+    for (int64_t i = g0; i < ne; i += ng) {
+        const int32_t e = ids[i];
+        const int64_t p = eu[e], q = ev[e];
+        float gp[E], gq[E], pp[E], pq[E];
+        Vec<T>::load(XG + p * K + sub * E, gp);
+        Vec<T>::load(XG + q * K + sub * E, gq);
+        Vec<T>::load(XP + p * K + sub * E, pp);
+        Vec<T>::load(XP + q * K + sub * E, pq);
+        float dg = 0.f, dp = 0.f;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const float a = gp[k] - gq[k], b = pp[k] - pq[k];
+            dg = fmaf(a, a, dg);
+            dp = fmaf(b, b, dp);
+        }
+#pragma unroll
+        for (int o = 1; o < LPR; o <<= 1) {
+            dg += __shfl_xor_sync(gm, dg, o, LPR);
+            dp += __shfl_xor_sync(gm, dp, o, LPR);
+        }
+        if (sub == 0) {
+            const float w = ew[e];
+            const float sg = w * dg, sp = w * dp;
+            out[i] = mode == SFG_SCORE_G ? sg : (mode == SFG_SCORE_P ? sp : sp / (sg + eta));
+        }
+    }
+}
+
+// ||X_p||^2 in FP64, increasing k, no fused multiply-add.
+__global__ void k_rownorm(int32_t n, const float* __restrict__ X, int K, double* __restrict__ nn) {
+    for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * kBlock) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double x = (double)X[p * K + k];
+            s = __dadd_rn(s, __dmul_rn(x, x));
+        }
+        nn[p] = s;
+    }
+}
+
+// delta_e = 1 - (X_p . X_q)^2 / (||X_p||^2 ||X_q||^2) in FP64, same operation order as the
+// definition, no fused multiply-add; a zero row gives 1.
+__global__ void k_affinity(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                           const float* __restrict__ X, int K, const double* __restrict__ nn,
+                           double* __restrict__ delta) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock) {
+        const int64_t p = eu[e], q = ev[e];
+        double dot = 0.0;
+        for (int k = 0; k < K; ++k)
+            dot = __dadd_rn(dot, __dmul_rn((double)X[p * K + k], (double)X[q * K + k]));
+        const double den = __dmul_rn(nn[p], nn[q]);
+        delta[e] = den > 0.0 ? __dsub_rn(1.0, __ddiv_rn(__dmul_rn(dot, dot), den)) : 1.0;
+    }
+}
+
+template <typename T, int LPR>
+sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
+                        const int32_t* ids, int64_t ne, int mode, float* out) {
+    if (ne == 0) return SFG_OK;
+    const int grid = sfg_grid(ctx, (const void*)k_score<T, LPR>, kBlock, 0, ne * LPR);
+    sfg_tic(ctx, "score");
+    k_score<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(ne, ids, LG->eu, LG->ev, LG->ew,
+                                                      (const T*)XG, (const T*)XP, mode, 1e-30f,
+                                                      out);
+    sfg_toc(ctx);
+    SFG_LAUNCH_CHECK(ctx, "k_score");
+    return SFG_OK;
+}
+
+}  // namespace
+
+sfg_status sfg_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
+                          int K, sfg_dtype storage, const int32_t* ids, int64_t ne,
+                          sfg_score_mode mode, float* out) {
+    if (storage == SFG_F32) {
+        switch (K) {
+            case 4: return launch_score<float, 1>(ctx, LG, XG, XP, ids, ne, mode, out);
+            case 8: return launch_score<float, 2>(ctx, LG, XG, XP, ids, ne, mode, out);
+            case 16: return launch_score<float, 4>(ctx, LG, XG, XP, ids, ne, mode, out);
+            case 32: return launch_score<float, 8>(ctx, LG, XG, XP, ids, ne, mode, out);
+            case 64: return launch_score<float, 16>(ctx, LG, XG, XP, ids, ne, mode, out);
+        }
+    } else if (storage == SFG_BF16) {
+        switch (K) {
+            case 8: return launch_score<__nv_bfloat16, 1>(ctx, LG, XG, XP, ids, ne, mode, out);
+            case 16: return launch_score<__nv_bfloat16, 2>(ctx, LG, XG, XP, ids, ne, mode, out);
+            case 32: return launch_score<__nv_bfloat16, 4>(ctx, LG, XG, XP, ids, ne, mode, out);
+            case 64: return launch_score<__nv_bfloat16, 8>(ctx, LG, XG, XP, ids, ne, mode, out);
+        }
+    }
+    return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", K, (int)storage);
+}
+
+sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
+                             double* delta) {
+    Scratch s(ctx);
+    double* nn;
+    SFG_TRY(s.get(&nn, (size_t)L->n));
+    k_rownorm<<<sfg_grid(ctx, (const void*)k_rownorm, kBlock, 0, L->n), kBlock, 0, ctx->stream>>>(
+        L->n, X, K, nn);
+    SFG_LAUNCH_CHECK(ctx, "k_rownorm");
+    if (L->m > 0) {
+        sfg_tic(ctx, "affinity");
+        k_affinity<<<sfg_grid(ctx, (const void*)k_affinity, kBlock, 0, L->m), kBlock, 0,
+                     ctx->stream>>>(L->m, L->eu, L->ev, X, K, nn, delta);
+        sfg_toc(ctx);
+        SFG_LAUNCH_CHECK(ctx, "k_affinity");
+    }
+    return SFG_OK;
+}
+
+extern "C" {
+
+sfg_status sfg_score_edges(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
+                           int K, sfg_dtype storage, const int32_t* edge_ids, int64_t ne,
+                           sfg_score_mode mode, float* scores_out) {
+    if (!ctx) return SFG_EINVAL;
+    if (!LG) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
+    if (ne < 0) return sfg_fail(ctx, SFG_EINVAL, "ne must be >= 0");
+    if (mode != SFG_SCORE_RATIO && mode != SFG_SCORE_G && mode != SFG_SCORE_P)
+        return sfg_fail(ctx, SFG_EINVAL, "unknown score mode %d", (int)mode);
+    if (!sfg_k_supported(K, storage))
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", K, (int)storage);
+    if (ne == 0) return SFG_OK;
+    SFG_TRY(sfg_check_dev(ctx, XG, "XG"));
+    SFG_TRY(sfg_check_dev(ctx, XP, "XP"));
+    SFG_TRY(sfg_check_dev(ctx, edge_ids, "edge_ids"));
+    SFG_TRY(sfg_check_dev(ctx, scores_out, "scores_out"));
+    if ((((uintptr_t)XG) | ((uintptr_t)XP)) & 15)
+        return sfg_fail(ctx, SFG_EINVAL, "XG and XP must be 16-byte aligned");
+    return sfg_score_impl(ctx, LG, XG, XP, K, storage, edge_ids, ne, mode, scores_out);
+}
+
+sfg_status sfg_affinity(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
+                        double* delta_out) {
+    if (!ctx) return SFG_EINVAL;
+    if (!L) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
+    if (K < 1) return sfg_fail(ctx, SFG_EINVAL, "K must be >= 1");
+    SFG_TRY(sfg_check_dev(ctx, X, "X"));
+    if (L->m > 0) SFG_TRY(sfg_check_dev(ctx, delta_out, "delta_out"));
+    return sfg_affinity_impl(ctx, L, X, K, delta_out);
+}
+
+}  // extern "C"

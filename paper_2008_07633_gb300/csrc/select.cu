@@ -1,0 +1,141 @@
+// Top-k selection (Algorithm 1 line 14: "include top few edges with large distortion").
+//
+// Each candidate becomes a unique 64-bit key: the order-preserving image of its FP32 score in the
+// high word and the complement of its id in the low word, so "larger key" is exactly the strict
+// order (score descending, id ascending). An MSB-first radix select (8 passes of 8-bit digits,
+// histogram in shared memory, the digit pick done on the device) finds the k-th largest key
+// without any host round trip; one compaction pass keeps the keys at or above it and a small
+// radix sort returns the chosen ids in ascending order.
+#include "sfg_internal.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ uint64_t sel_key(float s, int32_t id) {
+    const uint32_t b = __float_as_uint(s);
+    const uint32_t o = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    return ((uint64_t)o << 32) | (uint64_t)(~(uint32_t)id);
+}
+
+struct SelState {
+    unsigned long long prefix;
+    long long krem;
+    unsigned long long hist[256];
+};
+
+__global__ void k_sel_init(SelState* st, int64_t k) {
+    st->prefix = 0ull;
+    st->krem = k;
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) st->hist[d] = 0ull;
+}
+
+__global__ void __launch_bounds__(kBlock)
+    k_sel_hist(int64_t ne, const float* __restrict__ scores, const int32_t* __restrict__ ids,
+               int shift, SelState* __restrict__ st) {
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t prefix = st->prefix;
+    const int hi = shift + 8;  // bits at and above `hi` must match the prefix
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < ne;
+         i += (int64_t)gridDim.x * kBlock) {
+        const uint64_t key = sel_key(scores[i], ids[i]);
+        if (hi >= 64 || (key >> hi) == (prefix >> hi)) atomicAdd(&h[(key >> shift) & 0xff], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
+__global__ void k_sel_pick(int shift, SelState* st) {
+    if (threadIdx.x == 0) {
+        long long above = 0;
+        int d = 255;
+        for (; d > 0; --d) {
+            const long long c = (long long)st->hist[d];
+            if (above + c >= st->krem) break;
+            above += c;
+        }
+        st->prefix |= (unsigned long long)d << shift;
+        st->krem -= above;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) st->hist[d] = 0ull;
+}
+
+__global__ void k_sel_flags(int64_t ne, const float* __restrict__ scores,
+                            const int32_t* __restrict__ ids, const SelState* __restrict__ st,
+                            uint8_t* __restrict__ flag) {
+    const uint64_t thr = st->prefix;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < ne;
+         i += (int64_t)gridDim.x * kBlock)
+        flag[i] = sel_key(scores[i], ids[i]) >= thr;
+}
+
+__global__ void k_sel_compact(int64_t ne, const int32_t* __restrict__ ids,
+                              const uint8_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                              uint64_t* __restrict__ out_keys, uint32_t* __restrict__ out_vals) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < ne;
+         i += (int64_t)gridDim.x * kBlock)
+        if (flag[i]) {
+            out_keys[pos[i]] = (uint64_t)(uint32_t)ids[i];
+            out_vals[pos[i]] = 0u;
+        }
+}
+
+__global__ void k_sel_emit(int64_t k, const uint64_t* __restrict__ keys, int32_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < k;
+         i += (int64_t)gridDim.x * kBlock)
+        out[i] = (int32_t)keys[i];
+}
+
+}  // namespace
+
+sfg_status sfg_topk_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids, int64_t ne,
+                         int64_t k, int32_t* out) {
+    if (k == 0) return SFG_OK;
+    Scratch s(ctx);
+    SelState* st;
+    uint8_t* flag;
+    int64_t* pos;
+    uint64_t *ka, *kb;
+    uint32_t *va, *vb;
+    SFG_TRY(s.get(&st, 1));
+    SFG_TRY(s.get(&flag, ne));
+    SFG_TRY(s.get(&pos, ne + 1));
+    SFG_TRY(s.get(&ka, k));
+    SFG_TRY(s.get(&kb, k));
+    SFG_TRY(s.get(&va, k));
+    SFG_TRY(s.get(&vb, k));
+    const int grid = sfg_grid(ctx, (const void*)k_sel_hist, kBlock, 0, ne);
+    sfg_tic(ctx, "topk");
+    k_sel_init<<<1, kBlock, 0, ctx->stream>>>(st, k);
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        k_sel_hist<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, shift, st);
+        k_sel_pick<<<1, kBlock, 0, ctx->stream>>>(shift, st);
+    }
+    k_sel_flags<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, st, flag);
+    sfg_toc(ctx);
+    SFG_LAUNCH_CHECK(ctx, "k_sel");
+    SFG_TRY(sfg_scan_u8(ctx, flag, pos, ne));
+    k_sel_compact<<<grid, kBlock, 0, ctx->stream>>>(ne, ids, flag, pos, ka, va);
+    SFG_LAUNCH_CHECK(ctx, "k_sel_compact");
+    SFG_TRY(sfg_radix_sort_pairs(ctx, &ka, &va, &kb, &vb, k, 32));
+    k_sel_emit<<<sfg_grid(ctx, (const void*)k_sel_emit, kBlock, 0, k), kBlock, 0, ctx->stream>>>(
+        k, ka, out);
+    SFG_LAUNCH_CHECK(ctx, "k_sel_emit");
+    return SFG_OK;
+}
+
+extern "C" sfg_status sfg_select_topk(sfg_ctx* ctx, const float* scores, const int32_t* ids,
+                                      int64_t ne, int64_t k, int32_t* ids_out) {
+    if (!ctx) return SFG_EINVAL;
+    if (ne < 0 || k < 0 || k > ne)
+        return sfg_fail(ctx, SFG_EINVAL, "need 0 <= k <= ne (k=%lld, ne=%lld)", (long long)k,
+                        (long long)ne);
+    if (k == 0) return SFG_OK;
+    SFG_TRY(sfg_check_dev(ctx, scores, "scores"));
+    SFG_TRY(sfg_check_dev(ctx, ids, "ids"));
+    SFG_TRY(sfg_check_dev(ctx, ids_out, "ids_out"));
+    return sfg_topk_impl(ctx, scores, ids, ne, k, ids_out);
+}

@@ -1,0 +1,160 @@
+// Internal declarations shared by the translation units of libsfg (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/sfg.h"
+
+// ------------------------------------------------------------------------------------------------
+// Context: device, borrowed stream, last error text, optional per-kernel event timers.
+// ------------------------------------------------------------------------------------------------
+struct sfg_timer_rec {
+    const char* name;
+    cudaEvent_t start, stop;
+};
+
+struct sfg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string last_error;
+    bool timing = false;
+    std::vector<sfg_timer_rec> timers;     // recorded this session
+    std::vector<cudaEvent_t> event_pool;   // free events
+    int64_t alloc_count = 0;               // for the allocation-failure injection hook
+    int64_t fail_alloc_at = -1;            // SFG_FAULT_ALLOC=<n>: the n-th allocation fails
+};
+
+struct sfg_graph {
+    int32_t n = 0;
+    int64_t m = 0;             // canonical edges
+    int32_t* eu = nullptr;     // [m] canonical edge endpoints, eu < ev, sorted
+    int32_t* ev = nullptr;
+    float* ew = nullptr;       // [m]
+    int32_t* row_ptr = nullptr;// [n+1]
+    int2* colval = nullptr;    // [2m] (column, float bits of the weight), rows sorted by column
+    int32_t* eid = nullptr;    // [2m] canonical edge id of each CSR entry
+    double* deg = nullptr;     // [n]
+    cudaStream_t stream = nullptr;
+};
+
+// ------------------------------------------------------------------------------------------------
+// Status helpers. Every API entry point returns through these so the text lands in ctx.
+// ------------------------------------------------------------------------------------------------
+sfg_status sfg_fail(sfg_ctx* ctx, sfg_status st, const char* fmt, ...);
+sfg_status sfg_cuda_fail(sfg_ctx* ctx, cudaError_t e, const char* where);
+
+#define SFG_CUDA(ctx, call)                                                 \
+    do {                                                                    \
+        cudaError_t _e = (call);                                            \
+        if (_e != cudaSuccess) return sfg_cuda_fail((ctx), _e, #call);      \
+    } while (0)
+
+#define SFG_TRY(call)                                                       \
+    do {                                                                    \
+        sfg_status _s = (call);                                             \
+        if (_s != SFG_OK) return _s;                                        \
+    } while (0)
+
+#define SFG_LAUNCH_CHECK(ctx, name)                                         \
+    do {                                                                    \
+        cudaError_t _e = cudaGetLastError();                                \
+        if (_e != cudaSuccess) return sfg_cuda_fail((ctx), _e, name);       \
+    } while (0)
+
+// Stream-ordered device allocation from the context's pool (cudaMallocAsync).
+sfg_status sfg_alloc(sfg_ctx* ctx, void** p, size_t bytes);
+void sfg_free(sfg_ctx* ctx, void* p);
+
+// Scoped list of scratch allocations released (stream-ordered) at scope exit.
+struct Scratch {
+    sfg_ctx* ctx;
+    std::vector<void*> ptrs;
+    explicit Scratch(sfg_ctx* c) : ctx(c) {}
+    ~Scratch() {
+        for (void* p : ptrs) sfg_free(ctx, p);
+    }
+    template <typename T>
+    sfg_status get(T** p, size_t count) {
+        void* q = nullptr;
+        sfg_status s = sfg_alloc(ctx, &q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+        if (s != SFG_OK) return s;
+        ptrs.push_back(q);
+        *p = static_cast<T*>(q);
+        return SFG_OK;
+    }
+    void release(void* p) {  // hand ownership to the caller
+        for (auto& q : ptrs)
+            if (q == p) q = nullptr;
+    }
+};
+
+// Kernel timing (no-ops unless ctx->timing).
+void sfg_tic(sfg_ctx* ctx, const char* name);
+void sfg_toc(sfg_ctx* ctx);
+
+// Pointer checks: NULL or not device-accessible memory -> SFG_EINVAL.
+sfg_status sfg_check_dev(sfg_ctx* ctx, const void* p, const char* what);
+
+// Grid size for a grid-stride kernel: a whole number of waves over the SMs.
+int sfg_grid(sfg_ctx* ctx, const void* kernel, int block, size_t smem, int64_t work_items);
+
+static inline unsigned ceil_div_u(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------------------------------------
+// Device primitives (primitives.cu)
+// ------------------------------------------------------------------------------------------------
+// out[i] = sum_{j<i} in[j] for i in [0, n]; out has n + 1 entries (out[n] = total).
+sfg_status sfg_scan_u8(sfg_ctx* ctx, const uint8_t* in, int64_t* out, int64_t n);
+sfg_status sfg_scan_i32(sfg_ctx* ctx, const int32_t* in, int64_t* out, int64_t n);
+sfg_status sfg_scan_i64(sfg_ctx* ctx, const int64_t* in, int64_t* out, int64_t n);
+// Stable LSD radix sort of (key, val) pairs on the low `bits` bits of the keys. The sorted data
+// ends in (*keys, *vals); the pointers may be swapped with the alternate buffers.
+sfg_status sfg_radix_sort_pairs(sfg_ctx* ctx, uint64_t** keys, uint32_t** vals,
+                                uint64_t** keys_alt, uint32_t** vals_alt, int64_t n, int bits);
+// Copy scalars back (synchronises the stream).
+sfg_status sfg_read_i64(sfg_ctx* ctx, const int64_t* dev, int64_t* host);
+
+// ------------------------------------------------------------------------------------------------
+// Cross-unit helpers
+// ------------------------------------------------------------------------------------------------
+// Build an sfg_graph from an input edge list already on the device (validated or not).
+sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
+                           const int32_t* v, const float* w, bool validate, sfg_graph** out,
+                           int32_t* fine2coarse_out);
+sfg_status sfg_subgraph_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* mask,
+                             sfg_graph** out);
+sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, uint8_t* mask,
+                        int64_t* n_tree);
+sfg_status sfg_smooth_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
+                           uint64_t seed, sfg_dtype storage, void* X_out);
+sfg_status sfg_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
+                          int K, sfg_dtype storage, const int32_t* ids, int64_t ne,
+                          sfg_score_mode mode, float* out);
+sfg_status sfg_topk_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids, int64_t ne,
+                         int64_t k, int32_t* out);
+sfg_status sfg_coarsen_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
+                            int32_t* agg, int32_t* f2c, int32_t* nc, sfg_graph** coarse);
+sfg_status sfg_backward_impl(sfg_ctx* ctx, const sfg_graph* fine, const int32_t* agg,
+                             const int32_t* f2c, const sfg_graph* coarse, const uint8_t* pmask_c,
+                             uint8_t* pmask_f);
+void sfg_graph_free(sfg_graph* g);
+bool sfg_k_supported(int K, sfg_dtype dt);
+
+// splitmix64 (Steele, Lea & Flood 2014), host and device.
+__host__ __device__ inline uint64_t sfg_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+sfg_status sfg_pointer_jump(sfg_ctx* ctx, int32_t n, const int32_t* comp, int32_t* parent);
+sfg_status sfg_count_mask(sfg_ctx* ctx, const uint8_t* mask, int64_t m, int64_t* count_host);
+sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
+                             double* delta);

@@ -1,0 +1,181 @@
+// The whole method (Algorithm 1), orchestrated on the host over the device kernels.
+//
+// Flat: maximum spanning forest of G, then one round of edge recovery: embed G and the current
+// sparsifier P from the same seed, score every edge of G outside P, add the top ones. Multilevel:
+// coarsen `levels` times (caching each level's embedding), sparsify the coarsest graph flat, then
+// for each finer level map the sparsifier back and run edge recovery there with the cached
+// embedding of G_l.
+#include <cmath>
+
+#include "sfg_internal.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__global__ void k_not_mask(int64_t m, const uint8_t* __restrict__ mask, uint8_t* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock)
+        out[e] = mask[e] == 0;
+}
+
+__global__ void k_compact_ids(int64_t m, const uint8_t* __restrict__ flag,
+                              const int64_t* __restrict__ pos, int32_t* __restrict__ ids) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock)
+        if (flag[e]) ids[pos[e]] = (int32_t)e;
+}
+
+__global__ void k_set_mask(int64_t k, const int32_t* __restrict__ ids, uint8_t* __restrict__ mask) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < k;
+         i += (int64_t)gridDim.x * kBlock)
+        mask[ids[i]] = 1;
+}
+
+__global__ void k_f32_to_bf16(int64_t n, const float* __restrict__ x, __nv_bfloat16* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kBlock)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+uint64_t level_seed(uint64_t seed, int l) { return l == 0 ? seed : sfg_splitmix64(seed ^ (uint64_t)l); }
+
+int64_t round_half_up(double x) { return (int64_t)std::floor(x + 0.5); }
+
+size_t elem_size(sfg_dtype dt) { return dt == SFG_BF16 ? 2 : 4; }
+
+// Edge recovery at one level (Sec. 3.5, Algorithm 1 lines 12-14). `mask` holds the current
+// sparsifier of g and receives the added edges. XG_f32: the FP32 embedding of g from this level's
+// seed (may be NULL: computed here in the requested storage).
+sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64_t seed,
+                   int64_t forest, const float* XG_f32, uint8_t* mask) {
+    const int64_t m = g->m;
+    const int64_t base = P->budget_unit == 0 ? (int64_t)g->n : m - forest;
+    const int64_t target = round_half_up(P->budget_frac * (double)base);
+    int64_t in_p = 0;
+    SFG_TRY(sfg_count_mask(ctx, mask, m, &in_p));
+    const int64_t ncand = m - in_p;
+    int64_t k = target - (in_p - forest);
+    if (k < 0) k = 0;
+    if (k > ncand) k = ncand;
+    if (k == 0) return SFG_OK;
+
+    Scratch s(ctx);
+    uint8_t* flag;
+    int64_t* pos;
+    int32_t *cand, *sel;
+    float* scores;
+    SFG_TRY(s.get(&flag, m));
+    SFG_TRY(s.get(&pos, m + 1));
+    SFG_TRY(s.get(&cand, ncand));
+    SFG_TRY(s.get(&scores, ncand));
+    SFG_TRY(s.get(&sel, k));
+    const int gm = sfg_grid(ctx, (const void*)k_not_mask, kBlock, 0, m);
+    k_not_mask<<<gm, kBlock, 0, ctx->stream>>>(m, mask, flag);
+    SFG_LAUNCH_CHECK(ctx, "k_not_mask");
+    SFG_TRY(sfg_scan_u8(ctx, flag, pos, m));
+    k_compact_ids<<<gm, kBlock, 0, ctx->stream>>>(m, flag, pos, cand);
+    SFG_LAUNCH_CHECK(ctx, "k_compact_ids");
+
+    sfg_graph* pg = nullptr;
+    SFG_TRY(sfg_subgraph_impl(ctx, g, mask, &pg));
+    struct Guard { sfg_graph* g; ~Guard() { sfg_graph_free(g); } } guard{pg};
+
+    const size_t blk = (size_t)g->n * P->K * elem_size(P->storage);
+    void* xp;
+    SFG_TRY(s.get((char**)&xp, blk));
+    const void* xg = XG_f32;  // the cached FP32 embedding is used as is
+    if (!XG_f32 || P->storage != SFG_F32) {
+        void* x;
+        SFG_TRY(s.get((char**)&x, blk));
+        if (XG_f32) {
+            const int64_t cnt = (int64_t)g->n * P->K;
+            k_f32_to_bf16<<<sfg_grid(ctx, (const void*)k_f32_to_bf16, kBlock, 0, cnt), kBlock, 0,
+                            ctx->stream>>>(cnt, XG_f32, (__nv_bfloat16*)x);
+            SFG_LAUNCH_CHECK(ctx, "k_f32_to_bf16");
+        } else {
+            SFG_TRY(sfg_smooth_impl(ctx, g, P->K, P->steps, P->omega, seed, P->storage, x));
+        }
+        xg = x;
+    }
+    SFG_TRY(sfg_smooth_impl(ctx, pg, P->K, P->steps, P->omega, seed, P->storage, xp));
+    SFG_TRY(sfg_score_impl(ctx, g, xg, xp, P->K, P->storage, cand, ncand, P->mode, scores));
+    SFG_TRY(sfg_topk_impl(ctx, scores, cand, ncand, k, sel));
+    k_set_mask<<<sfg_grid(ctx, (const void*)k_set_mask, kBlock, 0, k), kBlock, 0, ctx->stream>>>(
+        k, sel, mask);
+    SFG_LAUNCH_CHECK(ctx, "k_set_mask");
+    return SFG_OK;
+}
+
+struct Level {
+    sfg_graph* g = nullptr;   // G_l (level 0 borrowed)
+    int32_t* agg = nullptr;   // map G_{l-1} -> G_l (l >= 1)
+    int32_t* f2c = nullptr;   // fine edge of G_{l-1} -> edge of G_l
+    float* xg = nullptr;      // FP32 embedding of G_l used for coarsening (l < lf)
+};
+
+}  // namespace
+
+extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* P,
+                                   uint8_t* mask_out, int64_t* n_selected_host) {
+    if (!ctx) return SFG_EINVAL;
+    if (!G || !P) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
+    if (!sfg_k_supported(P->K, P->storage) || !sfg_k_supported(P->K, SFG_F32))
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K,
+                        (int)P->storage);
+    if (P->steps < 0 || P->levels < 0 || !(P->omega > 0.0 && P->omega <= 1.0) ||
+        !(P->budget_frac >= 0.0) || (P->budget_unit != 0 && P->budget_unit != 1) ||
+        (P->mode != SFG_SCORE_RATIO && P->mode != SFG_SCORE_G && P->mode != SFG_SCORE_P))
+        return sfg_fail(ctx, SFG_EINVAL, "invalid sfg_params");
+    if (G->m > 0) SFG_TRY(sfg_check_dev(ctx, mask_out, "mask_out"));
+
+    std::vector<Level> lv(1);
+    lv[0].g = const_cast<sfg_graph*>(G);
+    Scratch s(ctx);
+    struct Cleanup {
+        std::vector<Level>* lv;
+        ~Cleanup() {
+            for (size_t i = 1; i < lv->size(); ++i) sfg_graph_free((*lv)[i].g);
+        }
+    } cleanup{&lv};
+
+    // Algorithm 1 line 2: multilevel spectral graph reduction
+    for (int l = 1; l <= P->levels; ++l) {
+        Level& f = lv.back();
+        if (f.g->m == 0) break;
+        SFG_TRY(s.get(&f.xg, (size_t)f.g->n * P->K));
+        SFG_TRY(sfg_smooth_impl(ctx, f.g, P->K, P->steps, P->omega, level_seed(P->seed, l - 1),
+                                SFG_F32, f.xg));
+        Level c;
+        SFG_TRY(s.get(&c.agg, f.g->n));
+        SFG_TRY(s.get(&c.f2c, f.g->m));
+        int32_t nc = 0;
+        SFG_TRY(sfg_coarsen_impl(ctx, f.g, f.xg, P->K, c.agg, c.f2c, &nc, &c.g));
+        lv.push_back(c);
+    }
+    const int lf = (int)lv.size() - 1;
+
+    // coarsest level: spanning forest + recovered off-tree edges
+    const sfg_graph* gc = lv[lf].g;
+    uint8_t* pm;
+    SFG_TRY(s.get(&pm, gc->m));
+    int64_t n_tree = 0;
+    SFG_TRY(sfg_mst_impl(ctx, gc, nullptr, pm, &n_tree));
+    const int64_t comps = (int64_t)gc->n - n_tree;  // same at every level: aggregates are connected
+    SFG_TRY(recover(ctx, gc, P, level_seed(P->seed, lf), n_tree, nullptr, pm));
+
+    // Algorithm 1 lines 4-17: map back and recover edges level by level
+    for (int l = lf; l >= 1; --l) {
+        const sfg_graph* f = lv[l - 1].g;
+        uint8_t* pf;
+        SFG_TRY(s.get(&pf, f->m));
+        SFG_TRY(sfg_backward_impl(ctx, f, lv[l].agg, lv[l].f2c, lv[l].g, pm, pf));
+        SFG_TRY(recover(ctx, f, P, level_seed(P->seed, l - 1), (int64_t)f->n - comps, lv[l - 1].xg,
+                        pf));
+        pm = pf;
+    }
+    if (G->m > 0)
+        SFG_CUDA(ctx, cudaMemcpyAsync(mask_out, pm, G->m, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (n_selected_host) SFG_TRY(sfg_count_mask(ctx, mask_out, G->m, n_selected_host));
+    return SFG_OK;
+}

@@ -1,0 +1,290 @@
+"""Thin Python binding of libsfg (include/sfg.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls. Tensors are PyTorch CUDA tensors used
+as device memory; the context queues work on a CUDA stream (by default PyTorch's current stream at
+creation). No computation happens here: a missing or unloadable libsfg.so raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsfg.so")
+
+SFG_F32, SFG_BF16 = 0, 1
+SFG_SCORE_RATIO, SFG_SCORE_G, SFG_SCORE_P = 0, 1, 2
+STATUS = {0: "SFG_OK", 1: "SFG_EINVAL", 2: "SFG_ENOMEM", 3: "SFG_ECUDA", 4: "SFG_ETIMEOUT",
+          5: "SFG_ECAPACITY", 6: "SFG_EUNSUPPORTED"}
+
+# Every symbol declared in include/sfg.h.
+EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_error",
+           "sfg_ctx_timing", "sfg_ctx_kernel_time", "sfg_laplacian", "sfg_graph_destroy",
+           "sfg_graph_info", "sfg_graph_edges", "sfg_graph_csr", "sfg_graph_subgraph", "sfg_smooth",
+           "sfg_jacobi", "sfg_score_edges", "sfg_select_topk", "sfg_spanning_tree", "sfg_affinity",
+           "sfg_coarsen", "sfg_backward_map", "sfg_sparsify"]
+
+
+class SfgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sfg_params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("steps", ctypes.c_int), ("levels", ctypes.c_int),
+                ("omega", ctypes.c_double), ("seed", ctypes.c_uint64), ("mode", ctypes.c_int),
+                ("budget_frac", ctypes.c_double), ("budget_unit", ctypes.c_int),
+                ("storage", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32, _i64, _int, _dbl, _u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+_pi32, _pi64, _pdbl = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """Load libsfg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2008_07633_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "sfg_ctx_create": [ctypes.POINTER(_vp), _int, _vp],
+            "sfg_ctx_destroy": [_vp],
+            "sfg_ctx_set_stream": [_vp, _vp],
+            "sfg_last_error": [_vp],
+            "sfg_ctx_timing": [_vp, _int],
+            "sfg_ctx_kernel_time": [_vp, ctypes.c_char_p, _pi64, _pdbl],
+            "sfg_laplacian": [_vp, _i32, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp)],
+            "sfg_graph_destroy": [_vp],
+            "sfg_graph_info": [_vp, _pi32, _pi64],
+            "sfg_graph_edges": [_vp, _vp, _vp, _vp, _vp],
+            "sfg_graph_csr": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
+            "sfg_graph_subgraph": [_vp, _vp, _vp, ctypes.POINTER(_vp)],
+            "sfg_smooth": [_vp, _vp, _int, _int, _dbl, _u64, _int, _vp],
+            "sfg_jacobi": [_vp, _vp, _int, _int, _dbl, _int, _vp],
+            "sfg_score_edges": [_vp, _vp, _vp, _vp, _int, _int, _vp, _i64, _int, _vp],
+            "sfg_select_topk": [_vp, _vp, _vp, _i64, _i64, _vp],
+            "sfg_spanning_tree": [_vp, _vp, _vp, _vp, _pi64],
+            "sfg_affinity": [_vp, _vp, _vp, _int, _vp],
+            "sfg_coarsen": [_vp, _vp, _vp, _int, _vp, _vp, _pi32, ctypes.POINTER(_vp)],
+            "sfg_backward_map": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
+            "sfg_sparsify": [_vp, _vp, ctypes.POINTER(sfg_params), _vp, _pi64],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None if name in ("sfg_ctx_destroy", "sfg_graph_destroy") else _int
+        L.sfg_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dt(dtype):
+    if dtype in (torch.float32, SFG_F32):
+        return SFG_F32
+    if dtype in (torch.bfloat16, SFG_BF16):
+        return SFG_BF16
+    raise ValueError(f"unsupported storage {dtype}")
+
+
+def _tdt(code):
+    return torch.float32 if code == SFG_F32 else torch.bfloat16
+
+
+class Context:
+    def __init__(self, device=0, stream=None):
+        self.device = torch.device("cuda", device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._stream = s
+        h = _vp()
+        st = lib().sfg_ctx_create(ctypes.byref(h), device, _vp(s.cuda_stream))
+        if st != 0:
+            raise SfgError(st, "sfg_ctx_create failed")
+        self.h = h
+
+    def check(self, st):
+        if st != 0:
+            raise SfgError(st, lib().sfg_last_error(self.h).decode())
+
+    def set_stream(self, stream):
+        self._stream = stream
+        self.check(lib().sfg_ctx_set_stream(self.h, _vp(stream.cuda_stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sfg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Graph:
+    """Owner of an sfg_graph handle."""
+
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+        n, m = _i32(), _i64()
+        lib().sfg_graph_info(h, ctypes.byref(n), ctypes.byref(m))
+        self.n, self.m = n.value, m.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sfg_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sfg_ctx_create(device=0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def sfg_ctx_timing(ctx, on=True):
+    ctx.check(lib().sfg_ctx_timing(ctx.h, 1 if on else 0))
+
+
+def sfg_ctx_kernel_time(ctx, prefix):
+    n, ms = _i64(), _dbl()
+    ctx.check(lib().sfg_ctx_kernel_time(ctx.h, prefix.encode(), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def sfg_laplacian(ctx, n, u, v, w) -> Graph:
+    u, v, w = u.contiguous(), v.contiguous(), w.contiguous()
+    assert u.dtype == torch.int32 and v.dtype == torch.int32 and w.dtype == torch.float32
+    h = _vp()
+    ctx.check(lib().sfg_laplacian(ctx.h, int(n), int(u.numel()), _ptr(u), _ptr(v), _ptr(w),
+                                  ctypes.byref(h)))
+    return Graph(ctx, h)
+
+
+def sfg_graph_info(g):
+    return g.n, g.m
+
+
+def sfg_graph_edges(ctx, g):
+    dev = ctx.device
+    u = torch.empty(g.m, dtype=torch.int32, device=dev)
+    v = torch.empty(g.m, dtype=torch.int32, device=dev)
+    w = torch.empty(g.m, dtype=torch.float32, device=dev)
+    ctx.check(lib().sfg_graph_edges(ctx.h, g.h, _ptr(u), _ptr(v), _ptr(w)))
+    return u, v, w
+
+
+def sfg_graph_csr(ctx, g):
+    dev = ctx.device
+    rp = torch.empty(g.n + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(2 * g.m, dtype=torch.int32, device=dev)
+    val = torch.empty(2 * g.m, dtype=torch.float32, device=dev)
+    eid = torch.empty(2 * g.m, dtype=torch.int32, device=dev)
+    deg = torch.empty(g.n, dtype=torch.float64, device=dev)
+    ctx.check(lib().sfg_graph_csr(ctx.h, g.h, _ptr(rp), _ptr(col), _ptr(val), _ptr(eid), _ptr(deg)))
+    return rp, col, val, eid, deg
+
+
+def sfg_graph_subgraph(ctx, g, mask) -> Graph:
+    mask = mask.contiguous()
+    assert mask.dtype == torch.uint8 and mask.numel() == g.m
+    h = _vp()
+    ctx.check(lib().sfg_graph_subgraph(ctx.h, g.h, _ptr(mask), ctypes.byref(h)))
+    return Graph(ctx, h)
+
+
+def sfg_smooth(ctx, g, K, steps, omega=0.7, seed=0, storage=torch.float32, out=None):
+    code = _dt(storage)
+    if out is None:
+        out = torch.empty((g.n, K), dtype=_tdt(code), device=ctx.device)
+    ctx.check(lib().sfg_smooth(ctx.h, g.h, K, steps, omega, seed & (2**64 - 1), code, _ptr(out)))
+    return out
+
+
+def sfg_jacobi(ctx, g, X, steps, omega=0.7):
+    assert X.is_contiguous()
+    ctx.check(lib().sfg_jacobi(ctx.h, g.h, X.shape[1], steps, omega, _dt(X.dtype), _ptr(X)))
+    return X
+
+
+def sfg_score_edges(ctx, g, XG, XP, ids, mode=SFG_SCORE_RATIO, out=None):
+    assert XG.dtype == XP.dtype and XG.shape == XP.shape
+    ids = ids.contiguous()
+    if out is None:
+        out = torch.empty(ids.numel(), dtype=torch.float32, device=ctx.device)
+    ctx.check(lib().sfg_score_edges(ctx.h, g.h, _ptr(XG), _ptr(XP), XG.shape[1], _dt(XG.dtype),
+                                    _ptr(ids), ids.numel(), mode, _ptr(out)))
+    return out
+
+
+def sfg_select_topk(ctx, scores, ids, k, out=None):
+    if out is None:
+        out = torch.empty(max(int(k), 0), dtype=torch.int32, device=ctx.device)
+    ctx.check(lib().sfg_select_topk(ctx.h, _ptr(scores.contiguous()), _ptr(ids.contiguous()),
+                                    ids.numel(), int(k), _ptr(out)))
+    return out
+
+
+def sfg_spanning_tree(ctx, g, allow=None):
+    mask = torch.empty(g.m, dtype=torch.uint8, device=ctx.device)
+    nt = _i64()
+    ctx.check(lib().sfg_spanning_tree(ctx.h, g.h, _ptr(allow), _ptr(mask), ctypes.byref(nt)))
+    return mask, nt.value
+
+
+def sfg_affinity(ctx, g, X):
+    assert X.dtype == torch.float32 and X.is_contiguous()
+    d = torch.empty(g.m, dtype=torch.float64, device=ctx.device)
+    ctx.check(lib().sfg_affinity(ctx.h, g.h, _ptr(X), X.shape[1], _ptr(d)))
+    return d
+
+
+def sfg_coarsen(ctx, g, X):
+    assert X.dtype == torch.float32 and X.is_contiguous()
+    agg = torch.empty(g.n, dtype=torch.int32, device=ctx.device)
+    f2c = torch.empty(g.m, dtype=torch.int32, device=ctx.device)
+    nc = _i32()
+    h = _vp()
+    ctx.check(lib().sfg_coarsen(ctx.h, g.h, _ptr(X), X.shape[1], _ptr(agg), _ptr(f2c),
+                                ctypes.byref(nc), ctypes.byref(h)))
+    return agg, f2c, Graph(ctx, h)
+
+
+def sfg_backward_map(ctx, fine, agg, f2c, coarse, pmask_c):
+    out = torch.empty(fine.m, dtype=torch.uint8, device=ctx.device)
+    ctx.check(lib().sfg_backward_map(ctx.h, fine.h, _ptr(agg), _ptr(f2c), coarse.h,
+                                     _ptr(pmask_c.contiguous()), _ptr(out)))
+    return out
+
+
+def sfg_sparsify(ctx, g, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=SFG_SCORE_RATIO,
+                 budget_frac=0.1, budget_unit=1, storage=torch.float32, out=None):
+    p = sfg_params(K, steps, levels, omega, seed & (2**64 - 1), mode, budget_frac, budget_unit,
+                   _dt(storage))
+    if out is None:
+        out = torch.empty(g.m, dtype=torch.uint8, device=ctx.device)
+    ns = _i64()
+    ctx.check(lib().sfg_sparsify(ctx.h, g.h, ctypes.byref(p), _ptr(out), ctypes.byref(ns)))
+    return out, ns.value

@@ -1,0 +1,73 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports exactly the symbols
+include/sfg.h declares, and its host-side argument handling answers with status codes (no GPU
+needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "sfg.h")).read()
+    return sorted(set(re.findall(r"^SFG_API [^;]*?\b(sfg_\w+)\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2008_07633_gb300 import build
+
+    build.build()
+    import paper_2008_07633_gb300.sfg as S
+
+    return S.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = header_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(lib, s), s
+    import paper_2008_07633_gb300.sfg as S
+
+    assert sorted(S.EXPORTS) == syms
+
+
+def test_no_internal_symbols_exported(lib):
+    import subprocess
+
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True)
+    text_syms = [l.split()[-1] for l in out.stdout.splitlines() if " T " in l]
+    assert sorted(text_syms) == header_symbols()
+
+
+def test_host_side_status_without_gpu(lib):
+    # no context pointer -> EINVAL, never a crash
+    assert lib.sfg_ctx_timing(None, 1) == 1
+    assert lib.sfg_last_error(None) == b""
+    h = ctypes.c_void_p()
+    st = lib.sfg_ctx_create(ctypes.byref(h), 0, None)
+    try:
+        import torch
+
+        have_gpu = torch.cuda.is_available()
+    except Exception:
+        have_gpu = False
+    if have_gpu:
+        assert st == 0
+        lib.sfg_ctx_destroy(h)
+    else:
+        assert st != 0 and not h.value
+    assert lib.sfg_ctx_create(None, 0, None) == 1
+    assert lib.sfg_graph_info(None, None, None) == 1
+
+
+def test_params_struct_layout():
+    import paper_2008_07633_gb300.sfg as S
+
+    # C layout of sfg_params on LP64: 3 ints, pad, double, uint64, enum, pad, double, int, enum
+    assert ctypes.sizeof(S.sfg_params) == 56
+    assert S.sfg_params.omega.offset == 16 and S.sfg_params.seed.offset == 24
+    assert S.sfg_params.budget_frac.offset == 40 and S.sfg_params.storage.offset == 52

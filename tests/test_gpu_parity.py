@@ -1,0 +1,368 @@
+"""GPU parity: every C-ABI step against the CPU oracle on the same seeded inputs.
+
+Bars: integer, index and mask results bit-exact; FP32 vectors within 1e-5 normwise relative per
+column; FP32 scores within 1e-5 relative per edge (relative to max(|ref|, 1e-6 * median |ref|));
+sparsifier condition numbers within 5% of the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2008_07633_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+TOL_X = 1e-5
+TOL_S = 1e-5
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2008_07633_gb300.sfg as S
+
+    S.lib()
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    c = S.sfg_ctx_create(0)
+    yield c
+    c.close()
+
+
+DEV = torch.device("cuda", 0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def make(S, ctx, n, u, v, w):
+    return S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w)), O.canonicalize(n, u, v, w)
+
+
+def colwise_err(x, ref):
+    return (np.linalg.norm(x - ref, axis=0) / np.maximum(np.linalg.norm(ref, axis=0), 1e-300)).max()
+
+
+def score_err(s, ref):
+    floor = 1e-6 * np.median(np.abs(ref)) if ref.size else 0.0
+    return (np.abs(s - ref) / np.maximum(np.abs(ref), max(floor, 1e-300))).max() if ref.size else 0.0
+
+
+GRAPHS = {
+    "grid64": lambda: gen.grid2d(64, 64, seed=1),
+    "multigraph": lambda: gen.random_graph(3001, 12000, seed=3, dup_frac=0.1, self_loops=17),
+    "disconnected": lambda: gen.random_graph(2500, 3000, seed=4, connected=False),
+    "intweights": lambda: gen.random_graph(1500, 6000, seed=5, lo=1, hi=4),
+    "grid3d": lambda: gen.grid3d(17, seed=2),
+}
+
+
+def _intw(spec):
+    n, u, v, w = spec
+    return n, u, v, np.floor(w).astype(np.float32)
+
+
+# ------------------------------------------------------------------ Laplacian ------------------
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_laplacian_bit_exact(S, ctx, name):
+    spec = GRAPHS[name]()
+    if name == "intweights":
+        spec = _intw(spec)
+    g, og = make(S, ctx, *spec)
+    assert (g.n, g.m) == (og.n, og.m)
+    u, v, w = (host(t) for t in S.sfg_graph_edges(ctx, g))
+    assert np.array_equal(u, og.u) and np.array_equal(v, og.v)
+    assert np.array_equal(w.view(np.uint32), og.w.view(np.uint32))
+    rp, col, val, eid, deg = (host(t) for t in S.sfg_graph_csr(ctx, g))
+    orp, ocol, oval, oeid, odeg = O.laplacian_csr(og)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol) and np.array_equal(eid, oeid)
+    assert np.array_equal(val.astype(np.float64), oval)
+    assert np.array_equal(deg.view(np.uint64), odeg.view(np.uint64))
+
+
+def test_laplacian_rejects_bad_input(S, ctx):
+    n, u, v, w = gen.grid2d(8, 8)
+    for bad in ("range", "neg", "nan", "zero"):
+        uu, ww = u.copy(), w.copy()
+        if bad == "range":
+            uu[5] = n
+        elif bad == "neg":
+            ww[3] = -1.0
+        elif bad == "nan":
+            ww[3] = np.nan
+        else:
+            ww[7] = 0.0
+        with pytest.raises(S.SfgError) as e:
+            S.sfg_laplacian(ctx, n, dev(uu), dev(v), dev(ww))
+        assert e.value.status == 1
+    with pytest.raises(S.SfgError):
+        S.sfg_laplacian(ctx, 0, dev(u[:0]), dev(v[:0]), dev(w[:0]))
+
+
+def test_laplacian_edge_cases(S, ctx):
+    # no edges; only self-loops; a single node
+    g, og = make(S, ctx, 5, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    assert g.m == 0 and np.array_equal(host(S.sfg_graph_csr(ctx, g)[0]), np.zeros(6, np.int32))
+    g, og = make(S, ctx, 3, np.array([1, 2], np.int32), np.array([1, 2], np.int32),
+                 np.array([1.0, 2.0], np.float32))
+    assert g.m == 0
+    g, og = make(S, ctx, 1, np.array([0], np.int32), np.array([0], np.int32),
+                 np.array([1.0], np.float32))
+    assert g.n == 1 and g.m == 0
+
+
+@pytest.mark.parametrize("name", ["multigraph", "disconnected"])
+def test_subgraph_bit_exact(S, ctx, name):
+    spec = GRAPHS[name]()
+    g, og = make(S, ctx, *spec)
+    rng = np.random.default_rng(0)
+    mask = (rng.random(og.m) < 0.4).astype(np.uint8)
+    p = S.sfg_graph_subgraph(ctx, g, dev(mask))
+    op = og.subgraph(mask)
+    u, v, w = (host(t) for t in S.sfg_graph_edges(ctx, p))
+    assert np.array_equal(u, op.u) and np.array_equal(v, op.v) and np.array_equal(w, op.w)
+    rp, col, val, eid, deg = (host(t) for t in S.sfg_graph_csr(ctx, p))
+    orp, ocol, oval, oeid, odeg = O.laplacian_csr(op)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol) and np.array_equal(eid, oeid)
+    assert np.array_equal(deg, odeg)
+
+
+# ------------------------------------------------------------------ Smoothing ------------------
+@pytest.mark.parametrize("K,T", [(8, 10), (4, 3), (16, 7), (32, 20), (64, 5), (8, 0), (32, 1)])
+def test_smooth_fp32(S, ctx, K, T):
+    g, og = make(S, ctx, *gen.grid2d(64, 64, seed=1))
+    x = host(S.sfg_smooth(ctx, g, K, T, 0.7, seed=1001))
+    ref = O.smooth(og, K, T, 0.7, seed=1001)
+    err = colwise_err(x.astype(np.float64), ref)
+    assert err < TOL_X, err
+
+
+@pytest.mark.parametrize("name", ["multigraph", "disconnected", "grid3d"])
+def test_smooth_fp32_graphs(S, ctx, name):
+    g, og = make(S, ctx, *GRAPHS[name]())
+    x = host(S.sfg_smooth(ctx, g, 32, 20, 0.7, seed=7))
+    ref = O.smooth(og, 32, 20, 0.7, seed=7)
+    err = colwise_err(x.astype(np.float64), ref)
+    assert err < TOL_X, err
+
+
+@pytest.mark.parametrize("K", [4, 16, 64])
+def test_jacobi_same_input(S, ctx, K):
+    # raw sweeps from an identical FP32 block: ragged n (not a multiple of any tile), isolated nodes
+    n, u, v, w = gen.random_graph(4099, 9000, seed=11, connected=False)
+    g, og = make(S, ctx, n, u, v, w)
+    x0 = gen.gaussian_block(n, K, seed=12)
+    x = host(S.sfg_jacobi(ctx, g, dev(x0), 9, 0.7))
+    ref = O.jacobi(og, x0.astype(np.float64), 9, 0.7)
+    assert colwise_err(x.astype(np.float64), ref) < TOL_X
+
+
+def test_smooth_bf16_error_reported(S, ctx):
+    # BF16 storage is reported, not gated at 1e-5: its unit roundoff is 2^-9
+    g, og = make(S, ctx, *gen.grid2d(64, 64, seed=1))
+    x = host(S.sfg_smooth(ctx, g, 32, 10, 0.7, seed=3, storage=torch.bfloat16).float())
+    ref = O.smooth(og, 32, 10, 0.7, seed=3)
+    err = colwise_err(x.astype(np.float64), ref)
+    assert err < 2e-2, err
+
+
+def test_smooth_unsupported_k(S, ctx):
+    g, _ = make(S, ctx, *gen.grid2d(8, 8))
+    with pytest.raises(S.SfgError) as e:
+        S.sfg_smooth(ctx, g, 12, 3)
+    assert e.value.status == 6
+    with pytest.raises(S.SfgError):
+        S.sfg_smooth(ctx, g, 8, 3, omega=1.5)
+
+
+# ------------------------------------------------------------------ Scores ---------------------
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("K", [8, 32, 64])
+def test_score_same_input(S, ctx, mode, K):
+    n, u, v, w = gen.random_graph(5000, 20000, seed=21)
+    g, og = make(S, ctx, n, u, v, w)
+    xg = gen.gaussian_block(n, K, seed=1)
+    xp = gen.gaussian_block(n, K, seed=2)
+    ids = np.arange(0, og.m, 3, dtype=np.int32)[::-1].copy()   # unsorted, ragged count
+    s = host(S.sfg_score_edges(ctx, g, dev(xg), dev(xp), dev(ids), mode=mode))
+    ref = O.score_edges(og, xg, xp, ids, mode)
+    assert score_err(s.astype(np.float64), ref) < TOL_S
+
+
+def test_score_pipeline_grid(S, ctx):
+    # smoothed on the GPU vs smoothed by the oracle, then scored: RATIO mode
+    n, u, v, w = gen.grid2d(64, 64, seed=1)
+    g, og = make(S, ctx, n, u, v, w)
+    tree, _ = S.sfg_spanning_tree(ctx, g)
+    p = S.sfg_graph_subgraph(ctx, g, tree)
+    xg = S.sfg_smooth(ctx, g, 8, 10, 0.7, seed=1001)
+    xp = S.sfg_smooth(ctx, p, 8, 10, 0.7, seed=1001)
+    off = np.nonzero(host(tree) == 0)[0].astype(np.int32)
+    s = host(S.sfg_score_edges(ctx, g, xg, xp, dev(off)))
+    otree = O.mst(og)
+    ref = O.score_edges(og, O.smooth(og, 8, 10, 0.7, 1001),
+                        O.smooth(og.subgraph(otree), 8, 10, 0.7, 1001), off)
+    err = np.linalg.norm(s - ref) / np.linalg.norm(ref)
+    assert err < TOL_S, err
+
+
+# ------------------------------------------------------------------ Top-k ----------------------
+@pytest.mark.parametrize("ne,k", [(1, 1), (1000, 0), (1000, 1000), (77777, 1234), (300001, 29999)])
+def test_topk_bit_exact(S, ctx, ne, k):
+    rng = np.random.default_rng(ne + k)
+    scores = rng.integers(0, 50, ne).astype(np.float32) * np.float32(0.25)   # heavy ties
+    cont = rng.random(ne) < 0.5
+    scores[cont] = rng.random(int(cont.sum())).astype(np.float32)
+    ids = rng.permutation(3 * ne)[:ne].astype(np.int32)
+    out = host(S.sfg_select_topk(ctx, dev(scores), dev(ids), k))
+    ref = O.topk(scores.astype(np.float64), ids, k)
+    assert np.array_equal(out, ref)
+
+
+def test_topk_all_equal_and_negative(S, ctx):
+    ids = np.arange(5000, dtype=np.int32)[::-1].copy()
+    out = host(S.sfg_select_topk(ctx, dev(np.ones(5000, np.float32)), dev(ids), 100))
+    assert np.array_equal(out, np.arange(100))
+    rng = np.random.default_rng(3)
+    sc = rng.standard_normal(20000).astype(np.float32)
+    ids = np.arange(20000, dtype=np.int32)
+    out = host(S.sfg_select_topk(ctx, dev(sc), dev(ids), 777))
+    assert np.array_equal(out, O.topk(sc.astype(np.float64), ids, 777))
+    with pytest.raises(S.SfgError):
+        S.sfg_select_topk(ctx, dev(sc), dev(ids), 20001)
+
+
+# ------------------------------------------------------------------ Spanning tree --------------
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_spanning_tree_bit_exact(S, ctx, name):
+    spec = GRAPHS[name]()
+    if name == "intweights":
+        spec = _intw(spec)
+    g, og = make(S, ctx, *spec)
+    mask, nt = S.sfg_spanning_tree(ctx, g)
+    ref = O.mst(og)
+    assert np.array_equal(host(mask), ref)
+    assert nt == int(ref.sum()) == og.n - O.components(og)
+
+
+def test_spanning_tree_allow_mask(S, ctx):
+    n, u, v, w = _intw(gen.random_graph(2000, 8000, seed=6, lo=1, hi=3))
+    g, og = make(S, ctx, n, u, v, w)
+    allow = (np.random.default_rng(1).random(og.m) < 0.6).astype(np.uint8)
+    mask, _ = S.sfg_spanning_tree(ctx, g, dev(allow))
+    assert np.array_equal(host(mask), O.mst(og, allow))
+
+
+def test_spanning_tree_path_chain(S, ctx):
+    # monotone weights along a path: every Boruvka hook forms one long chain
+    n = 100000
+    u = np.arange(n - 1, dtype=np.int32)
+    w = (1.0 + np.arange(n - 1)).astype(np.float32)
+    g, og = make(S, ctx, n, u, u + 1, w)
+    mask, nt = S.sfg_spanning_tree(ctx, g)
+    assert nt == n - 1 and host(mask).all()
+
+
+# ------------------------------------------------------------------ Coarsening -----------------
+@pytest.mark.parametrize("name", ["grid64", "multigraph", "disconnected"])
+def test_affinity_and_coarsen_bit_exact(S, ctx, name):
+    g, og = make(S, ctx, *GRAPHS[name]())
+    x = gen.gaussian_block(og.n, 8, seed=5)
+    x[::97] = 0.0                                           # zero rows -> delta = 1
+    d = host(S.sfg_affinity(ctx, g, dev(x)))
+    od = O.affinity(og, x.astype(np.float64))
+    assert np.array_equal(d.view(np.uint64), od.view(np.uint64))
+    agg, f2c, c = S.sfg_coarsen(ctx, g, dev(x))
+    oagg, nc = O.aggregate(og, od)
+    assert np.array_equal(host(agg), oagg) and c.n == nc
+    oc, of2c = O.galerkin(og, oagg, nc)
+    cu, cv, cw = (host(t) for t in S.sfg_graph_edges(ctx, c))
+    assert np.array_equal(cu, oc.u) and np.array_equal(cv, oc.v)
+    assert np.array_equal(cw.view(np.uint32), oc.w.view(np.uint32))
+    assert np.array_equal(host(f2c), of2c)
+
+
+@pytest.mark.parametrize("name", ["grid64", "multigraph"])
+def test_backward_map_bit_exact(S, ctx, name):
+    g, og = make(S, ctx, *GRAPHS[name]())
+    x = gen.gaussian_block(og.n, 8, seed=9)
+    agg, f2c, c = S.sfg_coarsen(ctx, g, dev(x))
+    oagg, nc = O.aggregate(og, O.affinity(og, x.astype(np.float64)))
+    oc, of2c = O.galerkin(og, oagg, nc)
+    rng = np.random.default_rng(2)
+    pc = (rng.random(oc.m) < 0.5).astype(np.uint8)
+    pf = host(S.sfg_backward_map(ctx, g, agg, f2c, c, dev(pc)))
+    assert np.array_equal(pf, O.backward_map(og, oagg, of2c, oc, pc))
+
+
+# ------------------------------------------------------------------ Algorithm 1 ----------------
+def _kappa_close(og, gmask, omask):
+    kg, ko = O.kappa_dense(og, gmask), O.kappa_dense(og, omask)
+    assert abs(kg - ko) <= 0.05 * ko, (kg, ko)
+    return kg, ko
+
+
+def test_sparsify_flat_c1(S, ctx):
+    # 64 x 64 grid, weights U[1,10), K = 8, 10 sweeps, omega 0.7, 10% of the off-tree edges
+    n, u, v, w = gen.grid2d(64, 64, seed=1)
+    g, og = make(S, ctx, n, u, v, w)
+    mask, nsel = S.sfg_sparsify(ctx, g, K=8, steps=10, levels=0, seed=1001, budget_frac=0.1,
+                                budget_unit=1)
+    omask, _ = O.sparsify(og, K=8, steps=10, levels=0, seed=1001, budget_frac=0.1, budget_unit=1)
+    gm = host(mask)
+    tree = O.mst(og)
+    assert np.all(gm[tree == 1] == 1)
+    assert nsel == int(omask.sum()) == og.n - 1 + 397
+    overlap = ((gm == 1) & (omask == 1) & (tree == 0)).sum() / 397
+    assert overlap > 0.9, overlap
+    _kappa_close(og, gm, omask)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sparsify_flat_modes(S, ctx, mode):
+    n, u, v, w = gen.grid2d(40, 40, seed=3)
+    g, og = make(S, ctx, n, u, v, w)
+    mask, _ = S.sfg_sparsify(ctx, g, K=16, steps=12, levels=0, seed=5, mode=mode,
+                             budget_frac=0.08, budget_unit=0)
+    omask, _ = O.sparsify(og, K=16, steps=12, levels=0, seed=5, mode=mode, budget_frac=0.08,
+                          budget_unit=0)
+    _kappa_close(og, host(mask), omask)
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_sparsify_multilevel(S, ctx, levels):
+    n, u, v, w = gen.grid2d(48, 48, seed=4, weights="logu", lo=-2, hi=2)
+    g, og = make(S, ctx, n, u, v, w)
+    mask, nsel = S.sfg_sparsify(ctx, g, K=8, steps=10, levels=levels, seed=17, budget_frac=0.05,
+                                budget_unit=0)
+    omask, lf = O.sparsify(og, K=8, steps=10, levels=levels, seed=17, budget_frac=0.05,
+                           budget_unit=0)
+    assert lf == levels
+    kg, ko = _kappa_close(og, host(mask), omask)
+    assert np.isfinite(kg)
+
+
+def test_sparsify_tree_input_returns_itself(S, ctx):
+    n, u, v, w = gen.random_graph(3000, 2999, seed=8)
+    g, og = make(S, ctx, n, u, v, w)
+    mask, nsel = S.sfg_sparsify(ctx, g, K=8, steps=5, levels=0)
+    assert host(mask).all() and nsel == og.m
+
+
+def test_sparsify_bf16_storage(S, ctx):
+    n, u, v, w = gen.grid2d(40, 40, seed=5)
+    g, og = make(S, ctx, n, u, v, w)
+    mask, _ = S.sfg_sparsify(ctx, g, K=16, steps=10, levels=0, seed=5, budget_frac=0.1,
+                             budget_unit=1, storage=torch.bfloat16)
+    omask, _ = O.sparsify(og, K=16, steps=10, levels=0, seed=5, budget_frac=0.1, budget_unit=1)
+    kg, ko = O.kappa_dense(og, host(mask)), O.kappa_dense(og, omask)
+    assert kg <= 1.25 * ko, (kg, ko)     # reported tolerance for BF16 storage
