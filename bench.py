@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the SF-GRASS hot path on one GB300: filter + score throughput.
+
+Workload (one step): the 3-D 6-neighbour grid 128^3 (2,097,152 nodes, 6,242,304 edges, weights
+10^U[-2,2)), K = 32 seeded vectors, 20 weighted-Jacobi sweeps (omega 0.7) on the Laplacian of G and
+on that of its maximum spanning tree P, projection, RATIO scores of all 4,145,153 off-tree edges and
+the top round(0.05 N) = 104,858 of them. G, P and the off-tree id list are built once before the
+timed region (they are the inputs of the filter); every step recomputes everything else.
+
+Metric: filter+score algorithmic GB/s = bytes / step time with
+  B_sweep(L)  = 4(N+1) + 8 nnz(L) + 4N + 2 N K s     (row_ptr, (col, w), D^-1, X read + X written)
+  B_score     = 20 E_off + 2 N K s                    (id, endpoints, weight, score; both blocks)
+  B_step      = T (B_sweep(G) + B_sweep(P)) + B_score
+The timed region uses inputs larger than L2 (each vector block is 268 MB), so no L2 flush is done.
+
+Multi-GPU: the workload is one graph; N > 1 runs N independent replicas (weak scaling, no
+collective on the data path), one per rank, and the value is the sum over ranks.
+
+--impl reference times the CPU oracle (single thread, FP64) on a bounded sample of the same
+workload: the first 32 of the 128 planes (524,288 nodes), same K, sweeps and budget fraction.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+SIDE, K, T, OMEGA, SEED, BETA = 128, 32, 20, 0.7, 1002, 0.05
+SAMPLE_PLANES = 32
+METRIC = "filter+score GB/s (% HBM peak); sparsify time at matched kappa vs plain FP32"
+UNIT = "GB/s"
+
+
+def workload_name(side=SIDE):
+    return f"grid3d-{side}^3 6-neighbour, w=10^U[-2,2), K={K}, T={T}, omega={OMEGA}, fp32, flat filter+score+top-5%N"
+
+
+def sweep_bytes(n, nnz, k=K, s=4):
+    return 4 * (n + 1) + 8 * nnz + 4 * n + 2 * n * k * s
+
+
+def score_bytes(n, e_off, k=K, s=4):
+    return 20 * e_off + 2 * n * k * s
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_file, summary):
+    """DRAM bytes per launch from the committed ncu summary, or None if the kernel source changed
+    since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2008_07633_gb300", "csrc", kernel_file)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m_sha and m_b):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != m_sha.group(1):
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle on a bounded sample of the workload
+# ------------------------------------------------------------------------------------------------
+def oracle_sample():
+    import oracle as O
+    from paper_2008_07633_gb300 import inputs as gen
+
+    n, u, v, w = gen.grid3d(SIDE, seed=2)
+    ns = SAMPLE_PLANES * SIDE * SIDE
+    keep = (u < ns) & (v < ns)
+    g = O.canonicalize(ns, u[keep], v[keep], w[keep])
+    tree = O.mst(g)
+    p = g.subgraph(tree)
+    off = np.nonzero(tree == 0)[0].astype(np.int32)
+    k = int(np.floor(BETA * ns + 0.5))
+    nbytes = T * (sweep_bytes(ns, 2 * g.m) + sweep_bytes(ns, 2 * p.m)) + score_bytes(ns, off.size)
+
+    def step():
+        xg = O.smooth(g, K, T, OMEGA, SEED)
+        xp = O.smooth(p, K, T, OMEGA, SEED)
+        s = O.score_edges(g, xg, xp, off)
+        O.topk(s, off, k)
+
+    desc = (f"oracle (1 thread, FP64) on the first {SAMPLE_PLANES} of {SIDE} planes: {ns} nodes, "
+            f"{g.m} edges, {off.size} off-tree edges; full filter+score step (init, {T} sweeps on "
+            f"G and P, projection, scoring, top-{k})")
+    return step, nbytes, desc
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    step, nbytes, desc = oracle_sample()
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = nbytes / dt / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_name() + " (oracle sample)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def cpu_baseline():
+    step, nbytes, desc = oracle_sample()
+    t0 = time.perf_counter()
+    step()
+    dt = time.perf_counter() - t0
+    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": desc + f"; one step, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    import paper_2008_07633_gb300.sfg as S
+    from paper_2008_07633_gb300 import inputs as gen
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    n, u, v, w = gen.grid3d(SIDE, seed=2)
+    ctx = S.sfg_ctx_create(local)
+    U, V, W = (torch.from_numpy(a).to(dev) for a in (u, v, w))
+    G = S.sfg_laplacian(ctx, n, U, V, W)
+    tree, ntree = S.sfg_spanning_tree(ctx, G)
+    P = S.sfg_graph_subgraph(ctx, G, tree)
+    off = torch.nonzero(tree == 0).flatten().to(torch.int32)
+    e_off = off.numel()
+    kk = int(np.floor(BETA * n + 0.5))
+    XG = torch.empty((n, K), dtype=torch.float32, device=dev)
+    XP = torch.empty_like(XG)
+    scores = torch.empty(e_off, dtype=torch.float32, device=dev)
+    sel = torch.empty(kk, dtype=torch.int32, device=dev)
+    b_sweep_g, b_sweep_p = sweep_bytes(n, 2 * G.m), sweep_bytes(n, 2 * P.m)
+    b_step = T * (b_sweep_g + b_sweep_p) + score_bytes(n, e_off)
+
+    def step():
+        S.sfg_smooth(ctx, G, K, T, OMEGA, SEED, out=XG)
+        S.sfg_smooth(ctx, P, K, T, OMEGA, SEED, out=XP)
+        S.sfg_score_edges(ctx, G, XG, XP, off, out=scores)
+        S.sfg_select_topk(ctx, scores, off, kk, out=sel)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    S.sfg_ctx_timing(ctx, True)
+    l0 = S.sfg_ctx_launches(ctx)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    launches = S.sfg_ctx_launches(ctx) - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    nj, ms_j = S.sfg_ctx_kernel_time(ctx, "jacobi")
+    ns_, ms_s = S.sfg_ctx_kernel_time(ctx, "score")
+    S.sfg_ctx_timing(ctx, False)
+    if pg:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * b_step / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the Jacobi sweep), from its live CUDA-event durations
+    peak, peak_kind = load_peaks()
+    achieved = (args.steps * T * (b_sweep_g + b_sweep_p)) / (ms_j * 1e-3) / 1e9 if ms_j > 0 else None
+    traffic = ncu_traffic("smooth.cu", "k_jacobi_grid3d128_k32.txt")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "kernel": "k_jacobi", "peak_kind": peak_kind,
+            "bytes_per_launch": (b_sweep_g + b_sweep_p) / 2, "launches": nj,
+            "avg_launch_us": ms_j / nj * 1e3 if nj else None,
+            "score_kernel_GBps": score_bytes(n, e_off) * ns_ / (ms_s * 1e-3) / 1e9 if ms_s else None}
+
+    # sparsify time (device-resident G) and the end-to-end number through the public API with
+    # host buffers: H2D of the edge list, Laplacian, flat sparsify, D2H of the mask
+    if args.profile:  # launch-list / counter captures: the filter+score steps only
+        if rank == 0:
+            print(json.dumps({"profile": True, "ms_per_step": ms, "value": value,
+                              "roofline": roof, "gpu_launches": launches}), flush=True)
+        return 0
+    hu, hv, hw = (torch.from_numpy(a).pin_memory() for a in (u, v, w))
+    mask_host = torch.empty(G.m, dtype=torch.uint8).pin_memory()
+
+    def sparsify_only():
+        m_, _ = S.sfg_sparsify(ctx, G, K=K, steps=T, levels=0, omega=OMEGA, seed=SEED,
+                               budget_frac=BETA, budget_unit=0)
+        return m_
+
+    def e2e_step():
+        du, dv, dw = (t.to(dev, non_blocking=True) for t in (hu, hv, hw))
+        g2 = S.sfg_laplacian(ctx, n, du, dv, dw)
+        m_, _ = S.sfg_sparsify(ctx, g2, K=K, steps=T, levels=0, omega=OMEGA, seed=SEED,
+                               budget_frac=BETA, budget_unit=0)
+        mask_host.copy_(m_, non_blocking=True)
+        torch.cuda.synchronize()
+        g2.close()
+
+    e2e_iters = max(2, args.steps // 3)
+    sparsify_only()
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_iters):
+        sparsify_only()
+    torch.cuda.synchronize()
+    sparsify_ms = (time.perf_counter() - t0) / e2e_iters * 1e3
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_iters):
+        e2e_step()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) / e2e_iters * 1e3
+    if pg:
+        t = torch.tensor([e2e_ms, sparsify_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms, sparsify_ms = (float(x) for x in t.tolist())
+
+    if rank != 0:
+        return 0
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": workload_name(), "nodes": n, "edges": G.m, "nnz_G": 2 * G.m,
+                      "nnz_P": 2 * P.m, "off_tree_edges": e_off, "k_selected": kk,
+                      "bytes_per_step": b_step,
+                      "l2": "inputs larger than L2 (each N x K block is 268 MB); no flush",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roof,
+           "clocks": clk.summary(),
+           "e2e": {"value": world * b_step / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                   "h2d_bytes_per_step": int(u.nbytes + v.nbytes + w.nbytes),
+                   "d2h_bytes_per_step": int(G.m), "ms_per_step": e2e_ms,
+                   "what": "pinned host edge list -> H2D -> sfg_laplacian -> sfg_sparsify (flat) -> D2H mask"},
+           "sparsify_ms": sparsify_ms,
+           "gpu_launches": launches}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="time only the filter+score steps (for ncu launch lists and counters)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -80,6 +80,9 @@ SFG_API sfg_status sfg_ctx_timing(sfg_ctx* ctx, int on);
 SFG_API sfg_status sfg_ctx_kernel_time(sfg_ctx* ctx, const char* prefix, int64_t* launches_host,
                                double* ms_host);
 
+/* Number of kernels this context has launched so far (host counter, no synchronisation). */
+SFG_API sfg_status sfg_ctx_launches(const sfg_ctx* ctx, int64_t* launches_host);
+
 /* ---------------------------------------------------------------------------------------------
  * Graph and Laplacian (Sec. 2.1, Eq. formula_adjacency and the definition of D under it;
  * Sec. 4 input convention: positive weights)
@@ -113,12 +116,12 @@ SFG_API sfg_status sfg_graph_subgraph(sfg_ctx* ctx, const sfg_graph* g, const ui
  * ------------------------------------------------------------------------------------------- */
 
 /* X_out (n x K, row-major, `storage`) <- the smoothed, projected block:
- *  1. X0[i,k] = Gaussian draw j = i*K + k of the counter-based generator below, rounded to
- *     `storage`; each column's mean (FP64) removed.
- *     Generator: h = splitmix64 (Steele, Lea & Flood 2014); a = h(seed ^ h(2j)),
- *     b = h(seed ^ h(2j+1)); u1 = ((a >> 11) + 1) 2^-53, u2 = (b >> 11) 2^-53;
- *     X0 = sqrt(-2 ln u1) cos(2 pi u2); the uniforms are formed exactly in FP64 and the
- *     transform is evaluated in FP32 (logf, cospif), within a few FP32 ulp of the FP64 value.
+ *  1. X0[i,k] = Gaussian entry j = i*K + k of this counter-based generator, rounded to
+ *     `storage`; each column's mean (FP64) removed. SplitMix64 (Steele, Lea & Flood 2014),
+ *     started in state s0 = splitmix64(seed), gives output o_p = splitmix64(s0 + p * gamma) for
+ *     the pair of entries 2p, 2p+1: u1 = ((o_p >> 32) + 1) 2^-32, u2 = ((o_p >> 8) mod 2^24)
+ *     2^-24, r = sqrt(-2 ln u1), X0_2p = r cos(2 pi u2), X0_2p+1 = r sin(2 pi u2). Evaluated in
+ *     FP32 (logf, sincospif), within a few FP32 ulp of the FP64 value.
  *  2. `steps` weighted-Jacobi sweeps X <- X - omega D^-1 L X = (1 - omega) X + omega D^-1 A X
  *     (D^-1 formed in FP64 once per call; rows with D(p,p) = 0 are left unchanged).
  *  3. Projection: each column's mean removed again and the column scaled to unit RMS.

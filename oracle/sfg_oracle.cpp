@@ -27,26 +27,31 @@ namespace {
 
 // ---------------------------------------------------------------------------------------------
 // Counter-based Gaussian generator (reading of Sec. 3.2 "K initial random vectors"; the paper
-// does not fix a distribution or generator). splitmix64 is the published mixer of Steele, Lea
-// and Flood (OOPSLA 2014): add the golden-ratio increment, then the 64-bit finaliser. Element
-// j = i*K + k of the N x K block takes two draws a = mix(seed ^ mix(2j)), b = mix(seed ^ mix(2j+1)),
-// two uniforms u1 = ((a >> 11) + 1) * 2^-53 in (0,1], u2 = (b >> 11) * 2^-53 in [0,1), and the
-// cosine branch of Box-Muller: z = sqrt(-2 ln u1) * cos(2 pi u2).
+// does not fix a distribution or generator). SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the
+// generator adds the golden gamma to its state and returns the 64-bit finaliser of the new state;
+// splitmix64(x) below is that finaliser applied to x + gamma, i.e. the output of a generator in
+// state x. The stream starts in state s0 = splitmix64(seed), so its output number p + 1 is
+// o_p = splitmix64(s0 + p * gamma) and any output is reachable directly from its index.
+// Output o_p feeds entries 2p and 2p+1 of the row-major N x K block (entry j = i*K + k) through
+// both branches of Box-Muller: u1 = ((o_p >> 32) + 1) 2^-32 in (0,1], u2 = ((o_p >> 8) mod 2^24)
+// 2^-24 in [0,1), r = sqrt(-2 ln u1), x_2p = r cos(2 pi u2), x_2p+1 = r sin(2 pi u2).
 // ---------------------------------------------------------------------------------------------
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
 uint64_t splitmix64(uint64_t x) {
-    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    uint64_t z = x + kGamma;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
 
 double gaussian_draw(uint64_t seed, uint64_t j) {
-    const uint64_t a = splitmix64(seed ^ splitmix64(2 * j));
-    const uint64_t b = splitmix64(seed ^ splitmix64(2 * j + 1));
-    const double u1 = (double)((a >> 11) + 1) * 0x1.0p-53;
-    const double u2 = (double)(b >> 11) * 0x1.0p-53;
+    const uint64_t o = splitmix64(splitmix64(seed) + (j >> 1) * kGamma);
+    const double u1 = (double)((o >> 32) + 1) * 0x1.0p-32;
+    const double u2 = (double)((o >> 8) & 0xffffffull) * 0x1.0p-24;
     const double two_pi = 6.283185307179586;
-    return std::sqrt(-2.0 * std::log(u1)) * std::cos(two_pi * u2);
+    const double r = std::sqrt(-2.0 * std::log(u1));
+    return (j & 1) ? r * std::sin(two_pi * u2) : r * std::cos(two_pi * u2);
 }
 
 // Seed of the level-l embedding in the multilevel method (reading: each level re-embeds its own

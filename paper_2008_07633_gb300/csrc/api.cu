@@ -166,4 +166,10 @@ sfg_status sfg_ctx_kernel_time(sfg_ctx* ctx, const char* prefix, int64_t* launch
     return SFG_OK;
 }
 
+sfg_status sfg_ctx_launches(const sfg_ctx* ctx, int64_t* launches_host) {
+    if (!ctx || !launches_host) return SFG_EINVAL;
+    *launches_host = ctx->launches;
+    return SFG_OK;
+}
+
 }  // extern "C"

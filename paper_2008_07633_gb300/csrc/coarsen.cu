@@ -120,16 +120,16 @@ static sfg_status aggregate(sfg_ctx* ctx, const sfg_graph* L, const double* delt
     SFG_TRY(s.get(&first, n));
     SFG_TRY(s.get(&rank, (size_t)n + 1));
     const int gn = grid_of(ctx, k_hook, n);
-    k_hook<<<gn, kBlock, 0, ctx->stream>>>(n, L->row_ptr, L->colval, L->eid, delta, hook);
-    k_hook_forest<<<gn, kBlock, 0, ctx->stream>>>(n, hook, root);
+    k_hook<<<gn, kBlock, 0, ctx->stream>>>(n, L->row_ptr, L->colval, L->eid, delta, hook); ++ctx->launches;
+    k_hook_forest<<<gn, kBlock, 0, ctx->stream>>>(n, hook, root); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_hook");
     SFG_TRY(sfg_pointer_jump(ctx, n, nullptr, root));
     SFG_CUDA(ctx, cudaMemsetAsync(minm, 0x7f, sizeof(int32_t) * n, ctx->stream));
-    k_min_member<<<gn, kBlock, 0, ctx->stream>>>(n, root, minm);
-    k_is_first<<<gn, kBlock, 0, ctx->stream>>>(n, root, minm, first);
+    k_min_member<<<gn, kBlock, 0, ctx->stream>>>(n, root, minm); ++ctx->launches;
+    k_is_first<<<gn, kBlock, 0, ctx->stream>>>(n, root, minm, first); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_min_member");
     SFG_TRY(sfg_scan_u8(ctx, first, rank, n));
-    k_agg_label<<<gn, kBlock, 0, ctx->stream>>>(n, root, minm, rank, agg);
+    k_agg_label<<<gn, kBlock, 0, ctx->stream>>>(n, root, minm, rank, agg); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_agg_label");
     int64_t nc = 0;
     SFG_TRY(sfg_read_i64(ctx, rank + n, &nc));
@@ -151,7 +151,7 @@ sfg_status sfg_coarsen_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, in
     SFG_TRY(aggregate(ctx, L, delta, agg, &nc));
     if (L->m > 0) {
         k_relabel_edges<<<grid_of(ctx, k_relabel_edges, L->m), kBlock, 0, ctx->stream>>>(
-            L->m, L->eu, L->ev, agg, cu, cv);
+            L->m, L->eu, L->ev, agg, cu, cv); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_relabel_edges");
     }
     SFG_TRY(sfg_build_graph(ctx, nc, L->m, cu, cv, L->ew, false, coarse, f2c));
@@ -169,16 +169,16 @@ sfg_status sfg_backward_impl(sfg_ctx* ctx, const sfg_graph* fine, const int32_t*
     SFG_TRY(s.get(&best, coarse->m));
     if (fine->m > 0) {
         k_inner_allow<<<grid_of(ctx, k_inner_allow, fine->m), kBlock, 0, ctx->stream>>>(
-            fine->m, fine->eu, fine->ev, agg, allow);
+            fine->m, fine->eu, fine->ev, agg, allow); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_inner_allow");
     }
     SFG_TRY(sfg_mst_impl(ctx, fine, allow, pmask_f, nullptr));  // inner-cluster trees
     if (coarse->m > 0 && fine->m > 0) {
         SFG_CUDA(ctx, cudaMemsetAsync(best, 0, 8 * coarse->m, ctx->stream));
         k_inter_best<<<grid_of(ctx, k_inter_best, fine->m), kBlock, 0, ctx->stream>>>(
-            fine->m, fine->ew, f2c, pmask_c, best);
+            fine->m, fine->ew, f2c, pmask_c, best); ++ctx->launches;
         k_inter_mark<<<grid_of(ctx, k_inter_mark, coarse->m), kBlock, 0, ctx->stream>>>(
-            coarse->m, best, pmask_f);
+            coarse->m, best, pmask_f); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_inter");
     }
     return SFG_OK;

@@ -254,7 +254,7 @@ sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
     SFG_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
     if (m > 0) {
         k_lap_expand<<<grid_of(ctx, k_lap_expand, m), kBlock, 0, ctx->stream>>>(
-            n, m, u, v, w, bits, sent, keys, vals, err);
+            n, m, u, v, w, bits, sent, keys, vals, err); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_expand");
     }
     if (validate) {
@@ -268,7 +268,7 @@ sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
     SFG_TRY(sfg_radix_sort_pairs(ctx, &keys, &vals, &keys2, &vals2, len, 2 * bits));
     int64_t nnz = 0;
     if (len > 0) {
-        k_lap_heads<<<grid_of(ctx, k_lap_heads, len), kBlock, 0, ctx->stream>>>(keys, len, sent, head);
+        k_lap_heads<<<grid_of(ctx, k_lap_heads, len), kBlock, 0, ctx->stream>>>(keys, len, sent, head); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_heads");
         SFG_TRY(sfg_scan_u8(ctx, head, run_off, len));
         SFG_TRY(sfg_read_i64(ctx, run_off + len, &nnz));
@@ -285,7 +285,7 @@ sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
     int64_t mc = 0;
     if (nnz > 0) {
         k_lap_runs<<<grid_of(ctx, k_lap_runs, len), kBlock, 0, ctx->stream>>>(
-            keys, vals, w, len, head, run_off, bits, row_of_run, colval_tmp, upper);
+            keys, vals, w, len, head, run_off, bits, row_of_run, colval_tmp, upper); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_runs");
         SFG_TRY(sfg_scan_u8(ctx, upper, up_off, nnz));
         SFG_TRY(sfg_read_i64(ctx, up_off + nnz, &mc));
@@ -296,26 +296,26 @@ sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
         SFG_CUDA(ctx, cudaMemcpyAsync(g->colval, colval_tmp, sizeof(int2) * nnz,
                                       cudaMemcpyDeviceToDevice, ctx->stream));
     k_lap_rowptr<<<grid_of(ctx, k_lap_rowptr, nnz + 1), kBlock, 0, ctx->stream>>>(row_of_run, nnz,
-                                                                                   n, g->row_ptr);
+                                                                                   n, g->row_ptr); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_lap_rowptr");
     if (nnz > 0) {
         k_lap_upper<<<grid_of(ctx, k_lap_upper, nnz), kBlock, 0, ctx->stream>>>(
-            g->colval, row_of_run, upper, up_off, nnz, g->eu, g->ev, g->ew, g->eid);
+            g->colval, row_of_run, upper, up_off, nnz, g->eu, g->ev, g->ew, g->eid); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_upper");
         k_lap_lower<<<grid_of(ctx, k_lap_lower, nnz), kBlock, 0, ctx->stream>>>(
-            g->colval, row_of_run, upper, g->row_ptr, nnz, g->eid);
+            g->colval, row_of_run, upper, g->row_ptr, nnz, g->eid); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_lower");
     }
     if (n > 0) {
         k_lap_deg<<<grid_of(ctx, k_lap_deg, n), kBlock, 0, ctx->stream>>>(g->row_ptr, g->colval, n,
-                                                                          g->deg);
+                                                                          g->deg); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_deg");
     }
     if (f2c && m > 0) {
         SFG_CUDA(ctx, cudaMemsetAsync(f2c, 0xff, sizeof(int32_t) * m, ctx->stream));
         if (nnz > 0) {
             k_lap_f2c<<<grid_of(ctx, k_lap_f2c, len), kBlock, 0, ctx->stream>>>(
-                keys, vals, len, sent, run_off, upper, up_off, f2c);
+                keys, vals, len, sent, run_off, upper, up_off, f2c); ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_lap_f2c");
         }
     }
@@ -336,10 +336,10 @@ sfg_status sfg_subgraph_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* ma
     SFG_TRY(s.get(&escan, g->m + 1));
     int64_t ms = 0;
     if (g->m > 0) {
-        k_mask01<<<grid_of(ctx, k_mask01, g->m), kBlock, 0, ctx->stream>>>(mask, g->m, keep_e);
+        k_mask01<<<grid_of(ctx, k_mask01, g->m), kBlock, 0, ctx->stream>>>(mask, g->m, keep_e); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_mask01");
         k_sub_flags<<<grid_of(ctx, k_sub_flags, nnz), kBlock, 0, ctx->stream>>>(g->eid, mask, nnz,
-                                                                                keep);
+                                                                                keep); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_sub_flags");
         SFG_TRY(sfg_scan_u8(ctx, keep_e, escan, g->m));
         SFG_TRY(sfg_scan_u8(ctx, keep, jscan, nnz));
@@ -351,18 +351,18 @@ sfg_status sfg_subgraph_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* ma
     SFG_TRY(alloc_graph(ctx, g->n, ms, &p));
     if (g->m > 0) {
         k_sub_edges<<<grid_of(ctx, k_sub_edges, g->m), kBlock, 0, ctx->stream>>>(
-            g->eu, g->ev, g->ew, keep_e, escan, g->m, p->eu, p->ev, p->ew);
+            g->eu, g->ev, g->ew, keep_e, escan, g->m, p->eu, p->ev, p->ew); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_sub_edges");
         k_sub_csr<<<grid_of(ctx, k_sub_csr, nnz), kBlock, 0, ctx->stream>>>(
-            g->colval, g->eid, keep, jscan, escan, nnz, p->colval, p->eid);
+            g->colval, g->eid, keep, jscan, escan, nnz, p->colval, p->eid); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_sub_csr");
     }
     k_sub_rowptr<<<grid_of(ctx, k_sub_rowptr, (int64_t)g->n + 1), kBlock, 0, ctx->stream>>>(
-        g->row_ptr, jscan, g->n, p->row_ptr);
+        g->row_ptr, jscan, g->n, p->row_ptr); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_sub_rowptr");
     if (g->n > 0) {
         k_lap_deg<<<grid_of(ctx, k_lap_deg, g->n), kBlock, 0, ctx->stream>>>(p->row_ptr, p->colval,
-                                                                             g->n, p->deg);
+                                                                             g->n, p->deg); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_deg");
     }
     *out = p;
@@ -419,7 +419,7 @@ sfg_status sfg_graph_csr(sfg_ctx* ctx, const sfg_graph* g, int32_t* row_ptr, int
         SFG_CUDA(ctx, cudaMemcpyAsync(eid, g->eid, 4 * nnz, cudaMemcpyDeviceToDevice, ctx->stream));
     if (col || val) {
         k_split_colval<<<grid_of(ctx, k_split_colval, nnz), kBlock, 0, ctx->stream>>>(g->colval, nnz,
-                                                                                      col, val);
+                                                                                      col, val); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_split_colval");
     }
     return SFG_OK;

@@ -118,7 +118,7 @@ sfg_status sfg_pointer_jump(sfg_ctx* ctx, int32_t n, const int32_t* comp, int32_
     for (int it = 0; it < 64; ++it) {
         for (int k = 0; k < 4; ++k) {
             if (k == 3) SFG_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-            k_jump_step<<<grid, kBlock, 0, ctx->stream>>>(n, comp, a, b, flag);
+            k_jump_step<<<grid, kBlock, 0, ctx->stream>>>(n, comp, a, b, flag); ++ctx->launches;
             std::swap(a, b);
         }
         SFG_LAUNCH_CHECK(ctx, "k_jump_step");
@@ -140,7 +140,7 @@ sfg_status sfg_count_mask(sfg_ctx* ctx, const uint8_t* mask, int64_t m, int64_t*
     SFG_CUDA(ctx, cudaMemsetAsync(cnt, 0, 8, ctx->stream));
     if (m > 0) {
         k_count_u8<<<sfg_grid(ctx, (const void*)k_count_u8, kBlock, 0, m), kBlock, 0, ctx->stream>>>(
-            m, mask, cnt);
+            m, mask, cnt); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_count_u8");
     }
     return sfg_read_i64(ctx, (const int64_t*)cnt, count_host);
@@ -165,13 +165,13 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
     SFG_TRY(s.get(&flag, 1));
     const int gn = sfg_grid(ctx, (const void*)k_mst_hook, kBlock, 0, n);
     const int gm = sfg_grid(ctx, (const void*)k_mst_edges, kBlock, 0, m);
-    k_mst_init<<<gn, kBlock, 0, ctx->stream>>>(n, comp);
+    k_mst_init<<<gn, kBlock, 0, ctx->stream>>>(n, comp); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_mst_init");
     // each round at least halves the number of components that still have outgoing edges
     for (int round = 0; round < 64; ++round) {
-        k_mst_reset<<<gn, kBlock, 0, ctx->stream>>>(n, best, flag);
-        k_mst_edges<<<gm, kBlock, 0, ctx->stream>>>(m, g->eu, g->ev, g->ew, allow, comp, best);
-        k_mst_hook<<<gn, kBlock, 0, ctx->stream>>>(n, g->eu, g->ev, comp, best, parent, mask, flag);
+        k_mst_reset<<<gn, kBlock, 0, ctx->stream>>>(n, best, flag); ++ctx->launches;
+        k_mst_edges<<<gm, kBlock, 0, ctx->stream>>>(m, g->eu, g->ev, g->ew, allow, comp, best); ++ctx->launches;
+        k_mst_hook<<<gn, kBlock, 0, ctx->stream>>>(n, g->eu, g->ev, comp, best, parent, mask, flag); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_mst_round");
         int hflag = 0;
         SFG_CUDA(ctx, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -180,9 +180,9 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
             if (n_tree) SFG_TRY(sfg_count_mask(ctx, mask, m, n_tree));
             return SFG_OK;
         }
-        k_mst_break<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent);
+        k_mst_break<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent); ++ctx->launches;
         SFG_TRY(sfg_pointer_jump(ctx, n, comp, parent));
-        k_mst_relabel<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent);
+        k_mst_relabel<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_mst_relabel");
     }
     return sfg_fail(ctx, SFG_ETIMEOUT, "spanning forest did not converge in 64 rounds");

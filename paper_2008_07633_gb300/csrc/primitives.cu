@@ -101,7 +101,7 @@ __global__ void k_scan_single(const T* __restrict__ in, int64_t n, int64_t* __re
 template <typename T>
 sfg_status scan_impl(sfg_ctx* ctx, const T* in, int64_t* out, int64_t n) {
     if (n <= kScanTile) {
-        k_scan_single<T><<<1, kScanBlock, 0, ctx->stream>>>(in, n, out);
+        k_scan_single<T><<<1, kScanBlock, 0, ctx->stream>>>(in, n, out); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_scan_single");
         return SFG_OK;
     }
@@ -110,10 +110,10 @@ sfg_status scan_impl(sfg_ctx* ctx, const T* in, int64_t* out, int64_t n) {
     int64_t *sums, *offs;
     SFG_TRY(s.get(&sums, nb));
     SFG_TRY(s.get(&offs, nb + 1));
-    k_scan_reduce<T><<<(unsigned)nb, kScanBlock, 0, ctx->stream>>>(in, n, sums);
+    k_scan_reduce<T><<<(unsigned)nb, kScanBlock, 0, ctx->stream>>>(in, n, sums); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_scan_reduce");
     SFG_TRY(scan_impl<int64_t>(ctx, sums, offs, nb));
-    k_scan_apply<T><<<(unsigned)nb, kScanBlock, 0, ctx->stream>>>(in, n, offs, nb, out);
+    k_scan_apply<T><<<(unsigned)nb, kScanBlock, 0, ctx->stream>>>(in, n, offs, nb, out); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_scan_apply");
     return SFG_OK;
 }
@@ -220,11 +220,11 @@ sfg_status sfg_radix_sort_pairs(sfg_ctx* ctx, uint64_t** keys, uint32_t** vals,
     SFG_TRY(s.get(&counts, (size_t)kRadix * nb));
     SFG_TRY(s.get(&offs, (size_t)kRadix * nb + 1));
     for (int shift = 0; shift < bits; shift += 8) {
-        k_radix_hist<<<(unsigned)nb, kSortBlock, 0, ctx->stream>>>(*keys, n, shift, nb, counts);
+        k_radix_hist<<<(unsigned)nb, kSortBlock, 0, ctx->stream>>>(*keys, n, shift, nb, counts); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_radix_hist");
         SFG_TRY(sfg_scan_i32(ctx, counts, offs, (int64_t)kRadix * nb));
         k_radix_scatter<<<(unsigned)nb, kSortBlock, 0, ctx->stream>>>(*keys, *vals, n, shift, nb,
-                                                                      offs, *keys_alt, *vals_alt);
+                                                                      offs, *keys_alt, *vals_alt); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_radix_scatter");
         std::swap(*keys, *keys_alt);
         std::swap(*vals, *vals_alt);

@@ -95,7 +95,7 @@ sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const
     sfg_tic(ctx, "score");
     k_score<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(ne, ids, LG->eu, LG->ev, LG->ew,
                                                       (const T*)XG, (const T*)XP, mode, 1e-30f,
-                                                      out);
+                                                      out); ++ctx->launches;
     sfg_toc(ctx);
     SFG_LAUNCH_CHECK(ctx, "k_score");
     return SFG_OK;
@@ -131,12 +131,12 @@ sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, i
     double* nn;
     SFG_TRY(s.get(&nn, (size_t)L->n));
     k_rownorm<<<sfg_grid(ctx, (const void*)k_rownorm, kBlock, 0, L->n), kBlock, 0, ctx->stream>>>(
-        L->n, X, K, nn);
+        L->n, X, K, nn); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_rownorm");
     if (L->m > 0) {
         sfg_tic(ctx, "affinity");
         k_affinity<<<sfg_grid(ctx, (const void*)k_affinity, kBlock, 0, L->m), kBlock, 0,
-                     ctx->stream>>>(L->m, L->eu, L->ev, X, K, nn, delta);
+                     ctx->stream>>>(L->m, L->eu, L->ev, X, K, nn, delta); ++ctx->launches;
         sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_affinity");
     }

@@ -109,20 +109,20 @@ sfg_status sfg_topk_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids, 
     SFG_TRY(s.get(&vb, k));
     const int grid = sfg_grid(ctx, (const void*)k_sel_hist, kBlock, 0, ne);
     sfg_tic(ctx, "topk");
-    k_sel_init<<<1, kBlock, 0, ctx->stream>>>(st, k);
+    k_sel_init<<<1, kBlock, 0, ctx->stream>>>(st, k); ++ctx->launches;
     for (int shift = 56; shift >= 0; shift -= 8) {
-        k_sel_hist<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, shift, st);
-        k_sel_pick<<<1, kBlock, 0, ctx->stream>>>(shift, st);
+        k_sel_hist<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, shift, st); ++ctx->launches;
+        k_sel_pick<<<1, kBlock, 0, ctx->stream>>>(shift, st); ++ctx->launches;
     }
-    k_sel_flags<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, st, flag);
+    k_sel_flags<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, st, flag); ++ctx->launches;
     sfg_toc(ctx);
     SFG_LAUNCH_CHECK(ctx, "k_sel");
     SFG_TRY(sfg_scan_u8(ctx, flag, pos, ne));
-    k_sel_compact<<<grid, kBlock, 0, ctx->stream>>>(ne, ids, flag, pos, ka, va);
+    k_sel_compact<<<grid, kBlock, 0, ctx->stream>>>(ne, ids, flag, pos, ka, va); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_sel_compact");
     SFG_TRY(sfg_radix_sort_pairs(ctx, &ka, &va, &kb, &vb, k, 32));
     k_sel_emit<<<sfg_grid(ctx, (const void*)k_sel_emit, kBlock, 0, k), kBlock, 0, ctx->stream>>>(
-        k, ka, out);
+        k, ka, out); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_sel_emit");
     return SFG_OK;
 }

@@ -27,6 +27,7 @@ struct sfg_ctx {
     bool timing = false;
     std::vector<sfg_timer_rec> timers;     // recorded this session
     std::vector<cudaEvent_t> event_pool;   // free events
+    int64_t launches = 0;                  // kernels launched through this context
     int64_t alloc_count = 0;               // for the allocation-failure injection hook
     int64_t fail_alloc_at = -1;            // SFG_FAULT_ALLOC=<n>: the n-th allocation fails
 };

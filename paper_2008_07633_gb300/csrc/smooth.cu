@@ -19,15 +19,22 @@
 namespace {
 
 constexpr int kBlock = 256;
+#ifndef SFG_JACOBI_MIN_BLOCKS
+#define SFG_JACOBI_MIN_BLOCKS 3  // resident CTAs per SM requested from the compiler (caps registers at 80)
+#endif
 
-// Gaussian draw j of the counter-based generator (see sfg.h): splitmix64 uniforms formed exactly
-// in FP64, Box-Muller evaluated in FP32 (logf, cospif).
-__device__ __forceinline__ float gaussian_draw(uint64_t seed, uint64_t j) {
-    const uint64_t a = sfg_splitmix64(seed ^ sfg_splitmix64(2 * j));
-    const uint64_t b = sfg_splitmix64(seed ^ sfg_splitmix64(2 * j + 1));
-    const float u1 = (float)((double)((a >> 11) + 1) * 0x1.0p-53);
-    const float u2 = (float)((double)(b >> 11) * 0x1.0p-53);
-    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+// Gaussian entries 2p and 2p+1 of the counter-based generator (see sfg.h): SplitMix64 output
+// p + 1 of the stream started in state splitmix64(seed), both Box-Muller branches in FP32 (logf,
+// sincospif). The 24-bit angle uniform is exact in FP32.
+__device__ __forceinline__ void gaussian_pair(uint64_t s0, uint64_t p, float& x0, float& x1) {
+    const uint64_t o = sfg_splitmix64(s0 + p * 0x9E3779B97F4A7C15ull);
+    const float u1 = __ull2float_rn((o >> 32) + 1) * 0x1.0p-32f;
+    const float u2 = (float)(uint32_t)((o >> 8) & 0xffffffu) * 0x1.0p-24f;
+    const float r = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    x0 = r * cs;
+    x1 = r * sn;
 }
 
 template <int LPR>
@@ -77,12 +84,17 @@ __global__ void __launch_bounds__(kBlock) k_init(int32_t n, uint64_t seed, T* __
     float s1[E], s2[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) s1[e] = s2[e] = 0.f;
+    const uint64_t s0 = sfg_splitmix64(seed);
     for (int64_t row = g0; row < n; row += ng) {
         float x[E];
 #pragma unroll
+        for (int e = 0; e < E; e += 2) {
+            const uint64_t j = (uint64_t)row * K + sub * E + e;  // even
+            gaussian_pair(s0, j >> 1, x[e], x[e + 1]);
+        }
+#pragma unroll
         for (int e = 0; e < E; ++e) {
-            const uint64_t j = (uint64_t)row * K + sub * E + e;
-            x[e] = Vec<T>::round(gaussian_draw(seed, j));
+            x[e] = Vec<T>::round(x[e]);
             s1[e] += x[e];
             s2[e] = fmaf(x[e], x[e], s2[e]);
         }
@@ -91,67 +103,146 @@ __global__ void __launch_bounds__(kBlock) k_init(int32_t n, uint64_t seed, T* __
     block_column_partials<LPR, E>(s1, s2, part);
 }
 
+// A chunk of C = max(LPR, 8) consecutive (column, weight) entries of one row, spread over the
+// LPR lanes of the row's group (C / LPR per lane). Slots past the row's end hold (row, 0): they
+// gather the row itself with weight zero, so the gather loop needs no per-slot predicate.
+template <int LPR>
+struct Chunk {
+    static constexpr int C = LPR >= 8 ? LPR : 8, PER = C / LPR;
+    int2 cv[PER];
+    __device__ __forceinline__ void load(const int2* __restrict__ colval, int32_t j0, int32_t b,
+                                         int32_t self, int sub) {
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int32_t j = j0 + sub + t * LPR;
+            cv[t] = j < b ? colval[j] : make_int2(self, 0);
+        }
+    }
+};
+
+// acc += sum over slots [0, NS) of w * X[col] for this lane's E columns; all NS gathers are issued
+// before the first is consumed. The shuffle source of every slot is a compile-time constant.
+template <typename T, int LPR, int NS>
+__device__ __forceinline__ void gather_slots(const Chunk<LPR>& ch, int s0, unsigned gm,
+                                             const T* __restrict__ Xl, float (&acc)[Vec<T>::E]) {
+    constexpr int K = LPR * Vec<T>::E;
+    uint4 xv[NS];
+    float wv[NS];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+        const int slot = s0 + u;  // s0 is a multiple of NS; slot < C
+        const int c = __shfl_sync(gm, ch.cv[slot / LPR].x, slot % LPR, LPR);
+        wv[u] = __int_as_float(__shfl_sync(gm, ch.cv[slot / LPR].y, slot % LPR, LPR));
+        xv[u] = Vec<T>::load_raw(Xl + (int64_t)c * K);
+    }
+#pragma unroll
+    for (int u = 0; u < NS; ++u) Vec<T>::fma_raw(wv[u], xv[u], acc);
+}
+
+// One weighted-Jacobi sweep. A warp owns a tile of GPW = 32 / LPR consecutive rows (one LPR-lane
+// group per row) and moves by grid stride over tiles. The tile's row_ptr and D^-1 entries come
+// from one coalesced load per lane and are handed out by shuffles; each group holds its row's
+// first chunk of (column, weight) entries. The next tile's metadata and chunks are loaded before
+// this tile's gathers are consumed, so one gather round is the only exposed latency per tile.
+// Gathers go in warp-uniform batches of 8 or 4 slots sized by the tile's longest row.
 template <typename T, int LPR, bool SUB_MU, bool STATS>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
     k_jacobi(int32_t n, const int32_t* __restrict__ row_ptr, const int2* __restrict__ colval,
              const float* __restrict__ coef, float a_self, const T* __restrict__ X,
              T* __restrict__ Y, const float* __restrict__ mu, double* __restrict__ part) {
-    constexpr int E = Vec<T>::E, K = LPR * E;
-    const int lane = threadIdx.x & 31, sub = lane % LPR;
+    constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR, C = Chunk<LPR>::C;
+    const int lane = threadIdx.x & 31, grp = lane / LPR, sub = lane % LPR;
     const unsigned gm = group_mask<LPR>(lane);
-    const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
-    const int64_t ng = (int64_t)gridDim.x * kBlock / LPR;
+    const int32_t wid = (int32_t)((blockIdx.x * kBlock + threadIdx.x) >> 5);
+    const int32_t nw = (int32_t)(gridDim.x * (kBlock / 32));
+    const int32_t ntiles = (n + GPW - 1) / GPW;
+    const T* __restrict__ Xl = X + sub * E;
+
     float m[E], s1[E], s2[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         m[e] = SUB_MU ? mu[sub * E + e] : 0.f;
         s1[e] = s2[e] = 0.f;
     }
-    for (int64_t row = g0; row < n; row += ng) {
-        const int32_t a = row_ptr[row], b = row_ptr[row + 1];
-        float acc[E];
+    // Metadata of tile t, one value per lane: lo = row_ptr[r0 + lane], hi = row_ptr[r0 + lane + 1]
+    // (both clamped at n), cf = D^-1 of row r0 + lane.
+    struct Meta { int32_t lo, hi; float cf; };
+    auto load_meta = [&](int32_t t) {
+        Meta mt{0, 0, 0.f};
+        const int32_t r = t * GPW + lane;
+        if (t < ntiles && lane <= GPW) mt.lo = row_ptr[min(r, n)];
+        if (GPW == 32 && t < ntiles) mt.hi = row_ptr[min(r + 1, n)];
+        if (t < ntiles && lane < GPW && r < n) mt.cf = coef[r];
+        return mt;
+    };
+    // This group's row bounds within a tile.
+    auto bounds = [&](const Meta& mt, int32_t& a, int32_t& b) {
+        a = __shfl_sync(0xffffffffu, mt.lo, grp);
+        b = GPW == 32 ? mt.hi : __shfl_sync(0xffffffffu, mt.lo, grp + 1);
+    };
+
+    int32_t t = wid;
+    Meta mt = load_meta(t);
+    int32_t a, b;
+    bounds(mt, a, b);
+    int32_t r = t * GPW + grp;
+    Chunk<LPR> ch;
+    ch.load(colval, a, b, r < n ? r : 0, sub);
+    Meta mtn = load_meta(t + nw);
+    for (; t < ntiles; t += nw) {
+        // prefetch: the next tile's first chunks and the metadata of the tile after it
+        int32_t an, bn;
+        bounds(mtn, an, bn);
+        const int32_t rn = (t + nw) * GPW + grp;
+        Chunk<LPR> chn;
+        chn.load(colval, an, bn, rn < n ? rn : 0, sub);
+        const Meta mtnn = load_meta(t + 2 * nw);
+
+        const bool live = r < n;
+        const int32_t self = live ? r : 0;
+        const float cp = __shfl_sync(0xffffffffu, mt.cf, grp);
+        float xs[E], acc[E];
+        Vec<T>::load(Xl + (int64_t)self * K, xs);
 #pragma unroll
         for (int e = 0; e < E; ++e) acc[e] = 0.f;
-        for (int32_t j0 = a; j0 < b; j0 += LPR) {
-            const int32_t j = j0 + sub;
-            const int2 cv = j < b ? colval[j] : make_int2(0, 0);
-            const int cnt = min(LPR, b - j0);
-            float xv[LPR][E];
-            float wv[LPR];
+        const int32_t deg = b - a;
+        const int32_t maxdeg = __reduce_max_sync(0xffffffffu, deg);
+        if (maxdeg > 4 || C > 8) {
 #pragma unroll
-            for (int t = 0; t < LPR; ++t) {
-                if (t < cnt) {
-                    const int c = __shfl_sync(gm, cv.x, t, LPR);
-                    wv[t] = __int_as_float(__shfl_sync(gm, cv.y, t, LPR));
-                    Vec<T>::load(X + (int64_t)c * K + sub * E, xv[t]);
+            for (int s0 = 0; s0 < C; s0 += 8) gather_slots<T, LPR, 8>(ch, s0, gm, Xl, acc);
+        } else if (maxdeg > 0) {
+            gather_slots<T, LPR, 4>(ch, 0, gm, Xl, acc);
+        }
+        for (int32_t j0 = a + C; __any_sync(0xffffffffu, j0 < b); j0 += C) {  // long rows
+            Chunk<LPR> cx;
+            cx.load(colval, j0, b, self, sub);
+#pragma unroll
+            for (int s0 = 0; s0 < C; s0 += 8) gather_slots<T, LPR, 8>(cx, s0, gm, Xl, acc);
+        }
+        if (live) {
+            float y[E];
+            if (deg > 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) y[e] = fmaf(cp, acc[e], a_self * xs[e]) - m[e];
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) y[e] = xs[e] - m[e];
+            }
+            Vec<T>::store(Y + (int64_t)r * K + sub * E, y);
+            if (STATS)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const float q = Vec<T>::round(y[e]);
+                    s1[e] += q;
+                    s2[e] = fmaf(q, q, s2[e]);
                 }
-            }
-#pragma unroll
-            for (int t = 0; t < LPR; ++t)
-                if (t < cnt)
-#pragma unroll
-                    for (int e = 0; e < E; ++e) acc[e] = fmaf(wv[t], xv[t][e], acc[e]);
         }
-        float xs[E], y[E];
-        Vec<T>::load(X + row * K + sub * E, xs);
-        if (b > a) {
-            const float cp = coef[row];
-#pragma unroll
-            for (int e = 0; e < E; ++e) y[e] = fmaf(cp, acc[e], a_self * xs[e]);
-        } else {
-#pragma unroll
-            for (int e = 0; e < E; ++e) y[e] = xs[e];
-        }
-#pragma unroll
-        for (int e = 0; e < E; ++e) y[e] -= m[e];
-        Vec<T>::store(Y + row * K + sub * E, y);
-        if (STATS)
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const float r = Vec<T>::round(y[e]);
-                s1[e] += r;
-                s2[e] = fmaf(r, r, s2[e]);
-            }
+        ch = chn;
+        mt = mtn;
+        mtn = mtnn;
+        a = an;
+        b = bn;
+        r = rn;
     }
     if (STATS) block_column_partials<LPR, E>(s1, s2, part);
 }
@@ -207,7 +298,7 @@ struct Smoother {
     static constexpr int E = Vec<T>::E, K = LPR * E;
 
     static int grid_jacobi(sfg_ctx* ctx, int32_t n) {
-        return sfg_grid(ctx, (const void*)k_jacobi<T, LPR, false, true>, kBlock, 0,
+        return sfg_grid(ctx, (const void*)k_jacobi<T, LPR, false, false>, kBlock, 0,
                         (int64_t)n * LPR);
     }
 
@@ -216,6 +307,7 @@ struct Smoother {
                             bool stats, int grid) {
         const int32_t n = L->n;
         sfg_tic(ctx, "jacobi");
+        ++ctx->launches;
         if (sub_mu && stats)
             k_jacobi<T, LPR, true, true><<<grid, kBlock, 0, ctx->stream>>>(
                 n, L->row_ptr, L->colval, coef, a_self, X, Y, mu, part);
@@ -247,16 +339,16 @@ struct Smoother {
         SFG_TRY(s.get(&scale, K));
         SFG_TRY(s.get(&part, (size_t)grid * 2 * K));
         k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
-            n, L->deg, omega, coef);
+            n, L->deg, omega, coef); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_coef");
         // ping-pong so that the last sweep writes `buf` and the projection writes X_out
         T* cur = (steps % 2 == 0) ? buf : X_out;
         T* nxt = (cur == buf) ? X_out : buf;
         sfg_tic(ctx, "init");
-        k_init<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, seed, cur, part);
+        k_init<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, seed, cur, part); ++ctx->launches;
         sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_init");
-        k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 0, mu, scale);
+        k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 0, mu, scale); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_finalize");
         for (int t = 1; t <= steps; ++t) {
             SFG_TRY(sweep(ctx, L, coef, (float)(1.0 - omega), cur, nxt, mu, part, t == 1,
@@ -264,13 +356,13 @@ struct Smoother {
             std::swap(cur, nxt);
         }
         if (steps > 0) {
-            k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, 1, mu, scale);
+            k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, 1, mu, scale); ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_finalize");
         }
         sfg_tic(ctx, "project");
         k_project<T, LPR><<<sfg_grid(ctx, (const void*)k_project<T, LPR>, kBlock, 0,
                                      (int64_t)n * LPR),
-                            kBlock, 0, ctx->stream>>>(n, cur, X_out, mu, scale);
+                            kBlock, 0, ctx->stream>>>(n, cur, X_out, mu, scale); ++ctx->launches;
         sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_project");
         return SFG_OK;
@@ -285,7 +377,7 @@ struct Smoother {
         SFG_TRY(s.get(&buf, (size_t)n * K));
         SFG_TRY(s.get(&coef, (size_t)n));
         k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
-            n, L->deg, omega, coef);
+            n, L->deg, omega, coef); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_coef");
         T* cur = X;
         T* nxt = buf;

@@ -71,10 +71,10 @@ sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64
     SFG_TRY(s.get(&scores, ncand));
     SFG_TRY(s.get(&sel, k));
     const int gm = sfg_grid(ctx, (const void*)k_not_mask, kBlock, 0, m);
-    k_not_mask<<<gm, kBlock, 0, ctx->stream>>>(m, mask, flag);
+    k_not_mask<<<gm, kBlock, 0, ctx->stream>>>(m, mask, flag); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_not_mask");
     SFG_TRY(sfg_scan_u8(ctx, flag, pos, m));
-    k_compact_ids<<<gm, kBlock, 0, ctx->stream>>>(m, flag, pos, cand);
+    k_compact_ids<<<gm, kBlock, 0, ctx->stream>>>(m, flag, pos, cand); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_compact_ids");
 
     sfg_graph* pg = nullptr;
@@ -91,7 +91,7 @@ sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64
         if (XG_f32) {
             const int64_t cnt = (int64_t)g->n * P->K;
             k_f32_to_bf16<<<sfg_grid(ctx, (const void*)k_f32_to_bf16, kBlock, 0, cnt), kBlock, 0,
-                            ctx->stream>>>(cnt, XG_f32, (__nv_bfloat16*)x);
+                            ctx->stream>>>(cnt, XG_f32, (__nv_bfloat16*)x); ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_f32_to_bf16");
         } else {
             SFG_TRY(sfg_smooth_impl(ctx, g, P->K, P->steps, P->omega, seed, P->storage, x));
@@ -102,7 +102,7 @@ sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64
     SFG_TRY(sfg_score_impl(ctx, g, xg, xp, P->K, P->storage, cand, ncand, P->mode, scores));
     SFG_TRY(sfg_topk_impl(ctx, scores, cand, ncand, k, sel));
     k_set_mask<<<sfg_grid(ctx, (const void*)k_set_mask, kBlock, 0, k), kBlock, 0, ctx->stream>>>(
-        k, sel, mask);
+        k, sel, mask); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_set_mask");
     return SFG_OK;
 }

@@ -18,6 +18,16 @@ struct Vec<float> {
     }
     // value as stored (identity for FP32)
     __device__ __forceinline__ static float round(float x) { return x; }
+    // raw 16-byte load and a multiply-add of its widened entries
+    __device__ __forceinline__ static uint4 load_raw(const float* p) {
+        return *reinterpret_cast<const uint4*>(p);
+    }
+    __device__ __forceinline__ static void fma_raw(float w, uint4 r, float (&acc)[4]) {
+        acc[0] = fmaf(w, __uint_as_float(r.x), acc[0]);
+        acc[1] = fmaf(w, __uint_as_float(r.y), acc[1]);
+        acc[2] = fmaf(w, __uint_as_float(r.z), acc[2]);
+        acc[3] = fmaf(w, __uint_as_float(r.w), acc[3]);
+    }
 };
 
 template <>
@@ -44,5 +54,16 @@ struct Vec<__nv_bfloat16> {
     }
     __device__ __forceinline__ static float round(float x) {
         return __bfloat162float(__float2bfloat16_rn(x));
+    }
+    __device__ __forceinline__ static uint4 load_raw(const __nv_bfloat16* p) {
+        return *reinterpret_cast<const uint4*>(p);
+    }
+    __device__ __forceinline__ static void fma_raw(float w, uint4 r, float (&acc)[8]) {
+        const unsigned q[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            acc[2 * i] = fmaf(w, __uint_as_float(q[i] << 16), acc[2 * i]);
+            acc[2 * i + 1] = fmaf(w, __uint_as_float(q[i] & 0xffff0000u), acc[2 * i + 1]);
+        }
     }
 };

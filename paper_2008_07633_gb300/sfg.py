@@ -12,7 +12,7 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsfg.so")
+LIB_PATH = os.environ.get("SFG_LIB", os.path.join(_HERE, "libsfg.so"))
 
 SFG_F32, SFG_BF16 = 0, 1
 SFG_SCORE_RATIO, SFG_SCORE_G, SFG_SCORE_P = 0, 1, 2
@@ -21,7 +21,7 @@ STATUS = {0: "SFG_OK", 1: "SFG_EINVAL", 2: "SFG_ENOMEM", 3: "SFG_ECUDA", 4: "SFG
 
 # Every symbol declared in include/sfg.h.
 EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_error",
-           "sfg_ctx_timing", "sfg_ctx_kernel_time", "sfg_laplacian", "sfg_graph_destroy",
+           "sfg_ctx_timing", "sfg_ctx_kernel_time", "sfg_ctx_launches", "sfg_laplacian", "sfg_graph_destroy",
            "sfg_graph_info", "sfg_graph_edges", "sfg_graph_csr", "sfg_graph_subgraph", "sfg_smooth",
            "sfg_jacobi", "sfg_score_edges", "sfg_select_topk", "sfg_spanning_tree", "sfg_affinity",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify"]
@@ -60,6 +60,7 @@ def lib():
             "sfg_last_error": [_vp],
             "sfg_ctx_timing": [_vp, _int],
             "sfg_ctx_kernel_time": [_vp, ctypes.c_char_p, _pi64, _pdbl],
+            "sfg_ctx_launches": [_vp, _pi64],
             "sfg_laplacian": [_vp, _i32, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp)],
             "sfg_graph_destroy": [_vp],
             "sfg_graph_info": [_vp, _pi32, _pi64],
@@ -172,6 +173,12 @@ def sfg_ctx_kernel_time(ctx, prefix):
     n, ms = _i64(), _dbl()
     ctx.check(lib().sfg_ctx_kernel_time(ctx.h, prefix.encode(), ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def sfg_ctx_launches(ctx):
+    n = _i64()
+    ctx.check(lib().sfg_ctx_launches(ctx.h, ctypes.byref(n)))
+    return n.value
 
 
 def sfg_laplacian(ctx, n, u, v, w) -> Graph:
