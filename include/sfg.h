@@ -169,6 +169,22 @@ SFG_API sfg_status sfg_spanning_tree(sfg_ctx* ctx, const sfg_graph* g, const uin
 SFG_API sfg_status sfg_affinity(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
                         double* delta_out);
 
+/* Allocation-free sfg_affinity. The paper has no counterpart: this entry point exists for callers
+ * that cannot let a library allocate device memory (applications that give all device memory to
+ * their own pool, runtimes that must keep the device footprint fixed after start-up, code running
+ * where cudaMalloc / cudaMallocAsync are not permitted). Same arguments and the same bit-exact
+ * result as sfg_affinity, but its scratch (one FP64 row norm per node) is a fixed file-scope
+ * device array of SFG_AFFINITY_NOALLOC_MAX_N entries (8 MiB) that every GPU loading the library
+ * keeps until the process exits; the call itself allocates nothing.
+ *  - n > SFG_AFFINITY_NOALLOC_MAX_N gives SFG_ECAPACITY (use sfg_affinity).
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call on a device shares the one array: calls whose work overlaps on the GPU (several
+ *    streams or contexts at once) race on it. Serialise them, e.g. on one stream. */
+#define SFG_AFFINITY_NOALLOC_MAX_N (1 << 20)
+SFG_API sfg_status sfg_affinity_noalloc(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
+                                        double* delta_out);
+
 /* One coarsening level from an FP32 block X (n x K): affinities as sfg_affinity; each node hooks
  * to the neighbour with the smallest delta (ties: smaller id); aggregation sets S_i are the
  * connected components of the hooks, numbered by increasing smallest member (agg_out[p] = i for

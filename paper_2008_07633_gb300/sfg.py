@@ -24,6 +24,7 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_
            "sfg_ctx_timing", "sfg_ctx_kernel_time", "sfg_ctx_launches", "sfg_laplacian", "sfg_graph_destroy",
            "sfg_graph_info", "sfg_graph_edges", "sfg_graph_csr", "sfg_graph_subgraph", "sfg_smooth",
            "sfg_jacobi", "sfg_score_edges", "sfg_select_topk", "sfg_spanning_tree", "sfg_affinity",
+           "sfg_affinity_noalloc",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify"]
 
 
@@ -73,6 +74,7 @@ def lib():
             "sfg_select_topk": [_vp, _vp, _vp, _i64, _i64, _vp],
             "sfg_spanning_tree": [_vp, _vp, _vp, _vp, _pi64],
             "sfg_affinity": [_vp, _vp, _vp, _int, _vp],
+            "sfg_affinity_noalloc": [_vp, _vp, _vp, _int, _vp],
             "sfg_coarsen": [_vp, _vp, _vp, _int, _vp, _vp, _pi32, ctypes.POINTER(_vp)],
             "sfg_backward_map": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
             "sfg_sparsify": [_vp, _vp, ctypes.POINTER(sfg_params), _vp, _pi64],
@@ -266,6 +268,15 @@ def sfg_affinity(ctx, g, X):
     d = torch.empty(g.m, dtype=torch.float64, device=ctx.device)
     ctx.check(lib().sfg_affinity(ctx.h, g.h, _ptr(X), X.shape[1], _ptr(d)))
     return d
+
+
+def sfg_affinity_noalloc(ctx, g, X, out=None):
+    """sfg_affinity without any device allocation inside the library (see include/sfg.h)."""
+    assert X.dtype == torch.float32 and X.is_contiguous()
+    if out is None:
+        out = torch.empty(g.m, dtype=torch.float64, device=ctx.device)
+    ctx.check(lib().sfg_affinity_noalloc(ctx.h, g.h, _ptr(X), X.shape[1], _ptr(out)))
+    return out
 
 
 def sfg_coarsen(ctx, g, X):
