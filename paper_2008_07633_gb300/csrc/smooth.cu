@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kBlock = 256;
 #ifndef SFG_JACOBI_MIN_BLOCKS
-#define SFG_JACOBI_MIN_BLOCKS 3  // resident CTAs per SM requested from the compiler (caps registers at 80)
+#define SFG_JACOBI_MIN_BLOCKS 4  // resident CTAs per SM requested from the compiler (caps registers at 64)
 #endif
 
 // Gaussian entries 2p and 2p+1 of the counter-based generator (see sfg.h): SplitMix64 output
@@ -120,31 +120,55 @@ struct Chunk {
     }
 };
 
-// acc += sum over slots [0, NS) of w * X[col] for this lane's E columns; all NS gathers are issued
-// before the first is consumed. The shuffle source of every slot is a compile-time constant.
+// acc += sum over slots [s0, s0 + NS) (slots past the chunk ignored at compile time) of
+// w * X[col] for this lane's E columns. All NS gathers are issued before the first is consumed;
+// the weights are taken from the chunk at use time, so only the gathered vectors stay live.
 template <typename T, int LPR, int NS>
 __device__ __forceinline__ void gather_slots(const Chunk<LPR>& ch, int s0, unsigned gm,
                                              const T* __restrict__ Xl, float (&acc)[Vec<T>::E]) {
-    constexpr int K = LPR * Vec<T>::E;
+    constexpr int K = LPR * Vec<T>::E, C = Chunk<LPR>::C;
     uint4 xv[NS];
-    float wv[NS];
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
-        const int slot = s0 + u;  // s0 is a multiple of NS; slot < C
-        const int c = __shfl_sync(gm, ch.cv[slot / LPR].x, slot % LPR, LPR);
-        wv[u] = __int_as_float(__shfl_sync(gm, ch.cv[slot / LPR].y, slot % LPR, LPR));
-        xv[u] = Vec<T>::load_raw(Xl + (int64_t)c * K);
+        const int slot = s0 + u;
+        if (slot < C) {
+            const int c = __shfl_sync(gm, ch.cv[slot / LPR].x, slot % LPR, LPR);
+            xv[u] = Vec<T>::load_raw(Xl + (int64_t)c * K);
+        }
     }
 #pragma unroll
-    for (int u = 0; u < NS; ++u) Vec<T>::fma_raw(wv[u], xv[u], acc);
+    for (int u = 0; u < NS; ++u) {
+        const int slot = s0 + u;
+        if (slot < C) {
+            const float w = __int_as_float(__shfl_sync(gm, ch.cv[slot / LPR].y, slot % LPR, LPR));
+            Vec<T>::fma_raw(w, xv[u], acc);
+        }
+    }
+}
+
+// All slots of a chunk that the tile's longest row needs: warp-uniform batches of 2, 4 or 6.
+template <typename T, int LPR>
+__device__ __forceinline__ void gather_chunk(const Chunk<LPR>& ch, int need, unsigned gm,
+                                             const T* __restrict__ Xl, float (&acc)[Vec<T>::E]) {
+    constexpr int C = Chunk<LPR>::C;
+    if (need <= 2) {
+        if (need > 0) gather_slots<T, LPR, 2>(ch, 0, gm, Xl, acc);
+    } else if (need <= 4) {
+        gather_slots<T, LPR, 4>(ch, 0, gm, Xl, acc);
+    } else {
+#pragma unroll
+        for (int s0 = 0; s0 < C; s0 += 6)
+            if (s0 < need) gather_slots<T, LPR, 6>(ch, s0, gm, Xl, acc);
+    }
 }
 
 // One weighted-Jacobi sweep. A warp owns a tile of GPW = 32 / LPR consecutive rows (one LPR-lane
-// group per row) and moves by grid stride over tiles. The tile's row_ptr and D^-1 entries come
-// from one coalesced load per lane and are handed out by shuffles; each group holds its row's
-// first chunk of (column, weight) entries. The next tile's metadata and chunks are loaded before
-// this tile's gathers are consumed, so one gather round is the only exposed latency per tile.
-// Gathers go in warp-uniform batches of 8 or 4 slots sized by the tile's longest row.
+// group per row) and moves by grid stride over tiles, so all CTAs sweep one moving window of rows
+// and the neighbour rows of the window stay in L2. The tile's row_ptr and D^-1 entries come from
+// one coalesced load per lane and are handed out by shuffles; each group holds its row's first
+// chunk of (column, weight) entries. The next tile's metadata is loaded before this tile's
+// gathers are issued and its chunks right after, so one gather round is the only exposed latency
+// per tile. Gathers go in warp-uniform batches sized by the tile's longest row.
 template <typename T, int LPR, bool SUB_MU, bool STATS>
 __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
     k_jacobi(int32_t n, const int32_t* __restrict__ row_ptr, const int2* __restrict__ colval,
@@ -165,7 +189,7 @@ __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
         s1[e] = s2[e] = 0.f;
     }
     // Metadata of tile t, one value per lane: lo = row_ptr[r0 + lane], hi = row_ptr[r0 + lane + 1]
-    // (both clamped at n), cf = D^-1 of row r0 + lane.
+    // (both clamped at n; hi only when GPW = 32), cf = D^-1 of row r0 + lane.
     struct Meta { int32_t lo, hi; float cf; };
     auto load_meta = [&](int32_t t) {
         Meta mt{0, 0, 0.f};
@@ -175,50 +199,39 @@ __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
         if (t < ntiles && lane < GPW && r < n) mt.cf = coef[r];
         return mt;
     };
-    // This group's row bounds within a tile.
-    auto bounds = [&](const Meta& mt, int32_t& a, int32_t& b) {
-        a = __shfl_sync(0xffffffffu, mt.lo, grp);
-        b = GPW == 32 ? mt.hi : __shfl_sync(0xffffffffu, mt.lo, grp + 1);
-    };
 
     int32_t t = wid;
     Meta mt = load_meta(t);
-    int32_t a, b;
-    bounds(mt, a, b);
+    int32_t a = __shfl_sync(0xffffffffu, mt.lo, grp);
+    int32_t b = GPW == 32 ? mt.hi : __shfl_sync(0xffffffffu, mt.lo, grp + 1);
     int32_t r = t * GPW + grp;
     Chunk<LPR> ch;
     ch.load(colval, a, b, r < n ? r : 0, sub);
-    Meta mtn = load_meta(t + nw);
     for (; t < ntiles; t += nw) {
-        // prefetch: the next tile's first chunks and the metadata of the tile after it
-        int32_t an, bn;
-        bounds(mtn, an, bn);
-        const int32_t rn = (t + nw) * GPW + grp;
-        Chunk<LPR> chn;
-        chn.load(colval, an, bn, rn < n ? rn : 0, sub);
-        const Meta mtnn = load_meta(t + 2 * nw);
+        const Meta mtn = load_meta(t + nw);  // next tile's metadata, in flight with the gathers
 
         const bool live = r < n;
         const int32_t self = live ? r : 0;
         const float cp = __shfl_sync(0xffffffffu, mt.cf, grp);
+        const int32_t deg = b - a;
+        const int32_t maxdeg = __reduce_max_sync(0xffffffffu, deg);
         float xs[E], acc[E];
         Vec<T>::load(Xl + (int64_t)self * K, xs);
 #pragma unroll
         for (int e = 0; e < E; ++e) acc[e] = 0.f;
-        const int32_t deg = b - a;
-        const int32_t maxdeg = __reduce_max_sync(0xffffffffu, deg);
-        if (maxdeg > 4 || C > 8) {
-#pragma unroll
-            for (int s0 = 0; s0 < C; s0 += 8) gather_slots<T, LPR, 8>(ch, s0, gm, Xl, acc);
-        } else if (maxdeg > 0) {
-            gather_slots<T, LPR, 4>(ch, 0, gm, Xl, acc);
-        }
-        for (int32_t j0 = a + C; __any_sync(0xffffffffu, j0 < b); j0 += C) {  // long rows
+        gather_chunk<T, LPR>(ch, min(maxdeg, C), gm, Xl, acc);
+        for (int32_t j0 = C; j0 < maxdeg; j0 += C) {  // rows longer than one chunk
             Chunk<LPR> cx;
-            cx.load(colval, j0, b, self, sub);
-#pragma unroll
-            for (int s0 = 0; s0 < C; s0 += 8) gather_slots<T, LPR, 8>(cx, s0, gm, Xl, acc);
+            cx.load(colval, a + j0, b, self, sub);
+            gather_chunk<T, LPR>(cx, min(maxdeg - j0, C), gm, Xl, acc);
         }
+
+        // next tile: row bounds and first chunk (its metadata has had the gather round to arrive)
+        const int32_t an = __shfl_sync(0xffffffffu, mtn.lo, grp);
+        const int32_t bn = GPW == 32 ? mtn.hi : __shfl_sync(0xffffffffu, mtn.lo, grp + 1);
+        const int32_t rn = (t + nw) * GPW + grp;
+        ch.load(colval, an, bn, rn < n ? rn : 0, sub);
+
         if (live) {
             float y[E];
             if (deg > 0) {
@@ -237,9 +250,7 @@ __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
                     s2[e] = fmaf(q, q, s2[e]);
                 }
         }
-        ch = chn;
         mt = mtn;
-        mtn = mtnn;
         a = an;
         b = bn;
         r = rn;
