@@ -144,6 +144,18 @@ SFG_API sfg_status sfg_score_edges(sfg_ctx* ctx, const sfg_graph* LG, const void
                            int K, sfg_dtype storage, const int32_t* edge_ids, int64_t ne,
                            sfg_score_mode mode, float* scores_out);
 
+/* The filter + score step of edge recovery (Sec. 3.5 with Sec. 3.2's embedding; Algorithm 1
+ * lines 12-13) in one call: one seeded block (sfg_smooth step 1) is swept `steps` times on L_G
+ * and on L_P (same node count), and the listed edges of LG are scored as sfg_score_edges would
+ * score the two projected blocks. The projected blocks are not materialised: the projection's
+ * mean removal cancels in X_p - X_q and its per-column scaling is applied inside the scorer, so
+ * the scores equal sfg_smooth x 2 + sfg_score_edges up to FP32 rounding. Scratch: five n x K
+ * blocks. */
+SFG_API sfg_status sfg_filter_score(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
+                                    int steps, double omega, uint64_t seed, sfg_dtype storage,
+                                    const int32_t* edge_ids, int64_t ne, sfg_score_mode mode,
+                                    float* scores_out);
+
 /* ids_out[0..k) = the ids of the k largest entries under the strict order (score descending,
  * id ascending), written in ascending id order. ids must be distinct; 0 <= k <= ne else
  * SFG_EINVAL. */

@@ -19,17 +19,25 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
     return ((1u << LPR) - 1u) << ((lane / LPR) * LPR);
 }
 
-template <typename T, int LPR>
+// SCALED: the blocks are raw smoothed blocks and column k of each is multiplied by its projection
+// scale (sg, sp) on the fly; the projection's mean removal cancels in X_p - X_q.
+template <typename T, int LPR, bool SCALED>
 __global__ void __launch_bounds__(kBlock)
     k_score(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
             const int32_t* __restrict__ ev, const float* __restrict__ ew,
             const T* __restrict__ XG, const T* __restrict__ XP, int mode, float eta,
-            float* __restrict__ out) {
+            const float* __restrict__ sg, const float* __restrict__ sp, float* __restrict__ out) {
     constexpr int E = Vec<T>::E, K = LPR * E;
     const int lane = threadIdx.x & 31, sub = lane % LPR;
     const unsigned gm = group_mask<LPR>(lane);
     const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
     const int64_t ng = (int64_t)gridDim.x * kBlock / LPR;
+    float scg[E], scp[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        scg[k] = SCALED ? sg[sub * E + k] : 1.f;
+        scp[k] = SCALED ? sp[sub * E + k] : 1.f;
+    }
     for (int64_t i = g0; i < ne; i += ng) {
         const int32_t e = ids[i];
         const int64_t p = eu[e], q = ev[e];
@@ -41,7 +49,7 @@ __global__ void __launch_bounds__(kBlock)
         float dg = 0.f, dp = 0.f;
 #pragma unroll
         for (int k = 0; k < E; ++k) {
-            const float a = gp[k] - gq[k], b = pp[k] - pq[k];
+            const float a = (gp[k] - gq[k]) * scg[k], b = (pp[k] - pq[k]) * scp[k];
             dg = fmaf(a, a, dg);
             dp = fmaf(b, b, dp);
         }
@@ -89,13 +97,18 @@ __global__ void k_affinity(int64_t m, const int32_t* __restrict__ eu, const int3
 
 template <typename T, int LPR>
 sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
-                        const int32_t* ids, int64_t ne, int mode, float* out) {
+                        const int32_t* ids, int64_t ne, int mode, const float* sg,
+                        const float* sp, float* out) {
     if (ne == 0) return SFG_OK;
-    const int grid = sfg_grid(ctx, (const void*)k_score<T, LPR>, kBlock, 0, ne * LPR);
+    const int grid = sfg_grid(ctx, (const void*)k_score<T, LPR, false>, kBlock, 0, ne * LPR);
     sfg_tic(ctx, "score");
-    k_score<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(ne, ids, LG->eu, LG->ev, LG->ew,
-                                                      (const T*)XG, (const T*)XP, mode, 1e-30f,
-                                                      out); ++ctx->launches;
+    if (sg)
+        k_score<T, LPR, true><<<grid, kBlock, 0, ctx->stream>>>(
+            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp, out);
+    else
+        k_score<T, LPR, false><<<grid, kBlock, 0, ctx->stream>>>(
+            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp, out);
+    ++ctx->launches;
     sfg_toc(ctx);
     SFG_LAUNCH_CHECK(ctx, "k_score");
     return SFG_OK;
@@ -105,21 +118,21 @@ sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const
 
 sfg_status sfg_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
                           int K, sfg_dtype storage, const int32_t* ids, int64_t ne,
-                          sfg_score_mode mode, float* out) {
+                          sfg_score_mode mode, float* out, const float* sg, const float* sp) {
     if (storage == SFG_F32) {
         switch (K) {
-            case 4: return launch_score<float, 1>(ctx, LG, XG, XP, ids, ne, mode, out);
-            case 8: return launch_score<float, 2>(ctx, LG, XG, XP, ids, ne, mode, out);
-            case 16: return launch_score<float, 4>(ctx, LG, XG, XP, ids, ne, mode, out);
-            case 32: return launch_score<float, 8>(ctx, LG, XG, XP, ids, ne, mode, out);
-            case 64: return launch_score<float, 16>(ctx, LG, XG, XP, ids, ne, mode, out);
+            case 4: return launch_score<float, 1>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
+            case 8: return launch_score<float, 2>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
+            case 16: return launch_score<float, 4>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
+            case 32: return launch_score<float, 8>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
+            case 64: return launch_score<float, 16>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
         }
     } else if (storage == SFG_BF16) {
         switch (K) {
-            case 8: return launch_score<__nv_bfloat16, 1>(ctx, LG, XG, XP, ids, ne, mode, out);
-            case 16: return launch_score<__nv_bfloat16, 2>(ctx, LG, XG, XP, ids, ne, mode, out);
-            case 32: return launch_score<__nv_bfloat16, 4>(ctx, LG, XG, XP, ids, ne, mode, out);
-            case 64: return launch_score<__nv_bfloat16, 8>(ctx, LG, XG, XP, ids, ne, mode, out);
+            case 8: return launch_score<__nv_bfloat16, 1>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
+            case 16: return launch_score<__nv_bfloat16, 2>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
+            case 32: return launch_score<__nv_bfloat16, 4>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
+            case 64: return launch_score<__nv_bfloat16, 8>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
         }
     }
     return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", K, (int)storage);
@@ -162,7 +175,8 @@ sfg_status sfg_score_edges(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, co
     SFG_TRY(sfg_check_dev(ctx, scores_out, "scores_out"));
     if ((((uintptr_t)XG) | ((uintptr_t)XP)) & 15)
         return sfg_fail(ctx, SFG_EINVAL, "XG and XP must be 16-byte aligned");
-    return sfg_score_impl(ctx, LG, XG, XP, K, storage, edge_ids, ne, mode, scores_out);
+    return sfg_score_impl(ctx, LG, XG, XP, K, storage, edge_ids, ne, mode, scores_out, nullptr,
+                          nullptr);
 }
 
 sfg_status sfg_affinity(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,

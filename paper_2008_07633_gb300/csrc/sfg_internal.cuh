@@ -135,9 +135,15 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
                         int64_t* n_tree);
 sfg_status sfg_smooth_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                            uint64_t seed, sfg_dtype storage, void* X_out);
+// sg, sp (may be NULL): per-column scales applied to raw blocks (projection folded in).
 sfg_status sfg_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
                           int K, sfg_dtype storage, const int32_t* ids, int64_t ne,
-                          sfg_score_mode mode, float* out);
+                          sfg_score_mode mode, float* out, const float* sg = nullptr,
+                          const float* sp = nullptr);
+sfg_status sfg_filter_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
+                                 int steps, double omega, uint64_t seed, sfg_dtype storage,
+                                 const int32_t* ids, int64_t ne, sfg_score_mode mode,
+                                 float* scores);
 sfg_status sfg_topk_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids, int64_t ne,
                          int64_t k, int32_t* out);
 sfg_status sfg_coarsen_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,

@@ -379,6 +379,75 @@ struct Smoother {
         return SFG_OK;
     }
 
+    // Sweeps of one Laplacian from the block x0 (not overwritten) through the ping-pong pair
+    // (b0, b1); *out = the raw smoothed block, mean/scale = its projection statistics.
+    static sfg_status sweeps_from(sfg_ctx* ctx, const sfg_graph* L, int steps, double omega,
+                                  int grid, const T* x0, T* b0, T* b1, const float* mu,
+                                  double* part, float* coef, float* mean, float* scale,
+                                  const T** out) {
+        const int32_t n = L->n;
+        k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
+            n, L->deg, omega, coef);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_coef");
+        const T* cur = x0;
+        T* nxt = b0;
+        for (int t = 1; t <= steps; ++t) {
+            SFG_TRY(sweep(ctx, L, coef, (float)(1.0 - omega), cur, nxt, mu, part, t == 1,
+                          t == steps, grid));
+            cur = nxt;
+            nxt = (nxt == b0) ? b1 : b0;
+        }
+        if (steps > 0) {
+            k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, 1, mean, scale);
+            ++ctx->launches;
+            SFG_LAUNCH_CHECK(ctx, "k_finalize");
+        }
+        *out = cur;
+        return SFG_OK;
+    }
+
+    // Filter + score: one seeded block, swept on L_G and on L_P, scored with the projection
+    // folded into the scorer (its mean removal cancels in X_p - X_q; its scaling is per column).
+    static sfg_status filter_score(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP,
+                                   int steps, double omega, uint64_t seed, const int32_t* ids,
+                                   int64_t ne, sfg_score_mode mode, float* scores) {
+        const int32_t n = LG->n;
+        const int grid = grid_jacobi(ctx, n);
+        Scratch s(ctx);
+        T *x0, *g0, *g1, *p0, *p1;
+        float *coef, *mu, *mu_scale, *mg, *sg, *mp, *sp;
+        double* part;
+        SFG_TRY(s.get(&x0, (size_t)n * K));
+        SFG_TRY(s.get(&g0, (size_t)n * K));
+        SFG_TRY(s.get(&g1, (size_t)n * K));
+        SFG_TRY(s.get(&p0, (size_t)n * K));
+        SFG_TRY(s.get(&p1, (size_t)n * K));
+        SFG_TRY(s.get(&coef, (size_t)n));
+        SFG_TRY(s.get(&mu, K));
+        SFG_TRY(s.get(&mu_scale, K));
+        SFG_TRY(s.get(&mg, K));
+        SFG_TRY(s.get(&sg, K));
+        SFG_TRY(s.get(&mp, K));
+        SFG_TRY(s.get(&sp, K));
+        SFG_TRY(s.get(&part, (size_t)grid * 2 * K));
+        sfg_tic(ctx, "init");
+        k_init<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, seed, x0, part);
+        ++ctx->launches;
+        sfg_toc(ctx);
+        SFG_LAUNCH_CHECK(ctx, "k_init");
+        // steps == 0: the projection statistics of both blocks are those of x0
+        k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 0, mu, mu_scale);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_finalize");
+        const T *xg = x0, *xp = x0;
+        SFG_TRY(sweeps_from(ctx, LG, steps, omega, grid, x0, g0, g1, mu, part, coef, mg, sg, &xg));
+        SFG_TRY(sweeps_from(ctx, LP, steps, omega, grid, x0, p0, p1, mu, part, coef, mp, sp, &xp));
+        if (steps == 0) sg = sp = mu_scale;
+        return sfg_score_impl(ctx, LG, xg, xp, K, Vec<T>::E == 4 ? SFG_F32 : SFG_BF16, ids, ne,
+                              mode, scores, sg, sp);
+    }
+
     static sfg_status jacobi(sfg_ctx* ctx, const sfg_graph* L, int steps, double omega, T* X) {
         const int32_t n = L->n;
         const int grid = grid_jacobi(ctx, n);
@@ -441,6 +510,16 @@ sfg_status sfg_smooth_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, d
     });
 }
 
+sfg_status sfg_filter_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
+                                 int steps, double omega, uint64_t seed, sfg_dtype storage,
+                                 const int32_t* ids, int64_t ne, sfg_score_mode mode,
+                                 float* scores) {
+    return dispatch(K, storage, [&](auto S) {
+        using Sm = decltype(S);
+        return Sm::filter_score(ctx, LG, LP, steps, omega, seed, ids, ne, mode, scores);
+    });
+}
+
 static sfg_status check_smooth_args(sfg_ctx* ctx, const sfg_graph* L, int K, int steps,
                                     double omega, sfg_dtype storage, const void* X) {
     if (!L) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
@@ -470,6 +549,27 @@ sfg_status sfg_jacobi(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double
         using Sm = decltype(S);
         return Sm::jacobi(ctx, L, steps, omega, static_cast<typename Sm::Elem*>(X_inout));
     });
+}
+
+sfg_status sfg_filter_score(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
+                            int steps, double omega, uint64_t seed, sfg_dtype storage,
+                            const int32_t* edge_ids, int64_t ne, sfg_score_mode mode,
+                            float* scores_out) {
+    if (!ctx) return SFG_EINVAL;
+    if (!LG || !LP) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
+    if (LG->n != LP->n) return sfg_fail(ctx, SFG_EINVAL, "L_G and L_P differ in node count");
+    if (!sfg_k_supported(K, storage))
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", K, (int)storage);
+    if (steps < 0) return sfg_fail(ctx, SFG_EINVAL, "steps must be >= 0");
+    if (!(omega > 0.0 && omega <= 1.0)) return sfg_fail(ctx, SFG_EINVAL, "omega must be in (0, 1]");
+    if (ne < 0) return sfg_fail(ctx, SFG_EINVAL, "ne must be >= 0");
+    if (mode != SFG_SCORE_RATIO && mode != SFG_SCORE_G && mode != SFG_SCORE_P)
+        return sfg_fail(ctx, SFG_EINVAL, "unknown score mode %d", (int)mode);
+    if (ne == 0) return SFG_OK;
+    SFG_TRY(sfg_check_dev(ctx, edge_ids, "edge_ids"));
+    SFG_TRY(sfg_check_dev(ctx, scores_out, "scores_out"));
+    return sfg_filter_score_impl(ctx, LG, LP, K, steps, omega, seed, storage, edge_ids, ne, mode,
+                                 scores_out);
 }
 
 }  // extern "C"

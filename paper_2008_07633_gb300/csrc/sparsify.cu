@@ -81,25 +81,27 @@ sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64
     SFG_TRY(sfg_subgraph_impl(ctx, g, mask, &pg));
     struct Guard { sfg_graph* g; ~Guard() { sfg_graph_free(g); } } guard{pg};
 
-    const size_t blk = (size_t)g->n * P->K * elem_size(P->storage);
-    void* xp;
-    SFG_TRY(s.get((char**)&xp, blk));
-    const void* xg = XG_f32;  // the cached FP32 embedding is used as is
-    if (!XG_f32 || P->storage != SFG_F32) {
-        void* x;
-        SFG_TRY(s.get((char**)&x, blk));
-        if (XG_f32) {
+    if (!XG_f32) {  // embed G and P from one seeded block and score in one pass
+        SFG_TRY(sfg_filter_score_impl(ctx, g, pg, P->K, P->steps, P->omega, seed, P->storage, cand,
+                                      ncand, P->mode, scores));
+    } else {  // reuse the level's cached FP32 embedding of G
+        const size_t blk = (size_t)g->n * P->K * elem_size(P->storage);
+        void* xp;
+        SFG_TRY(s.get((char**)&xp, blk));
+        const void* xg = XG_f32;
+        if (P->storage != SFG_F32) {
+            void* x;
+            SFG_TRY(s.get((char**)&x, blk));
             const int64_t cnt = (int64_t)g->n * P->K;
             k_f32_to_bf16<<<sfg_grid(ctx, (const void*)k_f32_to_bf16, kBlock, 0, cnt), kBlock, 0,
-                            ctx->stream>>>(cnt, XG_f32, (__nv_bfloat16*)x); ++ctx->launches;
+                            ctx->stream>>>(cnt, XG_f32, (__nv_bfloat16*)x);
+            ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_f32_to_bf16");
-        } else {
-            SFG_TRY(sfg_smooth_impl(ctx, g, P->K, P->steps, P->omega, seed, P->storage, x));
+            xg = x;
         }
-        xg = x;
+        SFG_TRY(sfg_smooth_impl(ctx, pg, P->K, P->steps, P->omega, seed, P->storage, xp));
+        SFG_TRY(sfg_score_impl(ctx, g, xg, xp, P->K, P->storage, cand, ncand, P->mode, scores));
     }
-    SFG_TRY(sfg_smooth_impl(ctx, pg, P->K, P->steps, P->omega, seed, P->storage, xp));
-    SFG_TRY(sfg_score_impl(ctx, g, xg, xp, P->K, P->storage, cand, ncand, P->mode, scores));
     SFG_TRY(sfg_topk_impl(ctx, scores, cand, ncand, k, sel));
     k_set_mask<<<sfg_grid(ctx, (const void*)k_set_mask, kBlock, 0, k), kBlock, 0, ctx->stream>>>(
         k, sel, mask); ++ctx->launches;

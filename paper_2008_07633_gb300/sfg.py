@@ -24,7 +24,7 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_
            "sfg_ctx_timing", "sfg_ctx_kernel_time", "sfg_ctx_launches", "sfg_laplacian", "sfg_graph_destroy",
            "sfg_graph_info", "sfg_graph_edges", "sfg_graph_csr", "sfg_graph_subgraph", "sfg_smooth",
            "sfg_jacobi", "sfg_score_edges", "sfg_select_topk", "sfg_spanning_tree", "sfg_affinity",
-           "sfg_affinity_noalloc",
+           "sfg_affinity_noalloc", "sfg_filter_score",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify"]
 
 
@@ -72,6 +72,7 @@ def lib():
             "sfg_jacobi": [_vp, _vp, _int, _int, _dbl, _int, _vp],
             "sfg_score_edges": [_vp, _vp, _vp, _vp, _int, _int, _vp, _i64, _int, _vp],
             "sfg_select_topk": [_vp, _vp, _vp, _i64, _i64, _vp],
+            "sfg_filter_score": [_vp, _vp, _vp, _int, _int, _dbl, _u64, _int, _vp, _i64, _int, _vp],
             "sfg_spanning_tree": [_vp, _vp, _vp, _vp, _pi64],
             "sfg_affinity": [_vp, _vp, _vp, _int, _vp],
             "sfg_affinity_noalloc": [_vp, _vp, _vp, _int, _vp],
@@ -245,6 +246,16 @@ def sfg_score_edges(ctx, g, XG, XP, ids, mode=SFG_SCORE_RATIO, out=None):
         out = torch.empty(ids.numel(), dtype=torch.float32, device=ctx.device)
     ctx.check(lib().sfg_score_edges(ctx.h, g.h, _ptr(XG), _ptr(XP), XG.shape[1], _dt(XG.dtype),
                                     _ptr(ids), ids.numel(), mode, _ptr(out)))
+    return out
+
+
+def sfg_filter_score(ctx, LG, LP, ids, K, steps, omega=0.7, seed=0, storage=torch.float32,
+                     mode=SFG_SCORE_RATIO, out=None):
+    ids = ids.contiguous()
+    if out is None:
+        out = torch.empty(ids.numel(), dtype=torch.float32, device=ctx.device)
+    ctx.check(lib().sfg_filter_score(ctx.h, LG.h, LP.h, K, steps, omega, seed & (2**64 - 1),
+                                     _dt(storage), _ptr(ids), ids.numel(), mode, _ptr(out)))
     return out
 
 

@@ -366,3 +366,35 @@ def test_sparsify_bf16_storage(S, ctx):
     omask, _ = O.sparsify(og, K=16, steps=10, levels=0, seed=5, budget_frac=0.1, budget_unit=1)
     kg, ko = O.kappa_dense(og, host(mask)), O.kappa_dense(og, omask)
     assert kg <= 1.25 * ko, (kg, ko)     # reported tolerance for BF16 storage
+
+
+# ------------------------------------------------------------------ fused filter + score --------
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("T", [0, 1, 10])
+def test_filter_score_matches_oracle(S, ctx, mode, T):
+    n, u, v, w = gen.grid2d(64, 64, seed=1)
+    g, og = make(S, ctx, n, u, v, w)
+    tree, _ = S.sfg_spanning_tree(ctx, g)
+    p = S.sfg_graph_subgraph(ctx, g, tree)
+    off = np.nonzero(host(tree) == 0)[0].astype(np.int32)
+    s = host(S.sfg_filter_score(ctx, g, p, dev(off), 8, T, 0.7, seed=1001, mode=mode))
+    otree = O.mst(og)
+    ref = O.score_edges(og, O.smooth(og, 8, T, 0.7, 1001),
+                        O.smooth(og.subgraph(otree), 8, T, 0.7, 1001), off, mode)
+    err = np.linalg.norm(s - ref) / np.linalg.norm(ref)
+    assert err < TOL_S, err
+
+
+def test_filter_score_equals_smooth_then_score(S, ctx):
+    n, u, v, w = gen.grid3d(20, seed=2)
+    g, og = make(S, ctx, n, u, v, w)
+    tree, _ = S.sfg_spanning_tree(ctx, g)
+    p = S.sfg_graph_subgraph(ctx, g, tree)
+    off = torch.nonzero(tree == 0).flatten().to(torch.int32)
+    for K, dt in ((32, torch.float32), (64, torch.float32), (32, torch.bfloat16)):
+        fused = host(S.sfg_filter_score(ctx, g, p, off, K, 20, 0.7, seed=9, storage=dt))
+        xg = S.sfg_smooth(ctx, g, K, 20, 0.7, seed=9, storage=dt)
+        xp = S.sfg_smooth(ctx, p, K, 20, 0.7, seed=9, storage=dt)
+        sep = host(S.sfg_score_edges(ctx, g, xg, xp, off))
+        tol = 1e-5 if dt == torch.float32 else 3e-2   # BF16: projection rounded in the separate path
+        assert np.linalg.norm(fused - sep) / np.linalg.norm(sep) < tol
