@@ -108,12 +108,13 @@ __global__ void k_lap_lower(const int2* __restrict__ colval, const int32_t* __re
 }
 
 __global__ void k_lap_deg(const int32_t* __restrict__ row_ptr, const int2* __restrict__ colval,
-                          int32_t n, double* __restrict__ deg) {
+                          int32_t n, double* __restrict__ deg, double* __restrict__ invdeg) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;  // in column order
         for (int32_t j = row_ptr[p]; j < row_ptr[p + 1]; ++j) s += (double)__int_as_float(colval[j].y);
         deg[p] = s;
+        invdeg[p] = s > 0.0 ? 1.0 / s : 0.0;
     }
 }
 
@@ -201,7 +202,7 @@ int grid_of(sfg_ctx* ctx, K kernel, int64_t work) {
 void sfg_graph_free(sfg_graph* g) {
     if (!g) return;
     cudaStream_t s = g->stream;
-    void* ptrs[] = {g->eu, g->ev, g->ew, g->row_ptr, g->colval, g->eid, g->deg};
+    void* ptrs[] = {g->eu, g->ev, g->ew, g->row_ptr, g->colval, g->eid, g->deg, g->invdeg};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
     delete g;
@@ -224,6 +225,7 @@ static sfg_status alloc_graph(sfg_ctx* ctx, int32_t n, int64_t m, sfg_graph** ou
     A((void**)&g->colval, sizeof(int2) * 2 * m);
     A((void**)&g->eid, sizeof(int32_t) * 2 * m);
     A((void**)&g->deg, sizeof(double) * n);
+    A((void**)&g->invdeg, sizeof(double) * n);
     if (st != SFG_OK) {
         sfg_graph_free(g);
         return st;
@@ -308,7 +310,7 @@ sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
     }
     if (n > 0) {
         k_lap_deg<<<grid_of(ctx, k_lap_deg, n), kBlock, 0, ctx->stream>>>(g->row_ptr, g->colval, n,
-                                                                          g->deg); ++ctx->launches;
+                                                                          g->deg, g->invdeg); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_deg");
     }
     if (f2c && m > 0) {
@@ -362,7 +364,7 @@ sfg_status sfg_subgraph_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* ma
     SFG_LAUNCH_CHECK(ctx, "k_sub_rowptr");
     if (g->n > 0) {
         k_lap_deg<<<grid_of(ctx, k_lap_deg, g->n), kBlock, 0, ctx->stream>>>(p->row_ptr, p->colval,
-                                                                             g->n, p->deg); ++ctx->launches;
+                                                                             g->n, p->deg, p->invdeg); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_deg");
     }
     *out = p;

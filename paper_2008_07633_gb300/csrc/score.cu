@@ -19,6 +19,11 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
     return ((1u << LPR) - 1u) << ((lane / LPR) * LPR);
 }
 
+// Scorer, warp-tile schedule: a warp scores a tile of GPW = 32 / LPR consecutive list entries
+// (one LPR-lane group per edge) and moves by grid stride. Lane l < GPW loads the tile's l-th edge
+// id and then that edge's endpoints and weight; groups take theirs by shuffle. The next tile's
+// endpoints and the ids of the tile after it are loaded before this tile's four row gathers are
+// consumed, so one gather round is the exposed latency per tile.
 // SCALED: the blocks are raw smoothed blocks and column k of each is multiplied by its projection
 // scale (sg, sp) on the fly; the projection's mean removal cancels in X_p - X_q.
 template <typename T, int LPR, bool SCALED>
@@ -27,25 +32,45 @@ __global__ void __launch_bounds__(kBlock)
             const int32_t* __restrict__ ev, const float* __restrict__ ew,
             const T* __restrict__ XG, const T* __restrict__ XP, int mode, float eta,
             const float* __restrict__ sg, const float* __restrict__ sp, float* __restrict__ out) {
-    constexpr int E = Vec<T>::E, K = LPR * E;
-    const int lane = threadIdx.x & 31, sub = lane % LPR;
+    constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR;
+    const int lane = threadIdx.x & 31, grp = lane / LPR, sub = lane % LPR;
     const unsigned gm = group_mask<LPR>(lane);
-    const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
-    const int64_t ng = (int64_t)gridDim.x * kBlock / LPR;
+    const int64_t wid = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
+    const int64_t ntiles = (ne + GPW - 1) / GPW;
+    const T* __restrict__ Xg = XG + sub * E;
+    const T* __restrict__ Xp = XP + sub * E;
     float scg[E], scp[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) {
         scg[k] = SCALED ? sg[sub * E + k] : 1.f;
         scp[k] = SCALED ? sp[sub * E + k] : 1.f;
     }
-    for (int64_t i = g0; i < ne; i += ng) {
-        const int32_t e = ids[i];
-        const int64_t p = eu[e], q = ev[e];
+    auto load_id = [&](int64_t t) -> int32_t {
+        const int64_t i = t * GPW + lane;
+        return (t < ntiles && lane < GPW && i < ne) ? ids[i] : -1;
+    };
+    struct Edge { int32_t p, q; float w; };
+    auto load_edge = [&](int32_t e) {
+        Edge d{0, 0, 0.f};
+        if (e >= 0) { d.p = eu[e]; d.q = ev[e]; d.w = ew[e]; }
+        return d;
+    };
+    int64_t t = wid;
+    Edge cur = load_edge(load_id(t));
+    int32_t idn = load_id(t + nw);
+    for (; t < ntiles; t += nw) {
+        const Edge nxt = load_edge(idn);          // next tile's endpoints
+        idn = load_id(t + 2 * nw);                // ids of the tile after it
+        const int64_t i = t * GPW + grp;
+        const int64_t p = __shfl_sync(0xffffffffu, cur.p, grp);
+        const int64_t q = __shfl_sync(0xffffffffu, cur.q, grp);
+        const float w = __shfl_sync(0xffffffffu, cur.w, grp);
         float gp[E], gq[E], pp[E], pq[E];
-        Vec<T>::load(XG + p * K + sub * E, gp);
-        Vec<T>::load(XG + q * K + sub * E, gq);
-        Vec<T>::load(XP + p * K + sub * E, pp);
-        Vec<T>::load(XP + q * K + sub * E, pq);
+        Vec<T>::load(Xg + p * K, gp);
+        Vec<T>::load(Xg + q * K, gq);
+        Vec<T>::load(Xp + p * K, pp);
+        Vec<T>::load(Xp + q * K, pq);
         float dg = 0.f, dp = 0.f;
 #pragma unroll
         for (int k = 0; k < E; ++k) {
@@ -58,11 +83,11 @@ __global__ void __launch_bounds__(kBlock)
             dg += __shfl_xor_sync(gm, dg, o, LPR);
             dp += __shfl_xor_sync(gm, dp, o, LPR);
         }
-        if (sub == 0) {
-            const float w = ew[e];
-            const float sg = w * dg, sp = w * dp;
-            out[i] = mode == SFG_SCORE_G ? sg : (mode == SFG_SCORE_P ? sp : sp / (sg + eta));
+        if (sub == 0 && i < ne) {
+            const float sgv = w * dg, spv = w * dp;
+            out[i] = mode == SFG_SCORE_G ? sgv : (mode == SFG_SCORE_P ? spv : spv / (sgv + eta));
         }
+        cur = nxt;
     }
 }
 

@@ -47,20 +47,29 @@ __global__ void __launch_bounds__(kBlock)
     if (h[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
 }
 
+// Pick the digit holding the k-th largest key: suffix sums over the 256 buckets by a block scan
+// (thread d holds bucket 255 - d), then the first bucket whose suffix reaches krem.
 __global__ void k_sel_pick(int shift, SelState* st) {
-    if (threadIdx.x == 0) {
-        long long above = 0;
-        int d = 255;
-        for (; d > 0; --d) {
-            const long long c = (long long)st->hist[d];
-            if (above + c >= st->krem) break;
-            above += c;
-        }
-        st->prefix |= (unsigned long long)d << shift;
-        st->krem -= above;
-    }
+    __shared__ long long suf[256];
+    const int d = 255 - (int)threadIdx.x;
+    const long long c = (long long)st->hist[d];
+    suf[threadIdx.x] = c;
     __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += blockDim.x) st->hist[d] = 0ull;
+    for (int o = 1; o < 256; o <<= 1) {  // inclusive scan from the top bucket down
+        const long long v = threadIdx.x >= o ? suf[threadIdx.x - o] : 0;
+        __syncthreads();
+        suf[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const long long krem = st->krem;
+    const long long incl = suf[threadIdx.x], above = incl - c;
+    const bool pick = (above < krem && incl >= krem) || (d == 0 && incl < krem);
+    __syncthreads();
+    if (pick) {
+        st->prefix |= (unsigned long long)d << shift;
+        st->krem = krem - above;
+    }
+    st->hist[d] = 0ull;
 }
 
 __global__ void k_sel_flags(int64_t ne, const float* __restrict__ scores,
@@ -112,7 +121,7 @@ sfg_status sfg_topk_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids, 
     k_sel_init<<<1, kBlock, 0, ctx->stream>>>(st, k); ++ctx->launches;
     for (int shift = 56; shift >= 0; shift -= 8) {
         k_sel_hist<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, shift, st); ++ctx->launches;
-        k_sel_pick<<<1, kBlock, 0, ctx->stream>>>(shift, st); ++ctx->launches;
+        k_sel_pick<<<1, 256, 0, ctx->stream>>>(shift, st); ++ctx->launches;
     }
     k_sel_flags<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, st, flag); ++ctx->launches;
     sfg_toc(ctx);

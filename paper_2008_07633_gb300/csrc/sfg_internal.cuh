@@ -42,6 +42,7 @@ struct sfg_graph {
     int2* colval = nullptr;    // [2m] (column, float bits of the weight), rows sorted by column
     int32_t* eid = nullptr;    // [2m] canonical edge id of each CSR entry
     double* deg = nullptr;     // [n]
+    double* invdeg = nullptr;  // [n] 1 / deg in FP64 (0 for isolated nodes)
     cudaStream_t stream = nullptr;
 };
 

@@ -19,6 +19,12 @@
 namespace {
 
 constexpr int kBlock = 256;
+#ifndef SFG_JACOBI_TPI
+#define SFG_JACOBI_TPI 2  // consecutive row tiles a warp sweeps before its grid-stride jump
+#endif
+#ifndef SFG_JACOBI_STREAM_HINTS
+#define SFG_JACOBI_STREAM_HINTS 0  // 1: load CSR metadata with the evict-first (streaming) hint
+#endif
 #ifndef SFG_JACOBI_MIN_BLOCKS
 #define SFG_JACOBI_MIN_BLOCKS 4  // resident CTAs per SM requested from the compiler (caps registers at 64)
 #endif
@@ -103,6 +109,15 @@ __global__ void __launch_bounds__(kBlock) k_init(int32_t n, uint64_t seed, T* __
     block_column_partials<LPR, E>(s1, s2, part);
 }
 
+template <typename V>
+__device__ __forceinline__ V ldmeta(const V* p) {
+#if SFG_JACOBI_STREAM_HINTS
+    return __ldcs(p);
+#else
+    return *p;
+#endif
+}
+
 // A chunk of C = max(LPR, 8) consecutive (column, weight) entries of one row, spread over the
 // LPR lanes of the row's group (C / LPR per lane). Slots past the row's end hold (row, 0): they
 // gather the row itself with weight zero, so the gather loop needs no per-slot predicate.
@@ -115,7 +130,7 @@ struct Chunk {
 #pragma unroll
         for (int t = 0; t < PER; ++t) {
             const int32_t j = j0 + sub + t * LPR;
-            cv[t] = j < b ? colval[j] : make_int2(self, 0);
+            cv[t] = j < b ? ldmeta(colval + j) : make_int2(self, 0);
         }
     }
 };
@@ -181,6 +196,11 @@ __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
     const int32_t nw = (int32_t)(gridDim.x * (kBlock / 32));
     const int32_t ntiles = (n + GPW - 1) / GPW;
     const T* __restrict__ Xl = X + sub * E;
+    // tile order of this warp: TPI consecutive tiles, then a jump over the other warps' tiles
+    constexpr int32_t TPI = SFG_JACOBI_TPI;
+    auto next_tile = [&](int32_t t) {
+        return (t + 1) % TPI != 0 ? t + 1 : t + 1 + (nw - 1) * TPI;
+    };
 
     float m[E], s1[E], s2[E];
 #pragma unroll
@@ -194,21 +214,22 @@ __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
     auto load_meta = [&](int32_t t) {
         Meta mt{0, 0, 0.f};
         const int32_t r = t * GPW + lane;
-        if (t < ntiles && lane <= GPW) mt.lo = row_ptr[min(r, n)];
-        if (GPW == 32 && t < ntiles) mt.hi = row_ptr[min(r + 1, n)];
-        if (t < ntiles && lane < GPW && r < n) mt.cf = coef[r];
+        if (t < ntiles && lane <= GPW) mt.lo = ldmeta(row_ptr + min(r, n));
+        if (GPW == 32 && t < ntiles) mt.hi = ldmeta(row_ptr + min(r + 1, n));
+        if (t < ntiles && lane < GPW && r < n) mt.cf = ldmeta(coef + r);
         return mt;
     };
 
-    int32_t t = wid;
+    int32_t t = wid * TPI;
     Meta mt = load_meta(t);
     int32_t a = __shfl_sync(0xffffffffu, mt.lo, grp);
     int32_t b = GPW == 32 ? mt.hi : __shfl_sync(0xffffffffu, mt.lo, grp + 1);
     int32_t r = t * GPW + grp;
     Chunk<LPR> ch;
     ch.load(colval, a, b, r < n ? r : 0, sub);
-    for (; t < ntiles; t += nw) {
-        const Meta mtn = load_meta(t + nw);  // next tile's metadata, in flight with the gathers
+    for (; t < ntiles; t = next_tile(t)) {
+        const int32_t tn = next_tile(t);
+        const Meta mtn = load_meta(tn);  // next tile's metadata, in flight with the gathers
 
         const bool live = r < n;
         const int32_t self = live ? r : 0;
@@ -229,7 +250,7 @@ __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
         // next tile: row bounds and first chunk (its metadata has had the gather round to arrive)
         const int32_t an = __shfl_sync(0xffffffffu, mtn.lo, grp);
         const int32_t bn = GPW == 32 ? mtn.hi : __shfl_sync(0xffffffffu, mtn.lo, grp + 1);
-        const int32_t rn = (t + nw) * GPW + grp;
+        const int32_t rn = tn * GPW + grp;
         ch.load(colval, an, bn, rn < n ? rn : 0, sub);
 
         if (live) {
@@ -258,23 +279,39 @@ __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
     if (STATS) block_column_partials<LPR, E>(s1, s2, part);
 }
 
-// Fold the per-block partials in block order (FP64). proj = 0: mean only (mu = S1 / n).
-// proj = 1: mean and scale = 1 / RMS of the centred column (1 if the column is zero).
-__global__ void k_finalize(const double* __restrict__ part, int nblocks, int K, int32_t n,
-                           int proj, float* __restrict__ mean, float* __restrict__ scale) {
-    const int k = threadIdx.x;
-    if (k >= K) return;
+// Fold the per-block partials (FP64): one CTA per column, each thread sums a fixed stride of
+// blocks, then a fixed-shape tree, so the result does not depend on scheduling.
+// proj = 0: mean only (mu = S1 / n). proj = 1: mean and scale = 1 / RMS of the centred column
+// (1 if the column is zero).
+__global__ void __launch_bounds__(kBlock) k_finalize(const double* __restrict__ part, int nblocks,
+                                                     int K, int32_t n, int proj,
+                                                     float* __restrict__ mean,
+                                                     float* __restrict__ scale) {
+    __shared__ double r1[kBlock], r2[kBlock];
+    const int k = blockIdx.x;
     double s1 = 0.0, s2 = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
+    for (int b = threadIdx.x; b < nblocks; b += kBlock) {
         s1 += part[(size_t)b * 2 * K + k];
         s2 += part[(size_t)b * 2 * K + K + k];
     }
-    const double mu = s1 / (double)n;
-    mean[k] = (float)mu;
-    if (proj) {
-        const double var = s2 / (double)n - mu * mu;
-        const double rms = var > 0.0 ? sqrt(var) : 0.0;
-        scale[k] = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
+    r1[threadIdx.x] = s1;
+    r2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            r1[threadIdx.x] += r1[threadIdx.x + w];
+            r2[threadIdx.x] += r2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mu = r1[0] / (double)n;
+        mean[k] = (float)mu;
+        if (proj) {
+            const double var = r2[0] / (double)n - mu * mu;
+            const double rms = var > 0.0 ? sqrt(var) : 0.0;
+            scale[k] = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
+        }
     }
 }
 
@@ -296,11 +333,12 @@ __global__ void __launch_bounds__(kBlock) k_project(int32_t n, const T* __restri
     }
 }
 
-__global__ void k_coef(int32_t n, const double* __restrict__ deg, double omega,
+// c_p = omega * (1 / D(p,p)) with the reciprocal formed once per graph in FP64; 0 if D(p,p) = 0.
+__global__ void k_coef(int32_t n, const double* __restrict__ invdeg, double omega,
                        float* __restrict__ coef) {
     for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * kBlock)
-        coef[p] = deg[p] > 0.0 ? (float)(omega / deg[p]) : 0.0f;
+        coef[p] = (float)(omega * invdeg[p]);
 }
 
 template <typename T, int LPR>
@@ -350,7 +388,7 @@ struct Smoother {
         SFG_TRY(s.get(&scale, K));
         SFG_TRY(s.get(&part, (size_t)grid * 2 * K));
         k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
-            n, L->deg, omega, coef); ++ctx->launches;
+            n, L->invdeg, omega, coef); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_coef");
         // ping-pong so that the last sweep writes `buf` and the projection writes X_out
         T* cur = (steps % 2 == 0) ? buf : X_out;
@@ -359,7 +397,7 @@ struct Smoother {
         k_init<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, seed, cur, part); ++ctx->launches;
         sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_init");
-        k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 0, mu, scale); ++ctx->launches;
+        k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 0, mu, scale); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_finalize");
         for (int t = 1; t <= steps; ++t) {
             SFG_TRY(sweep(ctx, L, coef, (float)(1.0 - omega), cur, nxt, mu, part, t == 1,
@@ -367,7 +405,7 @@ struct Smoother {
             std::swap(cur, nxt);
         }
         if (steps > 0) {
-            k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, 1, mu, scale); ++ctx->launches;
+            k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, 1, mu, scale); ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_finalize");
         }
         sfg_tic(ctx, "project");
@@ -387,7 +425,7 @@ struct Smoother {
                                   const T** out) {
         const int32_t n = L->n;
         k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
-            n, L->deg, omega, coef);
+            n, L->invdeg, omega, coef);
         ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_coef");
         const T* cur = x0;
@@ -399,7 +437,7 @@ struct Smoother {
             nxt = (nxt == b0) ? b1 : b0;
         }
         if (steps > 0) {
-            k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, 1, mean, scale);
+            k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, 1, mean, scale);
             ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_finalize");
         }
@@ -437,7 +475,7 @@ struct Smoother {
         sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_init");
         // steps == 0: the projection statistics of both blocks are those of x0
-        k_finalize<<<1, 64, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 0, mu, mu_scale);
+        k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 0, mu, mu_scale);
         ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_finalize");
         const T *xg = x0, *xp = x0;
@@ -457,7 +495,7 @@ struct Smoother {
         SFG_TRY(s.get(&buf, (size_t)n * K));
         SFG_TRY(s.get(&coef, (size_t)n));
         k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
-            n, L->deg, omega, coef); ++ctx->launches;
+            n, L->invdeg, omega, coef); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_coef");
         T* cur = X;
         T* nxt = buf;
