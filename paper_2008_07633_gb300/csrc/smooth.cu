@@ -346,31 +346,26 @@ struct Smoother {
     using Elem = T;
     static constexpr int E = Vec<T>::E, K = LPR * E;
 
+    template <bool A, bool B>
+    static void* kern() { return (void*)k_jacobi<T, LPR, A, B>; }
+
     static int grid_jacobi(sfg_ctx* ctx, int32_t n) {
-        return sfg_grid(ctx, (const void*)k_jacobi<T, LPR, false, false>, kBlock, 0,
-                        (int64_t)n * LPR);
+        return sfg_grid(ctx, kern<false, false>(), kBlock, 0, (int64_t)n * LPR);
     }
 
     static sfg_status sweep(sfg_ctx* ctx, const sfg_graph* L, const float* coef, float a_self,
                             const T* X, T* Y, const float* mu, double* part, bool sub_mu,
                             bool stats, int grid) {
         const int32_t n = L->n;
+        void* args[] = {(void*)&n, (void*)&L->row_ptr, (void*)&L->colval, (void*)&coef,
+                        (void*)&a_self, (void*)&X, (void*)&Y, (void*)&mu, (void*)&part};
+        void* k = sub_mu ? (stats ? kern<true, true>() : kern<true, false>())
+                         : (stats ? kern<false, true>() : kern<false, false>());
         sfg_tic(ctx, "jacobi");
         ++ctx->launches;
-        if (sub_mu && stats)
-            k_jacobi<T, LPR, true, true><<<grid, kBlock, 0, ctx->stream>>>(
-                n, L->row_ptr, L->colval, coef, a_self, X, Y, mu, part);
-        else if (sub_mu)
-            k_jacobi<T, LPR, true, false><<<grid, kBlock, 0, ctx->stream>>>(
-                n, L->row_ptr, L->colval, coef, a_self, X, Y, mu, part);
-        else if (stats)
-            k_jacobi<T, LPR, false, true><<<grid, kBlock, 0, ctx->stream>>>(
-                n, L->row_ptr, L->colval, coef, a_self, X, Y, mu, part);
-        else
-            k_jacobi<T, LPR, false, false><<<grid, kBlock, 0, ctx->stream>>>(
-                n, L->row_ptr, L->colval, coef, a_self, X, Y, mu, part);
+        const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kBlock), args, 0, ctx->stream);
         sfg_toc(ctx);
-        SFG_LAUNCH_CHECK(ctx, "k_jacobi");
+        if (e != cudaSuccess) return sfg_cuda_fail(ctx, e, "k_jacobi");
         return SFG_OK;
     }
 
