@@ -117,7 +117,10 @@ SFG_API sfg_status sfg_graph_subgraph(sfg_ctx* ctx, const sfg_graph* g, const ui
 
 /* X_out (n x K, row-major, `storage`) <- the smoothed, projected block:
  *  1. X0[i,k] = Gaussian entry j = i*K + k of this counter-based generator, rounded to
- *     `storage`; each column's mean (FP64) removed. SplitMix64 (Steele, Lea & Flood 2014),
+ *     `storage`; each column's mean removed (FP64 sums). The removed mean is the D-weighted one,
+ *     which the sweeps keep: it differs from the plain mean by a constant vector that step 3
+ *     removes anyway, so the result is that of the plain reading, without FP32 having to cancel
+ *     a persisting constant on fast-mixing graphs. SplitMix64 (Steele, Lea & Flood 2014),
  *     started in state s0 = splitmix64(seed), gives output o_p = splitmix64(s0 + p * gamma) for
  *     the pair of entries 2p, 2p+1: u1 = ((o_p >> 32) + 1) 2^-32, u2 = ((o_p >> 8) mod 2^24)
  *     2^-24, r = sqrt(-2 ln u1), X0_2p = r cos(2 pi u2), X0_2p+1 = r sin(2 pi u2). Evaluated in
@@ -239,6 +242,17 @@ typedef struct {
  * already over. n_selected_host (may be NULL) receives the number of edges in P. Synchronises. */
 SFG_API sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* params,
                         uint8_t* mask_out, int64_t* n_selected_host);
+
+/* Batched flat method: sparsify ng independent graphs in one set of launches (their disjoint
+ * union is processed as one graph; the seeded blocks, projection statistics, budgets and top-k
+ * are per graph). masks_out[g] is a device buffer of graph g's m_g entries; n_selected_host (may
+ * be NULL) receives ng counts. Each graph's mask is the one sfg_sparsify gives for that graph
+ * with the same parameters (up to FP32 summation order in the column statistics). levels must be
+ * 0 (else SFG_EUNSUPPORTED); the union must fit int32 indices (sum n < 2^31, 2 sum m < 2^31).
+ * Synchronises. */
+SFG_API sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* const* gs,
+                                        const sfg_params* params, uint8_t* const* masks_out,
+                                        int64_t* n_selected_host);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,277 @@
+// Batched flat sparsification of many graphs (a batch of independent problems, e.g. many small
+// k-NN graphs) in one set of launches.
+//
+// The graphs are joined into their disjoint union U: canonical lists, CSR rows and entries are
+// concatenated with node and edge offsets, which keeps every list sorted and every edge id order,
+// so no sort is needed. On U, one Boruvka run gives every graph's spanning forest (the forests of
+// disjoint components are independent and the strict edge order is preserved), one launch per
+// Jacobi sweep smooths every graph, and the per-graph parts -- the seeded blocks, their mean
+// removal, the projection scales, the budgets and the top-k -- are segmented by graph. Each
+// graph's result is the one sfg_sparsify gives for it alone with the same parameters (up to FP32
+// summation order in the column statistics).
+#include <cmath>
+#include <vector>
+
+#include "sfg_internal.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+struct GDesc {
+    const int32_t *eu, *ev;
+    const float* ew;
+    const int32_t* row_ptr;
+    const int2* colval;
+    const int32_t* eid;
+    const double *deg, *invdeg;
+    int32_t node_off;
+    int64_t edge_off;
+};
+
+template <typename O>
+__device__ __forceinline__ int seg_of(const O* __restrict__ off, int ng, int64_t i) {
+    int lo = 0, hi = ng;  // last g with off[g] <= i
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if ((int64_t)off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_union_edges(int64_t m, const GDesc* __restrict__ d, int ng,
+                              const int64_t* __restrict__ eoff, int32_t* __restrict__ eu,
+                              int32_t* __restrict__ ev, float* __restrict__ ew) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock) {
+        const int g = seg_of(eoff, ng, e);
+        const int64_t l = e - eoff[g];
+        eu[e] = d[g].eu[l] + d[g].node_off;
+        ev[e] = d[g].ev[l] + d[g].node_off;
+        ew[e] = d[g].ew[l];
+    }
+}
+
+__global__ void k_union_rows(int32_t n, int64_t m, const GDesc* __restrict__ d, int ng,
+                             const int32_t* __restrict__ noff, int32_t* __restrict__ row_ptr,
+                             double* __restrict__ deg, double* __restrict__ invdeg) {
+    for (int64_t r = (int64_t)blockIdx.x * kBlock + threadIdx.x; r <= n;
+         r += (int64_t)gridDim.x * kBlock) {
+        if (r == n) {
+            row_ptr[n] = (int32_t)(2 * m);
+            continue;
+        }
+        const int g = seg_of(noff, ng, r);
+        const int64_t l = r - noff[g];
+        row_ptr[r] = d[g].row_ptr[l] + (int32_t)(2 * d[g].edge_off);
+        deg[r] = d[g].deg[l];
+        invdeg[r] = d[g].invdeg[l];
+    }
+}
+
+__global__ void k_union_entries(int64_t m, const GDesc* __restrict__ d, int ng,
+                                const int64_t* __restrict__ eoff, int2* __restrict__ colval,
+                                int32_t* __restrict__ eid) {
+    for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < 2 * m;
+         j += (int64_t)gridDim.x * kBlock) {
+        const int g = seg_of(eoff, ng, j >> 1);  // graph g owns entries [2 eoff[g], 2 eoff[g+1])
+        const int64_t l = j - 2 * eoff[g];
+        const int2 cv = d[g].colval[l];
+        colval[j] = make_int2(cv.x + d[g].node_off, cv.y);
+        eid[j] = d[g].eid[l] + (int32_t)d[g].edge_off;
+    }
+}
+
+// per-graph count of set mask entries (edge ranges eoff)
+__global__ void k_seg_count(int64_t m, const uint8_t* __restrict__ mask, int ng,
+                            const int64_t* __restrict__ eoff, unsigned long long* __restrict__ cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock) {
+        const bool on = mask[e] != 0;
+        const unsigned bin = on ? (unsigned)seg_of(eoff, ng, e) : 0xffffffffu;
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, bin);
+        if (on && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+            atomicAdd(&cnt[bin], (unsigned long long)__popc(peers));
+    }
+}
+
+__global__ void k_not(int64_t m, const uint8_t* __restrict__ mask, uint8_t* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock)
+        out[e] = mask[e] == 0;
+}
+
+__global__ void k_compact(int64_t m, const uint8_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                          int32_t* __restrict__ ids) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock)
+        if (flag[e]) ids[pos[e]] = (int32_t)e;
+}
+
+__global__ void k_mark(int64_t k, const int32_t* __restrict__ ids, uint8_t* __restrict__ mask) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < k;
+         i += (int64_t)gridDim.x * kBlock)
+        mask[ids[i]] = 1;
+}
+
+__global__ void k_split(int64_t m, const uint8_t* __restrict__ mask, int ng,
+                        const int64_t* __restrict__ eoff, uint8_t* const* __restrict__ outs) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock) {
+        const int g = seg_of(eoff, ng, e);
+        outs[g][e - eoff[g]] = mask[e];
+    }
+}
+
+template <typename K>
+int grid_of(sfg_ctx* ctx, K kernel, int64_t work) {
+    return sfg_grid(ctx, (const void*)kernel, kBlock, 0, work);
+}
+
+int64_t round_half_up(double x) { return (int64_t)std::floor(x + 0.5); }
+
+struct GraphGuard {
+    sfg_graph* g = nullptr;
+    ~GraphGuard() { sfg_graph_free(g); }
+};
+
+}  // namespace
+
+extern "C" sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* const* gs,
+                                           const sfg_params* P, uint8_t* const* masks_out,
+                                           int64_t* n_selected_host) {
+    if (!ctx) return SFG_EINVAL;
+    if (ng < 1 || !gs || !P || !masks_out) return sfg_fail(ctx, SFG_EINVAL, "bad batch arguments");
+    if (P->levels != 0)
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "the batched form is flat (levels = 0)");
+    if (!sfg_k_supported(P->K, P->storage))
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K, (int)P->storage);
+    if (P->steps < 0 || !(P->omega > 0.0 && P->omega <= 1.0) || !(P->budget_frac >= 0.0) ||
+        (P->budget_unit != 0 && P->budget_unit != 1) ||
+        (P->mode != SFG_SCORE_RATIO && P->mode != SFG_SCORE_G && P->mode != SFG_SCORE_P))
+        return sfg_fail(ctx, SFG_EINVAL, "invalid sfg_params");
+    std::vector<int32_t> noff(ng + 1, 0);
+    std::vector<int64_t> eoff(ng + 1, 0);
+    std::vector<GDesc> desc(ng);
+    for (int g = 0; g < ng; ++g) {
+        const sfg_graph* G = gs[g];
+        if (!G) return sfg_fail(ctx, SFG_EINVAL, "graph %d is NULL", g);
+        if (G->m > 0) SFG_TRY(sfg_check_dev(ctx, masks_out[g], "masks_out[g]"));
+        if ((int64_t)noff[g] + G->n >= (1ll << 31) || 2 * (eoff[g] + G->m) >= (1ll << 31))
+            return sfg_fail(ctx, SFG_EINVAL, "batch too large for int32 indices");
+        noff[g + 1] = noff[g] + G->n;
+        eoff[g + 1] = eoff[g] + G->m;
+        desc[g] = GDesc{G->eu, G->ev, G->ew, G->row_ptr, G->colval, G->eid, G->deg, G->invdeg,
+                        noff[g], eoff[g]};
+    }
+    const int32_t n = noff[ng];
+    const int64_t m = eoff[ng];
+    Scratch s(ctx);
+    GDesc* d_desc;
+    int32_t* d_noff;
+    int64_t *d_eoff, *d_coff, *d_k;
+    uint8_t** d_outs;
+    unsigned long long* d_cnt;
+    SFG_TRY(s.get(&d_desc, ng));
+    SFG_TRY(s.get(&d_noff, ng + 1));
+    SFG_TRY(s.get(&d_eoff, ng + 1));
+    SFG_TRY(s.get(&d_coff, ng + 1));
+    SFG_TRY(s.get(&d_k, ng));
+    SFG_TRY(s.get(&d_outs, ng));
+    SFG_TRY(s.get(&d_cnt, ng));
+    SFG_CUDA(ctx, cudaMemcpyAsync(d_desc, desc.data(), sizeof(GDesc) * ng, cudaMemcpyHostToDevice, ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(d_noff, noff.data(), 4 * (ng + 1), cudaMemcpyHostToDevice, ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(d_eoff, eoff.data(), 8 * (ng + 1), cudaMemcpyHostToDevice, ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(d_outs, masks_out, sizeof(uint8_t*) * ng, cudaMemcpyHostToDevice, ctx->stream));
+
+    // the disjoint union U
+    GraphGuard U;
+    SFG_TRY(sfg_alloc_graph(ctx, n, m, &U.g));
+    if (m > 0) {
+        k_union_edges<<<grid_of(ctx, k_union_edges, m), kBlock, 0, ctx->stream>>>(
+            m, d_desc, ng, d_eoff, U.g->eu, U.g->ev, U.g->ew);
+        k_union_entries<<<grid_of(ctx, k_union_entries, 2 * m), kBlock, 0, ctx->stream>>>(
+            m, d_desc, ng, d_eoff, U.g->colval, U.g->eid);
+        ctx->launches += 2;
+    }
+    k_union_rows<<<grid_of(ctx, k_union_rows, (int64_t)n + 1), kBlock, 0, ctx->stream>>>(
+        n, m, d_desc, ng, d_noff, U.g->row_ptr, U.g->deg, U.g->invdeg);
+    ++ctx->launches;
+    SFG_LAUNCH_CHECK(ctx, "k_union");
+
+    // spanning forests of every graph, per-graph forest sizes
+    uint8_t* mask;
+    SFG_TRY(s.get(&mask, m));
+    int64_t n_tree = 0;
+    SFG_TRY(sfg_mst_impl(ctx, U.g, nullptr, mask, &n_tree));
+    std::vector<int64_t> tree(ng, 0);
+    SFG_CUDA(ctx, cudaMemsetAsync(d_cnt, 0, 8 * ng, ctx->stream));
+    if (m > 0) {
+        k_seg_count<<<grid_of(ctx, k_seg_count, m), kBlock, 0, ctx->stream>>>(m, mask, ng, d_eoff, d_cnt);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_seg_count");
+    }
+    SFG_CUDA(ctx, cudaMemcpyAsync(tree.data(), d_cnt, 8 * ng, cudaMemcpyDeviceToHost, ctx->stream));
+    SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+
+    // per-graph budgets (each graph's P starts as its forest: no edge is over budget)
+    std::vector<int64_t> kk(ng), coff(ng + 1, 0);
+    int64_t k_total = 0;
+    for (int g = 0; g < ng; ++g) {
+        const int64_t ng_n = noff[g + 1] - noff[g], ng_m = eoff[g + 1] - eoff[g];
+        const int64_t ncand = ng_m - tree[g];
+        const int64_t base = P->budget_unit == 0 ? ng_n : ncand;
+        int64_t k = round_half_up(P->budget_frac * (double)base);
+        if (k < 0) k = 0;
+        if (k > ncand) k = ncand;
+        kk[g] = k;
+        k_total += k;
+        coff[g + 1] = coff[g] + ncand;
+    }
+    const int64_t ncand = coff[ng];
+    SFG_CUDA(ctx, cudaMemcpyAsync(d_coff, coff.data(), 8 * (ng + 1), cudaMemcpyHostToDevice, ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(d_k, kk.data(), 8 * ng, cudaMemcpyHostToDevice, ctx->stream));
+
+    if (k_total > 0) {
+        uint8_t* flag;
+        int64_t* pos;
+        int32_t *cand, *sel;
+        float* scores;
+        SFG_TRY(s.get(&flag, m));
+        SFG_TRY(s.get(&pos, m + 1));
+        SFG_TRY(s.get(&cand, ncand));
+        SFG_TRY(s.get(&scores, ncand));
+        SFG_TRY(s.get(&sel, k_total));
+        k_not<<<grid_of(ctx, k_not, m), kBlock, 0, ctx->stream>>>(m, mask, flag);
+        ++ctx->launches;
+        SFG_TRY(sfg_scan_u8(ctx, flag, pos, m));
+        k_compact<<<grid_of(ctx, k_compact, m), kBlock, 0, ctx->stream>>>(m, flag, pos, cand);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_compact");
+        GraphGuard PU;
+        SFG_TRY(sfg_subgraph_impl(ctx, U.g, mask, &PU.g));
+        SFG_TRY(sfg_filter_score_batched_impl(ctx, U.g, PU.g, ng, d_noff, P->K, P->steps, P->omega,
+                                              P->seed, P->storage, cand, ncand, P->mode, scores));
+        SFG_TRY(sfg_topk_segmented_impl(ctx, scores, cand, ncand, ng, d_coff, d_k, k_total, sel));
+        k_mark<<<grid_of(ctx, k_mark, k_total), kBlock, 0, ctx->stream>>>(k_total, sel, mask);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_mark");
+    }
+    if (m > 0) {
+        k_split<<<grid_of(ctx, k_split, m), kBlock, 0, ctx->stream>>>(m, mask, ng, d_eoff, d_outs);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_split");
+    }
+    if (n_selected_host) {
+        SFG_CUDA(ctx, cudaMemsetAsync(d_cnt, 0, 8 * ng, ctx->stream));
+        if (m > 0) {
+            k_seg_count<<<grid_of(ctx, k_seg_count, m), kBlock, 0, ctx->stream>>>(m, mask, ng, d_eoff, d_cnt);
+            ++ctx->launches;
+            SFG_LAUNCH_CHECK(ctx, "k_seg_count");
+        }
+        SFG_CUDA(ctx, cudaMemcpyAsync(n_selected_host, d_cnt, 8 * ng, cudaMemcpyDeviceToHost, ctx->stream));
+        SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return SFG_OK;
+}

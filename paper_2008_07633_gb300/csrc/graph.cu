@@ -209,7 +209,7 @@ void sfg_graph_free(sfg_graph* g) {
 }
 
 // Allocate the arrays of a graph with n nodes and m canonical edges.
-static sfg_status alloc_graph(sfg_ctx* ctx, int32_t n, int64_t m, sfg_graph** out) {
+sfg_status sfg_alloc_graph(sfg_ctx* ctx, int32_t n, int64_t m, sfg_graph** out) {
     sfg_graph* g = new sfg_graph();
     g->n = n;
     g->m = m;
@@ -293,7 +293,7 @@ sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
         SFG_TRY(sfg_read_i64(ctx, up_off + nnz, &mc));
     }
     sfg_graph* g = nullptr;
-    SFG_TRY(alloc_graph(ctx, n, mc, &g));
+    SFG_TRY(sfg_alloc_graph(ctx, n, mc, &g));
     if (nnz > 0)
         SFG_CUDA(ctx, cudaMemcpyAsync(g->colval, colval_tmp, sizeof(int2) * nnz,
                                       cudaMemcpyDeviceToDevice, ctx->stream));
@@ -350,7 +350,7 @@ sfg_status sfg_subgraph_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* ma
         SFG_CUDA(ctx, cudaMemsetAsync(jscan, 0, sizeof(int64_t), ctx->stream));
     }
     sfg_graph* p = nullptr;
-    SFG_TRY(alloc_graph(ctx, g->n, ms, &p));
+    SFG_TRY(sfg_alloc_graph(ctx, g->n, ms, &p));
     if (g->m > 0) {
         k_sub_edges<<<grid_of(ctx, k_sub_edges, g->m), kBlock, 0, ctx->stream>>>(
             g->eu, g->ev, g->ew, keep_e, escan, g->m, p->eu, p->ev, p->ew); ++ctx->launches;

@@ -26,12 +26,15 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 // consumed, so one gather round is the exposed latency per tile.
 // SCALED: the blocks are raw smoothed blocks and column k of each is multiplied by its projection
 // scale (sg, sp) on the fly; the projection's mean removal cancels in X_p - X_q.
-template <typename T, int LPR, bool SCALED>
+// SCALED = 2: the scales are per graph of a disjoint union (graph g's rows start at node_off[g]),
+// looked up from each edge's first endpoint.
+template <typename T, int LPR, int SCALED>
 __global__ void __launch_bounds__(kBlock)
     k_score(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
             const int32_t* __restrict__ ev, const float* __restrict__ ew,
             const T* __restrict__ XG, const T* __restrict__ XP, int mode, float eta,
-            const float* __restrict__ sg, const float* __restrict__ sp, float* __restrict__ out) {
+            const float* __restrict__ sg, const float* __restrict__ sp,
+            const int32_t* __restrict__ node_off, int ngraphs, float* __restrict__ out) {
     constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR;
     const int lane = threadIdx.x & 31, grp = lane / LPR, sub = lane % LPR;
     const unsigned gm = group_mask<LPR>(lane);
@@ -43,8 +46,8 @@ __global__ void __launch_bounds__(kBlock)
     float scg[E], scp[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) {
-        scg[k] = SCALED ? sg[sub * E + k] : 1.f;
-        scp[k] = SCALED ? sp[sub * E + k] : 1.f;
+        scg[k] = SCALED == 1 ? sg[sub * E + k] : 1.f;
+        scp[k] = SCALED == 1 ? sp[sub * E + k] : 1.f;
     }
     auto load_id = [&](int64_t t) -> int32_t {
         const int64_t i = t * GPW + lane;
@@ -66,6 +69,18 @@ __global__ void __launch_bounds__(kBlock)
         const int64_t p = __shfl_sync(0xffffffffu, cur.p, grp);
         const int64_t q = __shfl_sync(0xffffffffu, cur.q, grp);
         const float w = __shfl_sync(0xffffffffu, cur.w, grp);
+        if (SCALED == 2) {
+            int lo = 0, hi = ngraphs;  // graph of row p
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (node_off[mid] <= p) lo = mid; else hi = mid;
+            }
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                scg[k] = sg[(size_t)lo * K + sub * E + k];
+                scp[k] = sp[(size_t)lo * K + sub * E + k];
+            }
+        }
         float gp[E], gq[E], pp[E], pq[E];
         Vec<T>::load(Xg + p * K, gp);
         Vec<T>::load(Xg + q * K, gq);
@@ -123,16 +138,22 @@ __global__ void k_affinity(int64_t m, const int32_t* __restrict__ eu, const int3
 template <typename T, int LPR>
 sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
                         const int32_t* ids, int64_t ne, int mode, const float* sg,
-                        const float* sp, float* out) {
+                        const float* sp, const int32_t* node_off, int ngraphs, float* out) {
     if (ne == 0) return SFG_OK;
-    const int grid = sfg_grid(ctx, (const void*)k_score<T, LPR, false>, kBlock, 0, ne * LPR);
+    const int grid = sfg_grid(ctx, (const void*)k_score<T, LPR, 0>, kBlock, 0, ne * LPR);
     sfg_tic(ctx, "score");
-    if (sg)
-        k_score<T, LPR, true><<<grid, kBlock, 0, ctx->stream>>>(
-            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp, out);
+    if (node_off)
+        k_score<T, LPR, 2><<<grid, kBlock, 0, ctx->stream>>>(
+            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp,
+            node_off, ngraphs, out);
+    else if (sg)
+        k_score<T, LPR, 1><<<grid, kBlock, 0, ctx->stream>>>(
+            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp,
+            nullptr, 0, out);
     else
-        k_score<T, LPR, false><<<grid, kBlock, 0, ctx->stream>>>(
-            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp, out);
+        k_score<T, LPR, 0><<<grid, kBlock, 0, ctx->stream>>>(
+            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp,
+            nullptr, 0, out);
     ++ctx->launches;
     sfg_toc(ctx);
     SFG_LAUNCH_CHECK(ctx, "k_score");
@@ -141,26 +162,37 @@ sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const
 
 }  // namespace
 
-sfg_status sfg_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
-                          int K, sfg_dtype storage, const int32_t* ids, int64_t ne,
-                          sfg_score_mode mode, float* out, const float* sg, const float* sp) {
+sfg_status sfg_score_batched_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG,
+                                  const void* XP, int K, sfg_dtype storage, const int32_t* ids,
+                                  int64_t ne, sfg_score_mode mode, float* out, const float* sg,
+                                  const float* sp, const int32_t* node_off, int ngraphs) {
+#define SFG_SCORE_CASE(TY, L) \
+    return launch_score<TY, L>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, node_off, ngraphs, out)
     if (storage == SFG_F32) {
         switch (K) {
-            case 4: return launch_score<float, 1>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
-            case 8: return launch_score<float, 2>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
-            case 16: return launch_score<float, 4>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
-            case 32: return launch_score<float, 8>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
-            case 64: return launch_score<float, 16>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
+            case 4: SFG_SCORE_CASE(float, 1);
+            case 8: SFG_SCORE_CASE(float, 2);
+            case 16: SFG_SCORE_CASE(float, 4);
+            case 32: SFG_SCORE_CASE(float, 8);
+            case 64: SFG_SCORE_CASE(float, 16);
         }
     } else if (storage == SFG_BF16) {
         switch (K) {
-            case 8: return launch_score<__nv_bfloat16, 1>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
-            case 16: return launch_score<__nv_bfloat16, 2>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
-            case 32: return launch_score<__nv_bfloat16, 4>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
-            case 64: return launch_score<__nv_bfloat16, 8>(ctx, LG, XG, XP, ids, ne, mode, sg, sp, out);
+            case 8: SFG_SCORE_CASE(__nv_bfloat16, 1);
+            case 16: SFG_SCORE_CASE(__nv_bfloat16, 2);
+            case 32: SFG_SCORE_CASE(__nv_bfloat16, 4);
+            case 64: SFG_SCORE_CASE(__nv_bfloat16, 8);
         }
     }
+#undef SFG_SCORE_CASE
     return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", K, (int)storage);
+}
+
+sfg_status sfg_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
+                          int K, sfg_dtype storage, const int32_t* ids, int64_t ne,
+                          sfg_score_mode mode, float* out, const float* sg, const float* sp) {
+    return sfg_score_batched_impl(ctx, LG, XG, XP, K, storage, ids, ne, mode, out, sg, sp, nullptr,
+                                  0);
 }
 
 sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,

@@ -148,3 +148,138 @@ extern "C" sfg_status sfg_select_topk(sfg_ctx* ctx, const float* scores, const i
     SFG_TRY(sfg_check_dev(ctx, ids_out, "ids_out"));
     return sfg_topk_impl(ctx, scores, ids, ne, k, ids_out);
 }
+
+// ------------------------------------------------------------------------------------------------
+// Segmented top-k (one selection per graph of a batch): the same MSB-first radix select, with one
+// histogram and one (prefix, remaining k) state per segment. Candidates are contiguous per
+// segment; each lane finds its segment by a binary search seeded once per warp.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+struct SegSel {
+    unsigned long long prefix;
+    long long krem;
+};
+
+__device__ __forceinline__ int seg_of(const int64_t* __restrict__ off, int nseg, int64_t i) {
+    int lo = 0, hi = nseg;  // last s with off[s] <= i
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_segsel_init(int nseg, const int64_t* __restrict__ k, SegSel* __restrict__ st,
+                              unsigned long long* __restrict__ hist) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)nseg * 256;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        hist[i] = 0ull;
+        if ((i & 255) == 0) st[i >> 8] = SegSel{0ull, (long long)k[i >> 8]};
+    }
+}
+
+__global__ void __launch_bounds__(kBlock)
+    k_segsel_hist(int64_t ne, const float* __restrict__ scores, const int32_t* __restrict__ ids,
+                  int nseg, const int64_t* __restrict__ off, const SegSel* __restrict__ st,
+                  int shift, unsigned long long* __restrict__ hist) {
+    const int hi = shift + 8;
+    for (int64_t base = (int64_t)blockIdx.x * kBlock + (threadIdx.x & ~31); base < ne;
+         base += (int64_t)gridDim.x * kBlock) {
+        const int64_t i = base + (threadIdx.x & 31);
+        int s = seg_of(off, nseg, base);
+        bool take = false;
+        int digit = 0;
+        if (i < ne) {
+            while (off[s + 1] <= i) ++s;
+            const SegSel ss = st[s];
+            const uint64_t key = sel_key(scores[i], ids[i]);
+            take = ss.krem > 0 && (hi >= 64 || (key >> hi) == (ss.prefix >> hi));
+            digit = (int)((key >> shift) & 0xff);
+        }
+        const unsigned bin = take ? (unsigned)s * 256u + (unsigned)digit : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        if (take && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
+            atomicAdd(&hist[bin], (unsigned long long)__popc(peers));
+    }
+}
+
+// one CTA of 256 threads per segment (see k_sel_pick)
+__global__ void k_segsel_pick(int shift, SegSel* __restrict__ st, unsigned long long* __restrict__ hist) {
+    __shared__ long long suf[256];
+    const int sgi = blockIdx.x;
+    unsigned long long* h = hist + (size_t)sgi * 256;
+    const long long krem = st[sgi].krem;
+    const int d = 255 - (int)threadIdx.x;
+    const long long c = (long long)h[d];
+    suf[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        const long long v = threadIdx.x >= o ? suf[threadIdx.x - o] : 0;
+        __syncthreads();
+        suf[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const long long incl = suf[threadIdx.x], above = incl - c;
+    const bool pick = krem > 0 && ((above < krem && incl >= krem) || (d == 0 && incl < krem));
+    __syncthreads();
+    if (pick) {
+        st[sgi].prefix |= (unsigned long long)d << shift;
+        st[sgi].krem = krem - above;
+    }
+    h[d] = 0ull;
+}
+
+__global__ void k_segsel_flags(int64_t ne, const float* __restrict__ scores,
+                               const int32_t* __restrict__ ids, int nseg,
+                               const int64_t* __restrict__ off, const SegSel* __restrict__ st,
+                               const int64_t* __restrict__ k, uint8_t* __restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < ne;
+         i += (int64_t)gridDim.x * kBlock) {
+        const int s = seg_of(off, nseg, i);
+        flag[i] = k[s] > 0 && sel_key(scores[i], ids[i]) >= st[s].prefix;
+    }
+}
+
+__global__ void k_segsel_emit(int64_t ne, const int32_t* __restrict__ ids,
+                              const uint8_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                              int32_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < ne;
+         i += (int64_t)gridDim.x * kBlock)
+        if (flag[i]) out[pos[i]] = ids[i];
+}
+
+}  // namespace
+
+sfg_status sfg_topk_segmented_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids,
+                                   int64_t ne, int nseg, const int64_t* seg_off,
+                                   const int64_t* k_dev, int64_t k_total, int32_t* out) {
+    if (k_total == 0 || ne == 0) return SFG_OK;
+    Scratch s(ctx);
+    SegSel* st;
+    unsigned long long* hist;
+    uint8_t* flag;
+    int64_t* pos;
+    SFG_TRY(s.get(&st, nseg));
+    SFG_TRY(s.get(&hist, (size_t)nseg * 256));
+    SFG_TRY(s.get(&flag, ne));
+    SFG_TRY(s.get(&pos, ne + 1));
+    const int grid = sfg_grid(ctx, (const void*)k_segsel_hist, kBlock, 0, ne);
+    sfg_tic(ctx, "topk");
+    k_segsel_init<<<ceil_div_u((int64_t)nseg * 256, kBlock), kBlock, 0, ctx->stream>>>(nseg, k_dev, st, hist);
+    ++ctx->launches;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        k_segsel_hist<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, nseg, seg_off, st, shift, hist);
+        k_segsel_pick<<<nseg, 256, 0, ctx->stream>>>(shift, st, hist);
+        ctx->launches += 2;
+    }
+    k_segsel_flags<<<grid, kBlock, 0, ctx->stream>>>(ne, scores, ids, nseg, seg_off, st, k_dev, flag);
+    ++ctx->launches;
+    sfg_toc(ctx);
+    SFG_LAUNCH_CHECK(ctx, "k_segsel");
+    SFG_TRY(sfg_scan_u8(ctx, flag, pos, ne));
+    k_segsel_emit<<<grid, kBlock, 0, ctx->stream>>>(ne, ids, flag, pos, out);
+    ++ctx->launches;
+    SFG_LAUNCH_CHECK(ctx, "k_segsel_emit");
+    return SFG_OK;
+}

@@ -141,6 +141,20 @@ sfg_status sfg_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, con
                           int K, sfg_dtype storage, const int32_t* ids, int64_t ne,
                           sfg_score_mode mode, float* out, const float* sg = nullptr,
                           const float* sp = nullptr);
+sfg_status sfg_score_batched_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG,
+                                  const void* XP, int K, sfg_dtype storage, const int32_t* ids,
+                                  int64_t ne, sfg_score_mode mode, float* out, const float* sg,
+                                  const float* sp, const int32_t* node_off, int ngraphs);
+sfg_status sfg_filter_score_batched_impl(sfg_ctx* ctx, const sfg_graph* U, const sfg_graph* PU,
+                                         int ng, const int32_t* node_off, int K, int steps,
+                                         double omega, uint64_t seed, sfg_dtype storage,
+                                         const int32_t* ids, int64_t ne, sfg_score_mode mode,
+                                         float* scores);
+// Top-k per segment: candidates [seg_off[s], seg_off[s+1]) of segment s keep their k_dev[s]
+// largest; the chosen ids of all segments are written in ascending order (out has sum k entries).
+sfg_status sfg_topk_segmented_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids,
+                                   int64_t ne, int nseg, const int64_t* seg_off,
+                                   const int64_t* k_dev, int64_t k_total, int32_t* out);
 sfg_status sfg_filter_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
                                  int steps, double omega, uint64_t seed, sfg_dtype storage,
                                  const int32_t* ids, int64_t ne, sfg_score_mode mode,
@@ -153,6 +167,8 @@ sfg_status sfg_backward_impl(sfg_ctx* ctx, const sfg_graph* fine, const int32_t*
                              const int32_t* f2c, const sfg_graph* coarse, const uint8_t* pmask_c,
                              uint8_t* pmask_f);
 void sfg_graph_free(sfg_graph* g);
+// Device arrays of a graph with n nodes and m canonical edges (contents unset).
+sfg_status sfg_alloc_graph(sfg_ctx* ctx, int32_t n, int64_t m, sfg_graph** out);
 bool sfg_k_supported(int K, sfg_dtype dt);
 
 // splitmix64 (Steele, Lea & Flood 2014), host and device.

@@ -80,9 +80,15 @@ __device__ __forceinline__ void block_column_partials(float (&s1)[E], float (&s2
     }
 }
 
-template <typename T, int LPR>
-__global__ void __launch_bounds__(kBlock) k_init(int32_t n, uint64_t seed, T* __restrict__ X,
-                                                 double* __restrict__ part) {
+// Seeded block. WEIGHTED = false: partials are the plain column sums and sums of squares (the
+// projection statistics when no sweep follows). WEIGHTED = true: partials are sum_i d_i x_ik and
+// sum_i d_i, i.e. the D-weighted column means that the first sweep removes. Jacobi sweeps keep
+// the D-weighted mean and damp everything else, so removing it (rather than the plain mean) keeps
+// the block free of a constant that the final projection would otherwise have to cancel in FP32;
+// the two choices differ by a constant vector only, which the projection removes either way.
+template <typename T, int LPR, bool WEIGHTED>
+__global__ void __launch_bounds__(kBlock) k_init(int32_t n, uint64_t seed, const double* __restrict__ deg,
+                                                 T* __restrict__ X, double* __restrict__ part) {
     constexpr int E = Vec<T>::E, K = LPR * E;
     const int lane = threadIdx.x & 31, sub = lane % LPR;
     const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
@@ -98,11 +104,17 @@ __global__ void __launch_bounds__(kBlock) k_init(int32_t n, uint64_t seed, T* __
             const uint64_t j = (uint64_t)row * K + sub * E + e;  // even
             gaussian_pair(s0, j >> 1, x[e], x[e + 1]);
         }
+        const float d = WEIGHTED ? (float)deg[row] : 1.f;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             x[e] = Vec<T>::round(x[e]);
-            s1[e] += x[e];
-            s2[e] = fmaf(x[e], x[e], s2[e]);
+            if (WEIGHTED) {
+                s1[e] = fmaf(d, x[e], s1[e]);
+                s2[e] += d;
+            } else {
+                s1[e] += x[e];
+                s2[e] = fmaf(x[e], x[e], s2[e]);
+            }
         }
         Vec<T>::store(X + row * K + sub * E, x);
     }
@@ -282,7 +294,7 @@ __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
 // Fold the per-block partials (FP64): one CTA per column, each thread sums a fixed stride of
 // blocks, then a fixed-shape tree, so the result does not depend on scheduling.
 // proj = 0: mean only (mu = S1 / n). proj = 1: mean and scale = 1 / RMS of the centred column
-// (1 if the column is zero).
+// (1 if the column is zero). proj = 2: D-weighted mean S1 / S2 of k_init<WEIGHTED>.
 __global__ void __launch_bounds__(kBlock) k_finalize(const double* __restrict__ part, int nblocks,
                                                      int K, int32_t n, int proj,
                                                      float* __restrict__ mean,
@@ -305,6 +317,10 @@ __global__ void __launch_bounds__(kBlock) k_finalize(const double* __restrict__ 
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        if (proj == 2) {  // D-weighted mean: sum d x / sum d
+            mean[k] = r2[0] > 0.0 ? (float)(r1[0] / r2[0]) : 0.f;
+            return;
+        }
         const double mu = r1[0] / (double)n;
         mean[k] = (float)mu;
         if (proj) {
@@ -339,6 +355,150 @@ __global__ void k_coef(int32_t n, const double* __restrict__ invdeg, double omeg
     for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * kBlock)
         coef[p] = (float)(omega * invdeg[p]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Batched embedding of a disjoint union of graphs (rows of graph g are [node_off[g],
+// node_off[g+1]) ). Sweeps need nothing per graph; the seeded block, its mean removal and the
+// projection statistics are per graph, so every graph gets exactly the block and statistics it
+// would get alone (up to FP32 summation order).
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ int32_t graph_of(const int32_t* __restrict__ off, int ng, int64_t r) {
+    int lo = 0, hi = ng;  // last g with off[g] <= r
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= r) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kBlock) k_init_batched(int32_t n, uint64_t seed,
+                                                         const int32_t* __restrict__ node_off,
+                                                         int ng, T* __restrict__ X) {
+    constexpr int E = Vec<T>::E, K = LPR * E;
+    const int lane = threadIdx.x & 31, sub = lane % LPR;
+    const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
+    const int64_t ng_ = (int64_t)gridDim.x * kBlock / LPR;
+    const uint64_t s0 = sfg_splitmix64(seed);
+    for (int64_t row = g0; row < n; row += ng_) {
+        const int64_t local = row - node_off[graph_of(node_off, ng, row)];
+        float x[E];
+#pragma unroll
+        for (int e = 0; e < E; e += 2) {
+            const uint64_t j = (uint64_t)local * K + sub * E + e;
+            gaussian_pair(s0, j >> 1, x[e], x[e + 1]);
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = Vec<T>::round(x[e]);
+        Vec<T>::store(X + row * K + sub * E, x);
+    }
+}
+
+// Per-graph column sums and sums of squares (FP64) of X: one CTA per graph; each LPR-lane group
+// folds 64-row chunks in FP32 into FP64, then a fixed-shape tree across the CTA.
+// deg != NULL: sums of d_i x_ik and of d_i instead (the D-weighted means, see k_init).
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kBlock) k_seg_stats(const T* __restrict__ X,
+                                                      const int32_t* __restrict__ node_off,
+                                                      const double* __restrict__ deg,
+                                                      double* __restrict__ stats) {
+    constexpr int E = Vec<T>::E, K = LPR * E, GPB = kBlock / LPR;
+    __shared__ double red[kBlock / 32][2 * K];
+    const int g = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane % LPR;
+    const int64_t r0 = node_off[g], r1 = node_off[g + 1];
+    double d1[E], d2[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) d1[e] = d2[e] = 0.0;
+    for (int64_t base = r0 + threadIdx.x / LPR; base < r1; base += (int64_t)GPB * 64) {
+        float f1[E], f2[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) f1[e] = f2[e] = 0.f;
+        for (int i = 0; i < 64; ++i) {
+            const int64_t r = base + (int64_t)i * GPB;
+            if (r >= r1) break;
+            float x[E];
+            Vec<T>::load(X + r * K + sub * E, x);
+            const float d = deg ? (float)deg[r] : 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (deg) {
+                    f1[e] = fmaf(d, x[e], f1[e]);
+                    f2[e] += d;
+                } else {
+                    f1[e] += x[e];
+                    f2[e] = fmaf(x[e], x[e], f2[e]);
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            d1[e] += f1[e];
+            d2[e] += f2[e];
+        }
+    }
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            d1[e] += __shfl_xor_sync(0xffffffffu, d1[e], o);
+            d2[e] += __shfl_xor_sync(0xffffffffu, d2[e], o);
+        }
+    if (lane < LPR)
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            red[warp][sub * E + e] = d1[e];
+            red[warp][K + sub * E + e] = d2[e];
+        }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * K; t += kBlock) {
+        double acc = 0.0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) acc += red[w][t];
+        stats[(size_t)g * 2 * K + t] = acc;
+    }
+}
+
+// mean[g][k], scale[g][k] (scale = 1 / RMS of the centred column, 1 if zero) from the stats.
+// weighted: mean = s1 / s2 of k_seg_stats with degrees (no scale).
+__global__ void k_seg_finalize(const double* __restrict__ stats, const int32_t* __restrict__ node_off,
+                               int ng, int K, int weighted, float* __restrict__ mean,
+                               float* __restrict__ scale) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ng * K) return;
+    const int g = (int)(i / K), k = (int)(i % K);
+    const double n = (double)(node_off[g + 1] - node_off[g]);
+    const double s1 = stats[(size_t)g * 2 * K + k], s2 = stats[(size_t)g * 2 * K + K + k];
+    if (weighted) {
+        mean[i] = s2 > 0.0 ? (float)(s1 / s2) : 0.f;
+        return;
+    }
+    const double mu = n > 0 ? s1 / n : 0.0;
+    mean[i] = (float)mu;
+    if (scale) {
+        const double var = n > 0 ? s2 / n - mu * mu : 0.0;
+        const double rms = var > 0.0 ? sqrt(var) : 0.0;
+        scale[i] = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
+    }
+}
+
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kBlock) k_center_batched(int32_t n, const int32_t* __restrict__ node_off,
+                                                           int ng, const float* __restrict__ mean,
+                                                           T* __restrict__ X) {
+    constexpr int E = Vec<T>::E, K = LPR * E;
+    const int lane = threadIdx.x & 31, sub = lane % LPR;
+    const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
+    const int64_t ng_ = (int64_t)gridDim.x * kBlock / LPR;
+    for (int64_t row = g0; row < n; row += ng_) {
+        const int g = graph_of(node_off, ng, row);
+        float x[E];
+        Vec<T>::load(X + row * K + sub * E, x);
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] -= mean[(size_t)g * K + sub * E + e];
+        Vec<T>::store(X + row * K + sub * E, x);
+    }
 }
 
 template <typename T, int LPR>
@@ -389,10 +549,14 @@ struct Smoother {
         T* cur = (steps % 2 == 0) ? buf : X_out;
         T* nxt = (cur == buf) ? X_out : buf;
         sfg_tic(ctx, "init");
-        k_init<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, seed, cur, part); ++ctx->launches;
+        if (steps == 0)
+            k_init<T, LPR, false><<<grid, kBlock, 0, ctx->stream>>>(n, seed, L->deg, cur, part);
+        else
+            k_init<T, LPR, true><<<grid, kBlock, 0, ctx->stream>>>(n, seed, L->deg, cur, part);
+        ++ctx->launches;
         sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_init");
-        k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 0, mu, scale); ++ctx->launches;
+        k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 2, mu, scale); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_finalize");
         for (int t = 1; t <= steps; ++t) {
             SFG_TRY(sweep(ctx, L, coef, (float)(1.0 - omega), cur, nxt, mu, part, t == 1,
@@ -465,12 +629,17 @@ struct Smoother {
         SFG_TRY(s.get(&sp, K));
         SFG_TRY(s.get(&part, (size_t)grid * 2 * K));
         sfg_tic(ctx, "init");
-        k_init<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, seed, x0, part);
+        // the D-weighted mean is taken on L_G; L_P has the same nodes, and any constant left in
+        // the block is removed by the projection in exact arithmetic
+        if (steps == 0)
+            k_init<T, LPR, false><<<grid, kBlock, 0, ctx->stream>>>(n, seed, LG->deg, x0, part);
+        else
+            k_init<T, LPR, true><<<grid, kBlock, 0, ctx->stream>>>(n, seed, LG->deg, x0, part);
         ++ctx->launches;
         sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_init");
         // steps == 0: the projection statistics of both blocks are those of x0
-        k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 0, mu, mu_scale);
+        k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, steps == 0 ? 1 : 2, mu, mu_scale);
         ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_finalize");
         const T *xg = x0, *xp = x0;
@@ -479,6 +648,66 @@ struct Smoother {
         if (steps == 0) sg = sp = mu_scale;
         return sfg_score_impl(ctx, LG, xg, xp, K, Vec<T>::E == 4 ? SFG_F32 : SFG_BF16, ids, ne,
                               mode, scores, sg, sp);
+    }
+
+    // Batched filter + score over a disjoint union (U, PU) of ng graphs (node_off on the device,
+    // ng + 1 entries): per-graph seeded blocks, means and projection scales; one launch per sweep
+    // for all graphs.
+    static sfg_status filter_score_batched(sfg_ctx* ctx, const sfg_graph* U, const sfg_graph* PU,
+                                           int ng, const int32_t* node_off, int steps,
+                                           double omega, uint64_t seed, const int32_t* ids,
+                                           int64_t ne, sfg_score_mode mode, float* scores) {
+        const int32_t n = U->n;
+        const int grid = grid_jacobi(ctx, n);
+        Scratch s(ctx);
+        T *x0, *g0, *g1, *p0, *p1;
+        float *coef, *mean, *sg, *sp;
+        double* stats;
+        SFG_TRY(s.get(&x0, (size_t)n * K));
+        SFG_TRY(s.get(&g0, (size_t)n * K));
+        SFG_TRY(s.get(&g1, (size_t)n * K));
+        SFG_TRY(s.get(&p0, (size_t)n * K));
+        SFG_TRY(s.get(&p1, (size_t)n * K));
+        SFG_TRY(s.get(&coef, (size_t)n));
+        SFG_TRY(s.get(&mean, (size_t)ng * K));
+        SFG_TRY(s.get(&sg, (size_t)ng * K));
+        SFG_TRY(s.get(&sp, (size_t)ng * K));
+        SFG_TRY(s.get(&stats, (size_t)ng * 2 * K));
+        const unsigned fin_grid = ceil_div_u((int64_t)ng * K, kBlock);
+        k_init_batched<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, seed, node_off, ng, x0);
+        const bool weighted = steps > 0;
+        k_seg_stats<T, LPR><<<ng, kBlock, 0, ctx->stream>>>(x0, node_off, weighted ? U->deg : nullptr,
+                                                             stats);
+        k_seg_finalize<<<fin_grid, kBlock, 0, ctx->stream>>>(stats, node_off, ng, K, weighted ? 1 : 0,
+                                                             mean, nullptr);
+        k_center_batched<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, node_off, ng, mean, x0);
+        ctx->launches += 4;
+        SFG_LAUNCH_CHECK(ctx, "k_init_batched");
+        const T* xr[2] = {x0, x0};
+        const sfg_graph* L[2] = {U, PU};
+        T* buf[2][2] = {{g0, g1}, {p0, p1}};
+        float* sc[2] = {sg, sp};
+        for (int w = 0; w < 2; ++w) {
+            k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
+                n, L[w]->invdeg, omega, coef);
+            ++ctx->launches;
+            SFG_LAUNCH_CHECK(ctx, "k_coef");
+            const T* cur = x0;
+            T* nxt = buf[w][0];
+            for (int t = 1; t <= steps; ++t) {
+                SFG_TRY(sweep(ctx, L[w], coef, (float)(1.0 - omega), cur, nxt, nullptr, nullptr,
+                              false, false, grid));
+                cur = nxt;
+                nxt = (nxt == buf[w][0]) ? buf[w][1] : buf[w][0];
+            }
+            xr[w] = cur;
+            k_seg_stats<T, LPR><<<ng, kBlock, 0, ctx->stream>>>(cur, node_off, nullptr, stats);
+            k_seg_finalize<<<fin_grid, kBlock, 0, ctx->stream>>>(stats, node_off, ng, K, 0, mean, sc[w]);
+            ctx->launches += 2;
+            SFG_LAUNCH_CHECK(ctx, "k_seg_stats");
+        }
+        return sfg_score_batched_impl(ctx, U, xr[0], xr[1], K, Vec<T>::E == 4 ? SFG_F32 : SFG_BF16,
+                                      ids, ne, mode, scores, sg, sp, node_off, ng);
     }
 
     static sfg_status jacobi(sfg_ctx* ctx, const sfg_graph* L, int steps, double omega, T* X) {
@@ -550,6 +779,18 @@ sfg_status sfg_filter_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_gr
     return dispatch(K, storage, [&](auto S) {
         using Sm = decltype(S);
         return Sm::filter_score(ctx, LG, LP, steps, omega, seed, ids, ne, mode, scores);
+    });
+}
+
+sfg_status sfg_filter_score_batched_impl(sfg_ctx* ctx, const sfg_graph* U, const sfg_graph* PU,
+                                         int ng, const int32_t* node_off, int K, int steps,
+                                         double omega, uint64_t seed, sfg_dtype storage,
+                                         const int32_t* ids, int64_t ne, sfg_score_mode mode,
+                                         float* scores) {
+    return dispatch(K, storage, [&](auto S) {
+        using Sm = decltype(S);
+        return Sm::filter_score_batched(ctx, U, PU, ng, node_off, steps, omega, seed, ids, ne,
+                                        mode, scores);
     });
 }
 

@@ -24,7 +24,7 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_
            "sfg_ctx_timing", "sfg_ctx_kernel_time", "sfg_ctx_launches", "sfg_laplacian", "sfg_graph_destroy",
            "sfg_graph_info", "sfg_graph_edges", "sfg_graph_csr", "sfg_graph_subgraph", "sfg_smooth",
            "sfg_jacobi", "sfg_score_edges", "sfg_select_topk", "sfg_spanning_tree", "sfg_affinity",
-           "sfg_affinity_noalloc", "sfg_filter_score",
+           "sfg_affinity_noalloc", "sfg_filter_score", "sfg_sparsify_batched",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify"]
 
 
@@ -79,6 +79,8 @@ def lib():
             "sfg_coarsen": [_vp, _vp, _vp, _int, _vp, _vp, _pi32, ctypes.POINTER(_vp)],
             "sfg_backward_map": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
             "sfg_sparsify": [_vp, _vp, ctypes.POINTER(sfg_params), _vp, _pi64],
+            "sfg_sparsify_batched": [_vp, _int, ctypes.POINTER(_vp), ctypes.POINTER(sfg_params),
+                                     ctypes.POINTER(_vp), _pi64],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -317,3 +319,17 @@ def sfg_sparsify(ctx, g, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=SFG_SC
     ns = _i64()
     ctx.check(lib().sfg_sparsify(ctx.h, g.h, ctypes.byref(p), _ptr(out), ctypes.byref(ns)))
     return out, ns.value
+
+
+def sfg_sparsify_batched(ctx, graphs, K=16, steps=15, omega=0.7, seed=0, mode=SFG_SCORE_RATIO,
+                         budget_frac=0.05, budget_unit=0, storage=torch.float32):
+    """Flat sparsification of a list of graphs in one batch; returns (masks, counts)."""
+    ng = len(graphs)
+    p = sfg_params(K, steps, 0, omega, seed & (2**64 - 1), mode, budget_frac, budget_unit,
+                   _dt(storage))
+    masks = [torch.empty(max(g.m, 1), dtype=torch.uint8, device=ctx.device) for g in graphs]
+    hs = (_vp * ng)(*[g.h for g in graphs])
+    outs = (_vp * ng)(*[m.data_ptr() for m in masks])
+    counts = (ctypes.c_int64 * ng)()
+    ctx.check(lib().sfg_sparsify_batched(ctx.h, ng, hs, ctypes.byref(p), outs, counts))
+    return [m[:g.m] for m, g in zip(masks, graphs)], list(counts)
