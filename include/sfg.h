@@ -254,6 +254,55 @@ SFG_API sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* c
                                         const sfg_params* params, uint8_t* const* masks_out,
                                         int64_t* n_selected_host);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned edge proposals (an addition to the paper's method; the paper has no learned part).
+ * A small network predicts each candidate edge's score after `steps` sweeps from features of a
+ * much shorter embedding; its best guesses are rescored by the plain method, which therefore
+ * stays both the fallback and the judge.
+ * Features (16 per edge, FP32, row-major), for e = (p, q) with weighted degree d, neighbour count
+ * deg and the projected-embedding distances s_G, s_P of sfg_score_edges (modes G and P) after
+ * `steps` sweeps from `seed`: ln w, ln d_p + ln d_q, |ln d_p - ln d_q|, ln(s_G + 1e-30),
+ * ln(s_P + 1e-30), ln(s_P + 1e-30) - ln(s_G + 1e-30), ln(deg_p deg_q), ln(s_G + s_P + 1e-30), 0 x 8.
+ * Network: 16 -> 64 -> 64 -> 1 with ReLU, BF16 operands on tensor cores, FP32 accumulation and
+ * FP32 master parameters, flat in the order W1 [16][64] (in x out), b1 [64], W2 [64][64], b2,
+ * w3 [64], b3: SFG_MLP_NPARAM values. Loss: mean squared error. Training: Adam (beta 0.9,
+ * 0.999, eps 1e-8) over consecutive minibatches; gradients are deterministic.
+ * Initial weights: Kaiming-uniform, weight j = (2u - 1) sqrt(6 / fan_in) with
+ * u = (splitmix64(splitmix64(seed) + j * 0x9E3779B97F4A7C15) >> 11) 2^-53; biases 0.
+ * ------------------------------------------------------------------------------------------- */
+#define SFG_MLP_NPARAM 5313
+#define SFG_MLP_NFEAT 16
+typedef struct sfg_mlp sfg_mlp;
+SFG_API sfg_status sfg_mlp_create(sfg_ctx* ctx, uint64_t seed, sfg_mlp** out);
+SFG_API void sfg_mlp_destroy(sfg_mlp* net);
+/* Copy the FP32 parameters out / in (set also clears the Adam state). */
+SFG_API sfg_status sfg_mlp_params(sfg_ctx* ctx, const sfg_mlp* net, float* theta_out);
+SFG_API sfg_status sfg_mlp_set_params(sfg_ctx* ctx, sfg_mlp* net, const float* theta);
+/* out[i] = network output for feature row i (ne rows). */
+SFG_API sfg_status sfg_mlp_forward(sfg_ctx* ctx, const sfg_mlp* net, const float* feats,
+                                   int64_t ne, float* out);
+/* Gradient of mean((y - targets)^2) over the ne rows (grad_out: SFG_MLP_NPARAM FP32, may be
+ * NULL); loss_host (may be NULL) receives the loss and synchronises. */
+SFG_API sfg_status sfg_mlp_gradient(sfg_ctx* ctx, sfg_mlp* net, const float* feats,
+                                    const float* targets, int64_t ne, float* grad_out,
+                                    double* loss_host);
+/* `epochs` passes of Adam steps over consecutive minibatches of `batch` rows; loss_host (may be
+ * NULL) receives the final full-data loss and synchronises. */
+SFG_API sfg_status sfg_mlp_train(sfg_ctx* ctx, sfg_mlp* net, const float* feats,
+                                 const float* targets, int64_t ne, int64_t batch, int epochs,
+                                 double lr, double* loss_host);
+/* Feature rows (ne x 16) of the listed edges of LG (see above); LP: the current sparsifier. */
+SFG_API sfg_status sfg_edge_features(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
+                                     int steps, double omega, uint64_t seed, sfg_dtype storage,
+                                     const int32_t* edge_ids, int64_t ne, float* feats_out);
+/* Flat method with learned proposals: spanning forest; features of every off-tree edge from a
+ * feat_steps embedding; the network's top round(propose_frac * candidates) edges (at least the
+ * budget k) are rescored by sfg_filter_score with params->steps and the top k of them are added.
+ * net == NULL or propose_frac >= 1 gives the plain flat method. params->levels must be 0. */
+SFG_API sfg_status sfg_sparsify_learned(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* params,
+                                        const sfg_mlp* net, int feat_steps, double propose_frac,
+                                        uint8_t* mask_out, int64_t* n_selected_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -155,6 +156,12 @@ sfg_status sfg_filter_score_batched_impl(sfg_ctx* ctx, const sfg_graph* U, const
 sfg_status sfg_topk_segmented_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids,
                                    int64_t ne, int nseg, const int64_t* seg_off,
                                    const int64_t* k_dev, int64_t k_total, int32_t* out);
+typedef struct sfg_mlp sfg_mlp;
+sfg_status sfg_mlp_forward_impl(sfg_ctx* ctx, const sfg_mlp* net, const float* feats, int64_t ne,
+                                float* out);
+sfg_status sfg_edge_features_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
+                                  int steps, double omega, uint64_t seed, sfg_dtype storage,
+                                  const int32_t* ids, int64_t ne, float* feats);
 sfg_status sfg_filter_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
                                  int steps, double omega, uint64_t seed, sfg_dtype storage,
                                  const int32_t* ids, int64_t ne, sfg_score_mode mode,

@@ -181,3 +181,68 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
     if (n_selected_host) SFG_TRY(sfg_count_mask(ctx, mask_out, G->m, n_selected_host));
     return SFG_OK;
 }
+
+extern "C" sfg_status sfg_sparsify_learned(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* P,
+                                           const sfg_mlp* net, int feat_steps, double propose_frac,
+                                           uint8_t* mask_out, int64_t* n_selected_host) {
+    if (!ctx) return SFG_EINVAL;
+    if (!G || !P) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
+    if (P->levels != 0) return sfg_fail(ctx, SFG_EUNSUPPORTED, "learned proposals are flat (levels = 0)");
+    if (!net || !(propose_frac < 1.0)) return sfg_sparsify(ctx, G, P, mask_out, n_selected_host);
+    if (!sfg_k_supported(P->K, P->storage))
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K, (int)P->storage);
+    if (feat_steps < 0 || !(propose_frac > 0.0) || P->steps < 0 || !(P->omega > 0.0 && P->omega <= 1.0) ||
+        !(P->budget_frac >= 0.0) || (P->budget_unit != 0 && P->budget_unit != 1) ||
+        (P->mode != SFG_SCORE_RATIO && P->mode != SFG_SCORE_G && P->mode != SFG_SCORE_P))
+        return sfg_fail(ctx, SFG_EINVAL, "invalid arguments");
+    if (G->m > 0) SFG_TRY(sfg_check_dev(ctx, mask_out, "mask_out"));
+    const int64_t m = G->m;
+    int64_t n_tree = 0;
+    SFG_TRY(sfg_mst_impl(ctx, G, nullptr, mask_out, &n_tree));
+    const int64_t ncand = m - n_tree;
+    const int64_t base = P->budget_unit == 0 ? (int64_t)G->n : ncand;
+    int64_t k = round_half_up(P->budget_frac * (double)base);
+    if (k < 0) k = 0;
+    if (k > ncand) k = ncand;
+    if (k > 0) {
+        int64_t nprop = round_half_up(propose_frac * (double)ncand);
+        if (nprop < k) nprop = k;
+        if (nprop > ncand) nprop = ncand;
+        Scratch s(ctx);
+        uint8_t* flag;
+        int64_t* pos;
+        int32_t *cand, *prop, *sel;
+        float *feats, *pred, *scores;
+        SFG_TRY(s.get(&flag, m));
+        SFG_TRY(s.get(&pos, m + 1));
+        SFG_TRY(s.get(&cand, ncand));
+        SFG_TRY(s.get(&feats, (size_t)ncand * SFG_MLP_NFEAT));
+        SFG_TRY(s.get(&pred, ncand));
+        SFG_TRY(s.get(&prop, nprop));
+        SFG_TRY(s.get(&scores, nprop));
+        SFG_TRY(s.get(&sel, k));
+        const int gm = sfg_grid(ctx, (const void*)k_not_mask, kBlock, 0, m);
+        k_not_mask<<<gm, kBlock, 0, ctx->stream>>>(m, mask_out, flag);
+        ++ctx->launches;
+        SFG_TRY(sfg_scan_u8(ctx, flag, pos, m));
+        k_compact_ids<<<gm, kBlock, 0, ctx->stream>>>(m, flag, pos, cand);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_compact_ids");
+        sfg_graph* pg = nullptr;
+        SFG_TRY(sfg_subgraph_impl(ctx, G, mask_out, &pg));
+        struct Guard { sfg_graph* g; ~Guard() { sfg_graph_free(g); } } guard{pg};
+        SFG_TRY(sfg_edge_features_impl(ctx, G, pg, P->K, feat_steps, P->omega, P->seed, P->storage,
+                                       cand, ncand, feats));
+        SFG_TRY(sfg_mlp_forward_impl(ctx, net, feats, ncand, pred));
+        SFG_TRY(sfg_topk_impl(ctx, pred, cand, ncand, nprop, prop));
+        SFG_TRY(sfg_filter_score_impl(ctx, G, pg, P->K, P->steps, P->omega, P->seed, P->storage,
+                                      prop, nprop, P->mode, scores));
+        SFG_TRY(sfg_topk_impl(ctx, scores, prop, nprop, k, sel));
+        k_set_mask<<<sfg_grid(ctx, (const void*)k_set_mask, kBlock, 0, k), kBlock, 0, ctx->stream>>>(
+            k, sel, mask_out);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_set_mask");
+    }
+    if (n_selected_host) SFG_TRY(sfg_count_mask(ctx, mask_out, m, n_selected_host));
+    return SFG_OK;
+}

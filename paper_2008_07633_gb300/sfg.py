@@ -24,7 +24,9 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_
            "sfg_ctx_timing", "sfg_ctx_kernel_time", "sfg_ctx_launches", "sfg_laplacian", "sfg_graph_destroy",
            "sfg_graph_info", "sfg_graph_edges", "sfg_graph_csr", "sfg_graph_subgraph", "sfg_smooth",
            "sfg_jacobi", "sfg_score_edges", "sfg_select_topk", "sfg_spanning_tree", "sfg_affinity",
-           "sfg_affinity_noalloc", "sfg_filter_score", "sfg_sparsify_batched",
+           "sfg_affinity_noalloc", "sfg_filter_score", "sfg_sparsify_batched", "sfg_mlp_create",
+           "sfg_mlp_destroy", "sfg_mlp_params", "sfg_mlp_set_params", "sfg_mlp_forward",
+           "sfg_mlp_gradient", "sfg_mlp_train", "sfg_edge_features", "sfg_sparsify_learned",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify"]
 
 
@@ -81,11 +83,22 @@ def lib():
             "sfg_sparsify": [_vp, _vp, ctypes.POINTER(sfg_params), _vp, _pi64],
             "sfg_sparsify_batched": [_vp, _int, ctypes.POINTER(_vp), ctypes.POINTER(sfg_params),
                                      ctypes.POINTER(_vp), _pi64],
+            "sfg_mlp_create": [_vp, _u64, ctypes.POINTER(_vp)],
+            "sfg_mlp_destroy": [_vp],
+            "sfg_mlp_params": [_vp, _vp, _vp],
+            "sfg_mlp_set_params": [_vp, _vp, _vp],
+            "sfg_mlp_forward": [_vp, _vp, _vp, _i64, _vp],
+            "sfg_mlp_gradient": [_vp, _vp, _vp, _vp, _i64, _vp, _pdbl],
+            "sfg_mlp_train": [_vp, _vp, _vp, _vp, _i64, _i64, _int, _dbl, _pdbl],
+            "sfg_edge_features": [_vp, _vp, _vp, _int, _int, _dbl, _u64, _int, _vp, _i64, _vp],
+            "sfg_sparsify_learned": [_vp, _vp, ctypes.POINTER(sfg_params), _vp, _int, _dbl, _vp,
+                                     _pi64],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = None if name in ("sfg_ctx_destroy", "sfg_graph_destroy") else _int
+            f.restype = None if name in ("sfg_ctx_destroy", "sfg_graph_destroy",
+                                         "sfg_mlp_destroy") else _int
         L.sfg_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -333,3 +346,85 @@ def sfg_sparsify_batched(ctx, graphs, K=16, steps=15, omega=0.7, seed=0, mode=SF
     counts = (ctypes.c_int64 * ng)()
     ctx.check(lib().sfg_sparsify_batched(ctx.h, ng, hs, ctypes.byref(p), outs, counts))
     return [m[:g.m] for m, g in zip(masks, graphs)], list(counts)
+
+
+MLP_NPARAM, MLP_NFEAT = 5313, 16
+
+
+class Mlp:
+    """Owner of an sfg_mlp handle (the learned edge-proposal network)."""
+
+    def __init__(self, ctx, seed=0):
+        self.ctx = ctx
+        h = _vp()
+        ctx.check(lib().sfg_mlp_create(ctx.h, seed & (2**64 - 1), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sfg_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sfg_mlp_create(ctx, seed=0):
+    return Mlp(ctx, seed)
+
+
+def sfg_mlp_params(ctx, net):
+    out = torch.empty(MLP_NPARAM, dtype=torch.float32, device=ctx.device)
+    ctx.check(lib().sfg_mlp_params(ctx.h, net.h, _ptr(out)))
+    return out
+
+
+def sfg_mlp_set_params(ctx, net, theta):
+    theta = theta.contiguous().float()
+    ctx.check(lib().sfg_mlp_set_params(ctx.h, net.h, _ptr(theta)))
+
+
+def sfg_mlp_forward(ctx, net, feats, out=None):
+    feats = feats.contiguous()
+    if out is None:
+        out = torch.empty(feats.shape[0], dtype=torch.float32, device=ctx.device)
+    ctx.check(lib().sfg_mlp_forward(ctx.h, net.h, _ptr(feats), feats.shape[0], _ptr(out)))
+    return out
+
+
+def sfg_mlp_gradient(ctx, net, feats, targets):
+    g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=ctx.device)
+    loss = _dbl()
+    ctx.check(lib().sfg_mlp_gradient(ctx.h, net.h, _ptr(feats.contiguous()), _ptr(targets.contiguous()),
+                                     feats.shape[0], _ptr(g), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def sfg_mlp_train(ctx, net, feats, targets, batch=65536, epochs=1, lr=1e-3):
+    loss = _dbl()
+    ctx.check(lib().sfg_mlp_train(ctx.h, net.h, _ptr(feats.contiguous()), _ptr(targets.contiguous()),
+                                  feats.shape[0], batch, epochs, lr, ctypes.byref(loss)))
+    return loss.value
+
+
+def sfg_edge_features(ctx, LG, LP, ids, K, steps, omega=0.7, seed=0, storage=torch.float32):
+    ids = ids.contiguous()
+    out = torch.empty((ids.numel(), MLP_NFEAT), dtype=torch.float32, device=ctx.device)
+    ctx.check(lib().sfg_edge_features(ctx.h, LG.h, LP.h, K, steps, omega, seed & (2**64 - 1),
+                                      _dt(storage), _ptr(ids), ids.numel(), _ptr(out)))
+    return out
+
+
+def sfg_sparsify_learned(ctx, g, net, K=32, steps=20, feat_steps=2, propose_frac=0.02, omega=0.7,
+                         seed=0, mode=SFG_SCORE_RATIO, budget_frac=0.05, budget_unit=0,
+                         storage=torch.float32):
+    p = sfg_params(K, steps, 0, omega, seed & (2**64 - 1), mode, budget_frac, budget_unit,
+                   _dt(storage))
+    out = torch.empty(max(g.m, 1), dtype=torch.uint8, device=ctx.device)
+    ns = _i64()
+    ctx.check(lib().sfg_sparsify_learned(ctx.h, g.h, ctypes.byref(p), None if net is None else net.h,
+                                         feat_steps, propose_frac, _ptr(out), ctypes.byref(ns)))
+    return out[:g.m], ns.value
