@@ -136,6 +136,21 @@ SFG_API sfg_status sfg_smooth(sfg_ctx* ctx, const sfg_graph* L, int K, int steps
 SFG_API sfg_status sfg_jacobi(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                       sfg_dtype storage, void* X_inout);
 
+/* Tile-shape autotuning of the sweep (not in the paper). Variant v of the plain sweep: a warp
+ * sweeps TPI = {1, 2, 4, 1, 2, 4}[v] consecutive row tiles before its grid-stride jump, with
+ * {4, 4, 4, 3, 3, 3}[v] CTAs per SM requested from the compiler; default v = 1. sfg_autotune times
+ * all variants on L (three sweeps each, synchronises) and records the fastest in ctx's table under
+ * (K, storage, degree bucket b: 2^b <= 2m/n < 2^(b+1)); later sweeps on graphs of that key use it.
+ * Every variant computes the same values bit for bit. sfg_tune_set writes (or, variant -1, clears)
+ * an entry; sfg_tune_table writes the table as JSON text (len_host: its length; SFG_ECAPACITY if
+ * cap is too small). */
+#define SFG_SWEEP_VARIANTS 6
+SFG_API sfg_status sfg_autotune(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype storage,
+                                int* variant_host, double* us_per_sweep_host);
+SFG_API sfg_status sfg_tune_set(sfg_ctx* ctx, int K, sfg_dtype storage, int degree_bucket,
+                                int variant);
+SFG_API sfg_status sfg_tune_table(const sfg_ctx* ctx, char* buf, int64_t cap, int64_t* len_host);
+
 /* ---------------------------------------------------------------------------------------------
  * Spectrally critical edges (Sec. 3.5; Algorithm 1 lines 13-14)
  * ------------------------------------------------------------------------------------------- */

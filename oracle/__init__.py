@@ -306,3 +306,38 @@ def kappa_dense(g: Graph, mask) -> float:
         return float("inf")
     ev = sl.eigh(A, B, eigvals_only=True)
     return float(ev[-1] / ev[0])
+
+
+def _grounded_sparse(g: Graph, mask=None):
+    """Sparse L_G (or L_P for mask) with one node per component of G grounded."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    sel = np.ones(g.m, bool) if mask is None else np.asarray(mask).astype(bool)
+    u, v, w = g.u[sel], g.v[sel], g.w[sel].astype(np.float64)
+    A = sp.coo_matrix((np.concatenate([w, w]), (np.concatenate([u, v]), np.concatenate([v, u]))),
+                      shape=(g.n, g.n)).tocsr()
+    L = sp.diags(np.asarray(A.sum(1)).ravel()) - A
+    G = sp.coo_matrix((np.ones(g.m), (g.u, g.v)), shape=(g.n, g.n))
+    _, lab = connected_components(G, directed=False)
+    first = np.full(lab.max() + 1, g.n)
+    np.minimum.at(first, lab, np.arange(g.n))
+    keep = np.ones(g.n, bool)
+    keep[first] = False
+    return L.tocsc()[keep][:, keep]
+
+
+def kappa_lanczos(g: Graph, mask) -> float:
+    """kappa(L_G, L_P) of Eq. eqn:ineq for larger graphs: the extreme eigenvalues of the grounded
+    pencil by implicitly restarted Lanczos (ARPACK through scipy, a library eigensolver), with
+    sparse LU factorisations of the grounded Laplacians for the inner solves. lambda_max from the
+    pencil (L_G, L_P), lambda_min as 1 / lambda_max of (L_P, L_G)."""
+    from scipy.sparse.linalg import eigsh
+
+    LG = _grounded_sparse(g)
+    LP = _grounded_sparse(g, mask)
+    if LG.shape[0] == 0:
+        return 1.0
+    hi = eigsh(LG, k=1, M=LP, which="LA", return_eigenvectors=False, tol=1e-8)[0]
+    inv_lo = eigsh(LP, k=1, M=LG, which="LA", return_eigenvectors=False, tol=1e-8)[0]
+    return float(hi * inv_lo)

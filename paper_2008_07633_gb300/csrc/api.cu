@@ -96,6 +96,27 @@ void sfg_toc(sfg_ctx* ctx) {
     cudaEventRecord(ctx->timers.back().stop, ctx->stream);
 }
 
+static uint32_t tune_key(int K, sfg_dtype dt, int bucket) {
+    return ((uint32_t)K << 16) | ((uint32_t)dt << 8) | (uint32_t)bucket;
+}
+
+int sfg_degree_bucket(const sfg_graph* L) {
+    const double avg = L->n > 0 ? (2.0 * (double)L->m) / (double)L->n : 0.0;
+    int b = 0;
+    while (b < 15 && (double)(2 << b) <= avg) ++b;  // bucket b: 2^b <= avg degree < 2^(b+1)
+    return b;
+}
+
+int sfg_tuned_variant(const sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L) {
+    if (ctx->tune.empty()) return -1;
+    auto it = ctx->tune.find(tune_key(K, dt, sfg_degree_bucket(L)));
+    return it == ctx->tune.end() ? -1 : it->second;
+}
+
+void sfg_tune_record(sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L, int variant) {
+    ctx->tune[tune_key(K, dt, sfg_degree_bucket(L))] = variant;
+}
+
 extern "C" {
 
 sfg_status sfg_ctx_create(sfg_ctx** out, int device, void* cuda_stream) {
@@ -169,6 +190,51 @@ sfg_status sfg_ctx_kernel_time(sfg_ctx* ctx, const char* prefix, int64_t* launch
 sfg_status sfg_ctx_launches(const sfg_ctx* ctx, int64_t* launches_host) {
     if (!ctx || !launches_host) return SFG_EINVAL;
     *launches_host = ctx->launches;
+    return SFG_OK;
+}
+
+sfg_status sfg_autotune(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype storage,
+                        int* variant_host, double* us_per_sweep_host) {
+    if (!ctx) return SFG_EINVAL;
+    if (!L) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
+    if (!sfg_k_supported(K, storage))
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", K, (int)storage);
+    return sfg_autotune_impl(ctx, L, K, storage, variant_host, us_per_sweep_host);
+}
+
+sfg_status sfg_tune_set(sfg_ctx* ctx, int K, sfg_dtype storage, int degree_bucket, int variant) {
+    if (!ctx) return SFG_EINVAL;
+    if (degree_bucket < 0 || degree_bucket > 15 || variant < -1 || variant >= SFG_SWEEP_VARIANTS)
+        return sfg_fail(ctx, SFG_EINVAL, "bad tuning entry");
+    const uint32_t key = tune_key(K, storage, degree_bucket);
+    if (variant < 0) ctx->tune.erase(key);
+    else ctx->tune[key] = variant;
+    return SFG_OK;
+}
+
+sfg_status sfg_tune_table(const sfg_ctx* ctx, char* buf, int64_t cap, int64_t* len_host) {
+    if (!ctx || !len_host) return SFG_EINVAL;
+    static const int tpi[SFG_SWEEP_VARIANTS] = {1, 2, 4, 1, 2, 4};
+    static const int minb[SFG_SWEEP_VARIANTS] = {4, 4, 4, 3, 3, 3};
+    std::string j = "[";
+    for (auto& kv : ctx->tune) {
+        char item[160];
+        const int v = kv.second;
+        snprintf(item, sizeof item,
+                 "%s{\"K\": %u, \"dtype\": %u, \"degree_bucket\": %u, \"variant\": %d, "
+                 "\"tiles_per_warp\": %d, \"ctas_per_sm\": %d}",
+                 j.size() > 1 ? ", " : "", kv.first >> 16, (kv.first >> 8) & 0xff, kv.first & 0xff,
+                 v, tpi[v], minb[v]);
+        j += item;
+    }
+    j += "]";
+    *len_host = (int64_t)j.size();
+    if (buf && cap > 0) {
+        const size_t n = std::min((size_t)cap - 1, j.size());
+        memcpy(buf, j.data(), n);
+        buf[n] = 0;
+        if ((int64_t)j.size() >= cap) return SFG_ECAPACITY;
+    }
     return SFG_OK;
 }
 

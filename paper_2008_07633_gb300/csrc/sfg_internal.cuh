@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <algorithm>
+#include <map>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -29,6 +30,7 @@ struct sfg_ctx {
     std::vector<sfg_timer_rec> timers;     // recorded this session
     std::vector<cudaEvent_t> event_pool;   // free events
     int64_t launches = 0;                  // kernels launched through this context
+    std::map<uint32_t, int> tune;          // (K, dtype, degree bucket) -> sweep variant
     int64_t alloc_count = 0;               // for the allocation-failure injection hook
     int64_t fail_alloc_at = -1;            // SFG_FAULT_ALLOC=<n>: the n-th allocation fails
 };
@@ -177,6 +179,12 @@ void sfg_graph_free(sfg_graph* g);
 // Device arrays of a graph with n nodes and m canonical edges (contents unset).
 sfg_status sfg_alloc_graph(sfg_ctx* ctx, int32_t n, int64_t m, sfg_graph** out);
 bool sfg_k_supported(int K, sfg_dtype dt);
+// Tile-shape tuning table of a context (see sfg_autotune). Variant -1 = none recorded.
+int sfg_degree_bucket(const sfg_graph* L);
+int sfg_tuned_variant(const sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L);
+void sfg_tune_record(sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L, int variant);
+sfg_status sfg_autotune_impl(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype storage,
+                             int* best, double* us);
 
 // splitmix64 (Steele, Lea & Flood 2014), host and device.
 __host__ __device__ inline uint64_t sfg_splitmix64(uint64_t x) {

@@ -19,15 +19,12 @@
 namespace {
 
 constexpr int kBlock = 256;
-#ifndef SFG_JACOBI_TPI
-#define SFG_JACOBI_TPI 2  // consecutive row tiles a warp sweeps before its grid-stride jump
-#endif
-#ifndef SFG_JACOBI_STREAM_HINTS
-#define SFG_JACOBI_STREAM_HINTS 0  // 1: load CSR metadata with the evict-first (streaming) hint
-#endif
-#ifndef SFG_JACOBI_MIN_BLOCKS
-#define SFG_JACOBI_MIN_BLOCKS 4  // resident CTAs per SM requested from the compiler (caps registers at 64)
-#endif
+// Tile-shape variants of the sweep, chosen per (K, storage, degree bucket) by sfg_autotune:
+// TPI = consecutive row tiles a warp sweeps before its grid-stride jump, MINB = resident CTAs per
+// SM requested from the compiler (4 caps registers at 64, 3 at 80).
+struct JVariant { int tpi, minb; };
+constexpr JVariant kJVariants[] = {{1, 4}, {2, 4}, {4, 4}, {1, 3}, {2, 3}, {4, 3}};
+constexpr int kJNumVariants = 6, kJDefault = 1;
 
 // Gaussian entries 2p and 2p+1 of the counter-based generator (see sfg.h): SplitMix64 output
 // p + 1 of the stream started in state splitmix64(seed), both Box-Muller branches in FP32 (logf,
@@ -123,11 +120,7 @@ __global__ void __launch_bounds__(kBlock) k_init(int32_t n, uint64_t seed, const
 
 template <typename V>
 __device__ __forceinline__ V ldmeta(const V* p) {
-#if SFG_JACOBI_STREAM_HINTS
-    return __ldcs(p);
-#else
     return *p;
-#endif
 }
 
 // A chunk of C = max(LPR, 8) consecutive (column, weight) entries of one row, spread over the
@@ -196,8 +189,8 @@ __device__ __forceinline__ void gather_chunk(const Chunk<LPR>& ch, int need, uns
 // chunk of (column, weight) entries. The next tile's metadata is loaded before this tile's
 // gathers are issued and its chunks right after, so one gather round is the only exposed latency
 // per tile. Gathers go in warp-uniform batches sized by the tile's longest row.
-template <typename T, int LPR, bool SUB_MU, bool STATS>
-__global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
+template <typename T, int LPR, bool SUB_MU, bool STATS, int TPI, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
     k_jacobi(int32_t n, const int32_t* __restrict__ row_ptr, const int2* __restrict__ colval,
              const float* __restrict__ coef, float a_self, const T* __restrict__ X,
              T* __restrict__ Y, const float* __restrict__ mu, double* __restrict__ part) {
@@ -209,7 +202,6 @@ __global__ void __launch_bounds__(kBlock, SFG_JACOBI_MIN_BLOCKS)
     const int32_t ntiles = (n + GPW - 1) / GPW;
     const T* __restrict__ Xl = X + sub * E;
     // tile order of this warp: TPI consecutive tiles, then a jump over the other warps' tiles
-    constexpr int32_t TPI = SFG_JACOBI_TPI;
     auto next_tile = [&](int32_t t) {
         return (t + 1) % TPI != 0 ? t + 1 : t + 1 + (nw - 1) * TPI;
     };
@@ -507,7 +499,19 @@ struct Smoother {
     static constexpr int E = Vec<T>::E, K = LPR * E;
 
     template <bool A, bool B>
-    static void* kern() { return (void*)k_jacobi<T, LPR, A, B>; }
+    static void* kern() {
+        return (void*)k_jacobi<T, LPR, A, B, kJVariants[kJDefault].tpi, kJVariants[kJDefault].minb>;
+    }
+    static void* plain_kern(int v) {  // the tuned variants of the plain sweep
+        switch (v) {
+            case 0: return (void*)k_jacobi<T, LPR, false, false, 1, 4>;
+            case 2: return (void*)k_jacobi<T, LPR, false, false, 4, 4>;
+            case 3: return (void*)k_jacobi<T, LPR, false, false, 1, 3>;
+            case 4: return (void*)k_jacobi<T, LPR, false, false, 2, 3>;
+            case 5: return (void*)k_jacobi<T, LPR, false, false, 4, 3>;
+            default: return (void*)k_jacobi<T, LPR, false, false, 2, 4>;
+        }
+    }
 
     static int grid_jacobi(sfg_ctx* ctx, int32_t n) {
         return sfg_grid(ctx, kern<false, false>(), kBlock, 0, (int64_t)n * LPR);
@@ -521,9 +525,17 @@ struct Smoother {
                         (void*)&a_self, (void*)&X, (void*)&Y, (void*)&mu, (void*)&part};
         void* k = sub_mu ? (stats ? kern<true, true>() : kern<true, false>())
                          : (stats ? kern<false, true>() : kern<false, false>());
+        int g = grid;
+        if (!sub_mu && !stats) {  // the plain sweep takes the tuned tile shape, if any
+            const int v = sfg_tuned_variant(ctx, K, Vec<T>::E == 4 ? SFG_F32 : SFG_BF16, L);
+            if (v >= 0 && v != kJDefault) {
+                k = plain_kern(v);
+                g = sfg_grid(ctx, k, kBlock, 0, (int64_t)n * LPR);
+            }
+        }
         sfg_tic(ctx, "jacobi");
         ++ctx->launches;
-        const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kBlock), args, 0, ctx->stream);
+        const cudaError_t e = cudaLaunchKernel(k, dim3(g), dim3(kBlock), args, 0, ctx->stream);
         sfg_toc(ctx);
         if (e != cudaSuccess) return sfg_cuda_fail(ctx, e, "k_jacobi");
         return SFG_OK;
@@ -710,6 +722,62 @@ struct Smoother {
                                       ids, ne, mode, scores, sg, sp, node_off, ng);
     }
 
+    // Time every tile-shape variant of the plain sweep on L and record the fastest.
+    static sfg_status autotune(sfg_ctx* ctx, const sfg_graph* L, int* best_host, double* us_host) {
+        const int32_t n = L->n;
+        const int grid = grid_jacobi(ctx, n);
+        Scratch s(ctx);
+        T *x, *y;
+        float* coef;
+        double* part;
+        SFG_TRY(s.get(&x, (size_t)n * K));
+        SFG_TRY(s.get(&y, (size_t)n * K));
+        SFG_TRY(s.get(&coef, (size_t)n));
+        SFG_TRY(s.get(&part, (size_t)grid * 2 * K));
+        k_init<T, LPR, false><<<grid, kBlock, 0, ctx->stream>>>(n, 12345, L->deg, x, part);
+        k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
+            n, L->invdeg, 0.7, coef);
+        ctx->launches += 2;
+        SFG_LAUNCH_CHECK(ctx, "autotune init");
+        cudaEvent_t e0, e1;
+        SFG_CUDA(ctx, cudaEventCreate(&e0));
+        SFG_CUDA(ctx, cudaEventCreate(&e1));
+        int best = kJDefault;
+        float best_ms = 1e30f;
+        const float a_self = 0.3f;
+        const float* mu = nullptr;
+        double* pp = nullptr;
+        for (int v = 0; v < kJNumVariants; ++v) {
+            void* k = plain_kern(v);
+            const int g = sfg_grid(ctx, k, kBlock, 0, (int64_t)n * LPR);
+            const T* X = x;
+            T* Y = y;
+            void* args[] = {(void*)&n, (void*)&L->row_ptr, (void*)&L->colval, (void*)&coef,
+                            (void*)&a_self, (void*)&X, (void*)&Y, (void*)&mu, (void*)&pp};
+            for (int r = 0; r < 4; ++r) {  // one warm-up, three timed
+                if (r == 1) cudaEventRecord(e0, ctx->stream);
+                const cudaError_t err = cudaLaunchKernel(k, dim3(g), dim3(kBlock), args, 0, ctx->stream);
+                ++ctx->launches;
+                if (err != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return sfg_cuda_fail(ctx, err, "autotune sweep");
+                }
+            }
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best = v; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        sfg_tune_record(ctx, K, Vec<T>::E == 4 ? SFG_F32 : SFG_BF16, L, best);
+        if (best_host) *best_host = best;
+        if (us_host) *us_host = best_ms / 3.0 * 1e3;
+        return SFG_OK;
+    }
+
     static sfg_status jacobi(sfg_ctx* ctx, const sfg_graph* L, int steps, double omega, T* X) {
         const int32_t n = L->n;
         const int grid = grid_jacobi(ctx, n);
@@ -791,6 +859,14 @@ sfg_status sfg_filter_score_batched_impl(sfg_ctx* ctx, const sfg_graph* U, const
         using Sm = decltype(S);
         return Sm::filter_score_batched(ctx, U, PU, ng, node_off, steps, omega, seed, ids, ne,
                                         mode, scores);
+    });
+}
+
+sfg_status sfg_autotune_impl(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype storage,
+                             int* best, double* us) {
+    return dispatch(K, storage, [&](auto S) {
+        using Sm = decltype(S);
+        return Sm::autotune(ctx, L, best, us);
     });
 }
 

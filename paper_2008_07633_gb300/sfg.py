@@ -27,6 +27,7 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_
            "sfg_affinity_noalloc", "sfg_filter_score", "sfg_sparsify_batched", "sfg_mlp_create",
            "sfg_mlp_destroy", "sfg_mlp_params", "sfg_mlp_set_params", "sfg_mlp_forward",
            "sfg_mlp_gradient", "sfg_mlp_train", "sfg_edge_features", "sfg_sparsify_learned",
+           "sfg_autotune", "sfg_tune_set", "sfg_tune_table",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify"]
 
 
@@ -84,6 +85,9 @@ def lib():
             "sfg_sparsify_batched": [_vp, _int, ctypes.POINTER(_vp), ctypes.POINTER(sfg_params),
                                      ctypes.POINTER(_vp), _pi64],
             "sfg_mlp_create": [_vp, _u64, ctypes.POINTER(_vp)],
+            "sfg_autotune": [_vp, _vp, _int, _int, ctypes.POINTER(_int), _pdbl],
+            "sfg_tune_set": [_vp, _int, _int, _int, _int],
+            "sfg_tune_table": [_vp, ctypes.c_char_p, _i64, _pi64],
             "sfg_mlp_destroy": [_vp],
             "sfg_mlp_params": [_vp, _vp, _vp],
             "sfg_mlp_set_params": [_vp, _vp, _vp],
@@ -428,3 +432,25 @@ def sfg_sparsify_learned(ctx, g, net, K=32, steps=20, feat_steps=2, propose_frac
     ctx.check(lib().sfg_sparsify_learned(ctx.h, g.h, ctypes.byref(p), None if net is None else net.h,
                                          feat_steps, propose_frac, _ptr(out), ctypes.byref(ns)))
     return out[:g.m], ns.value
+
+
+def sfg_autotune(ctx, g, K, storage=torch.float32):
+    """Time the sweep's tile-shape variants on g; returns (variant, microseconds per sweep)."""
+    v, us = _int(), _dbl()
+    ctx.check(lib().sfg_autotune(ctx.h, g.h, K, _dt(storage), ctypes.byref(v), ctypes.byref(us)))
+    return v.value, us.value
+
+
+def sfg_tune_set(ctx, K, storage, degree_bucket, variant):
+    ctx.check(lib().sfg_tune_set(ctx.h, K, _dt(storage), degree_bucket, variant))
+
+
+def sfg_tune_table(ctx):
+    """The context's tuning table as a list of dicts (JSON from the library)."""
+    import json
+
+    n = _i64()
+    ctx.check(lib().sfg_tune_table(ctx.h, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    ctx.check(lib().sfg_tune_table(ctx.h, buf, n.value + 1, ctypes.byref(n)))
+    return json.loads(buf.value.decode())

@@ -446,3 +446,14 @@ def test_sparsify_multilevel_properties():
     assert np.isfinite(k)
     target = int(np.floor(0.05 * g.n + 0.5))
     assert int(mask.sum()) >= g.n - 1 + target
+
+
+def test_kappa_lanczos_matches_dense():
+    for spec in (gen.grid2d(20, 25, seed=3), gen.random_graph(400, 1500, seed=4),
+                 gen.random_graph(300, 500, seed=6, connected=False)):
+        g = G(*spec)
+        tree = O.mst(g)
+        mask, _ = O.sparsify(g, K=8, steps=10, budget_frac=0.1, budget_unit=1, seed=2)
+        for mk in (tree, mask):
+            kd, kl = O.kappa_dense(g, mk), O.kappa_lanczos(g, mk)
+            assert abs(kd - kl) <= 1e-5 * kd, (kd, kl)
