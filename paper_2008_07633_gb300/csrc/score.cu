@@ -140,20 +140,18 @@ sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const
                         const int32_t* ids, int64_t ne, int mode, const float* sg,
                         const float* sp, const int32_t* node_off, int ngraphs, float* out) {
     if (ne == 0) return SFG_OK;
-    const int grid = sfg_grid(ctx, (const void*)k_score<T, LPR, 0>, kBlock, 0, ne * LPR);
+    // the grid fills the SMs at the occupancy of the variant that is launched
+    const void* k = node_off ? (const void*)k_score<T, LPR, 2>
+                             : (sg ? (const void*)k_score<T, LPR, 1> : (const void*)k_score<T, LPR, 0>);
+    const int grid = sfg_grid(ctx, k, kBlock, 0, ne * LPR);
     sfg_tic(ctx, "score");
-    if (node_off)
-        k_score<T, LPR, 2><<<grid, kBlock, 0, ctx->stream>>>(
-            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp,
-            node_off, ngraphs, out);
-    else if (sg)
-        k_score<T, LPR, 1><<<grid, kBlock, 0, ctx->stream>>>(
-            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp,
-            nullptr, 0, out);
-    else
-        k_score<T, LPR, 0><<<grid, kBlock, 0, ctx->stream>>>(
-            ne, ids, LG->eu, LG->ev, LG->ew, (const T*)XG, (const T*)XP, mode, 1e-30f, sg, sp,
-            nullptr, 0, out);
+    const T *xg = (const T*)XG, *xp = (const T*)XP;
+    float eta = 1e-30f;
+    void* args[] = {(void*)&ne, (void*)&ids, (void*)&LG->eu, (void*)&LG->ev, (void*)&LG->ew,
+                    (void*)&xg, (void*)&xp, (void*)&mode, (void*)&eta, (void*)&sg, (void*)&sp,
+                    (void*)&node_off, (void*)&ngraphs, (void*)&out};
+    const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kBlock), args, 0, ctx->stream);
+    if (e != cudaSuccess) return sfg_cuda_fail(ctx, e, "k_score");
     ++ctx->launches;
     sfg_toc(ctx);
     SFG_LAUNCH_CHECK(ctx, "k_score");

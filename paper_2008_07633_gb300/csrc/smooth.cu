@@ -223,25 +223,16 @@ __global__ void __launch_bounds__(kBlock, MINB)
         if (t < ntiles && lane < GPW && r < n) mt.cf = ldmeta(coef + r);
         return mt;
     };
-
-    int32_t t = wid * TPI;
-    Meta mt = load_meta(t);
-    int32_t a = __shfl_sync(0xffffffffu, mt.lo, grp);
-    int32_t b = GPW == 32 ? mt.hi : __shfl_sync(0xffffffffu, mt.lo, grp + 1);
-    int32_t r = t * GPW + grp;
-    Chunk<LPR> ch;
-    ch.load(colval, a, b, r < n ? r : 0, sub);
-    for (; t < ntiles; t = next_tile(t)) {
-        const int32_t tn = next_tile(t);
-        const Meta mtn = load_meta(tn);  // next tile's metadata, in flight with the gathers
-
+    // The rows of tile t: gathers, then mid() (work to overlap with the update), the update, the
+    // store and the projection statistics.
+    auto row_tile = [&](int32_t t, const Chunk<LPR>& ch, int32_t a, int32_t b, float cp, auto&& mid) {
+        const int32_t r = t * GPW + grp;
         const bool live = r < n;
         const int32_t self = live ? r : 0;
-        const float cp = __shfl_sync(0xffffffffu, mt.cf, grp);
         const int32_t deg = b - a;
         const int32_t maxdeg = __reduce_max_sync(0xffffffffu, deg);
-        float xs[E], acc[E];
-        Vec<T>::load(Xl + (int64_t)self * K, xs);
+        float acc[E];
+        const uint4 xr = Vec<T>::load_raw(Xl + (int64_t)self * K);  // widened at use
 #pragma unroll
         for (int e = 0; e < E; ++e) acc[e] = 0.f;
         gather_chunk<T, LPR>(ch, min(maxdeg, C), gm, Xl, acc);
@@ -250,15 +241,10 @@ __global__ void __launch_bounds__(kBlock, MINB)
             cx.load(colval, a + j0, b, self, sub);
             gather_chunk<T, LPR>(cx, min(maxdeg - j0, C), gm, Xl, acc);
         }
-
-        // next tile: row bounds and first chunk (its metadata has had the gather round to arrive)
-        const int32_t an = __shfl_sync(0xffffffffu, mtn.lo, grp);
-        const int32_t bn = GPW == 32 ? mtn.hi : __shfl_sync(0xffffffffu, mtn.lo, grp + 1);
-        const int32_t rn = tn * GPW + grp;
-        ch.load(colval, an, bn, rn < n ? rn : 0, sub);
-
+        mid();
         if (live) {
-            float y[E];
+            float xs[E], y[E];
+            Vec<T>::unpack(xr, xs);
             if (deg > 0) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) y[e] = fmaf(cp, acc[e], a_self * xs[e]) - m[e];
@@ -275,10 +261,58 @@ __global__ void __launch_bounds__(kBlock, MINB)
                     s2[e] = fmaf(q, q, s2[e]);
                 }
         }
-        mt = mtn;
-        a = an;
-        b = bn;
-        r = rn;
+    };
+
+    if constexpr (LPR <= 8) {
+        // Three tiles are in flight: t is gathered, the next tile's chunk is loaded, and the metadata
+        // of the one after it is loaded. The next tile's bounds come from metadata issued one gather
+        // round earlier and its chunk is issued before this tile's gathers, so each tile exposes one
+        // gather round and nothing else.
+        int32_t t = wid * TPI;
+        const Meta mt0 = load_meta(t);
+        Meta mt1 = load_meta(next_tile(t));
+        int32_t a = __shfl_sync(0xffffffffu, mt0.lo, grp);
+        int32_t b = GPW == 32 ? mt0.hi : __shfl_sync(0xffffffffu, mt0.lo, grp + 1);
+        float cp = __shfl_sync(0xffffffffu, mt0.cf, grp);
+        Chunk<LPR> ch;
+        ch.load(colval, a, b, min(t * GPW + grp, n - 1), sub);
+        while (t < ntiles) {
+            const int32_t t1 = next_tile(t);
+            Chunk<LPR> ch1;
+            ch1.load(colval, __shfl_sync(0xffffffffu, mt1.lo, grp),
+                     GPW == 32 ? mt1.hi : __shfl_sync(0xffffffffu, mt1.lo, grp + 1),
+                     min(t1 * GPW + grp, n - 1), sub);
+            const Meta mt2 = load_meta(next_tile(t1));
+            row_tile(t, ch, a, b, cp, [] {});
+            t = t1;
+            ch = ch1;
+            a = __shfl_sync(0xffffffffu, mt1.lo, grp);
+            b = GPW == 32 ? mt1.hi : __shfl_sync(0xffffffffu, mt1.lo, grp + 1);
+            cp = __shfl_sync(0xffffffffu, mt1.cf, grp);
+            mt1 = mt2;
+        }
+    } else {
+        // LPR = 16 (two rows per tile): two tiles in flight, t is gathered while the next tile's
+        // metadata is loaded and its chunk follows the gather round (measured faster at this shape).
+        int32_t t = wid * TPI;
+        Meta mt = load_meta(t);
+        int32_t a = __shfl_sync(0xffffffffu, mt.lo, grp);
+        int32_t b = GPW == 32 ? mt.hi : __shfl_sync(0xffffffffu, mt.lo, grp + 1);
+        Chunk<LPR> ch;
+        ch.load(colval, a, b, min(t * GPW + grp, n - 1), sub);
+        for (; t < ntiles;) {
+            const int32_t t1 = next_tile(t);
+            const Meta mt1 = load_meta(t1);
+            const int32_t a0 = a, b0 = b;
+            const Chunk<LPR> ch0 = ch;
+            row_tile(t, ch0, a0, b0, __shfl_sync(0xffffffffu, mt.cf, grp), [&] {
+                a = __shfl_sync(0xffffffffu, mt1.lo, grp);
+                b = GPW == 32 ? mt1.hi : __shfl_sync(0xffffffffu, mt1.lo, grp + 1);
+                ch.load(colval, a, b, min(t1 * GPW + grp, n - 1), sub);
+            });
+            mt = mt1;
+            t = t1;
+        }
     }
     if (STATS) block_column_partials<LPR, E>(s1, s2, part);
 }
@@ -521,8 +555,6 @@ struct Smoother {
                             const T* X, T* Y, const float* mu, double* part, bool sub_mu,
                             bool stats, int grid) {
         const int32_t n = L->n;
-        void* args[] = {(void*)&n, (void*)&L->row_ptr, (void*)&L->colval, (void*)&coef,
-                        (void*)&a_self, (void*)&X, (void*)&Y, (void*)&mu, (void*)&part};
         void* k = sub_mu ? (stats ? kern<true, true>() : kern<true, false>())
                          : (stats ? kern<false, true>() : kern<false, false>());
         int g = grid;
@@ -533,6 +565,8 @@ struct Smoother {
                 g = sfg_grid(ctx, k, kBlock, 0, (int64_t)n * LPR);
             }
         }
+        void* args[] = {(void*)&n, (void*)&L->row_ptr, (void*)&L->colval, (void*)&coef,
+                        (void*)&a_self, (void*)&X, (void*)&Y, (void*)&mu, (void*)&part};
         sfg_tic(ctx, "jacobi");
         ++ctx->launches;
         const cudaError_t e = cudaLaunchKernel(k, dim3(g), dim3(kBlock), args, 0, ctx->stream);

@@ -22,6 +22,10 @@ struct Vec<float> {
     __device__ __forceinline__ static uint4 load_raw(const float* p) {
         return *reinterpret_cast<const uint4*>(p);
     }
+    __device__ __forceinline__ static void unpack(uint4 r, float (&x)[4]) {
+        x[0] = __uint_as_float(r.x); x[1] = __uint_as_float(r.y);
+        x[2] = __uint_as_float(r.z); x[3] = __uint_as_float(r.w);
+    }
     __device__ __forceinline__ static void fma_raw(float w, uint4 r, float (&acc)[4]) {
         acc[0] = fmaf(w, __uint_as_float(r.x), acc[0]);
         acc[1] = fmaf(w, __uint_as_float(r.y), acc[1]);
@@ -57,6 +61,14 @@ struct Vec<__nv_bfloat16> {
     }
     __device__ __forceinline__ static uint4 load_raw(const __nv_bfloat16* p) {
         return *reinterpret_cast<const uint4*>(p);
+    }
+    __device__ __forceinline__ static void unpack(uint4 r, float (&x)[8]) {
+        const unsigned q[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[2 * i] = __uint_as_float(q[i] << 16);
+            x[2 * i + 1] = __uint_as_float(q[i] & 0xffff0000u);
+        }
     }
     __device__ __forceinline__ static void fma_raw(float w, uint4 r, float (&acc)[8]) {
         const unsigned q[4] = {r.x, r.y, r.z, r.w};
