@@ -12,6 +12,9 @@
 namespace {
 
 constexpr int kBlock = 256;
+#ifndef SFG_SCORE_U
+#define SFG_SCORE_U 2
+#endif
 
 template <int LPR>
 __device__ __forceinline__ unsigned group_mask(int lane) {
@@ -19,17 +22,18 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
     return ((1u << LPR) - 1u) << ((lane / LPR) * LPR);
 }
 
-// Scorer, warp-tile schedule: a warp scores a tile of GPW = 32 / LPR consecutive list entries
-// (one LPR-lane group per edge) and moves by grid stride. Lane l < GPW loads the tile's l-th edge
-// id and then that edge's endpoints and weight; groups take theirs by shuffle. The next tile's
-// endpoints and the ids of the tile after it are loaded before this tile's four row gathers are
-// consumed, so one gather round is the exposed latency per tile.
+// Scorer, warp-tile schedule: a warp scores U consecutive tiles of GPW = 32 / LPR list entries
+// each (one LPR-lane group per edge) and moves by grid stride over such tile groups. Lane
+// l < GPW loads the l-th edge id of each tile and then that edge's endpoints and weight; groups
+// take theirs by shuffle. The next group's endpoints and the ids of the group after it are loaded
+// before this group's 4U row gathers are consumed, so one gather round is the exposed latency per
+// U tiles. Gathered rows stay packed (16 bytes per gather) until they are used.
 // SCALED: the blocks are raw smoothed blocks and column k of each is multiplied by its projection
 // scale (sg, sp) on the fly; the projection's mean removal cancels in X_p - X_q.
 // SCALED = 2: the scales are per graph of a disjoint union (graph g's rows start at node_off[g]),
 // looked up from each edge's first endpoint.
-template <typename T, int LPR, int SCALED>
-__global__ void __launch_bounds__(kBlock)
+template <typename T, int LPR, int SCALED, int U>
+__global__ void __launch_bounds__(kBlock, U > 1 ? 4 : 1)
     k_score(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
             const int32_t* __restrict__ ev, const float* __restrict__ ew,
             const T* __restrict__ XG, const T* __restrict__ XP, int mode, float eta,
@@ -41,17 +45,21 @@ __global__ void __launch_bounds__(kBlock)
     const int64_t wid = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
     const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
     const int64_t ntiles = (ne + GPW - 1) / GPW;
+    const int64_t ngroups = (ntiles + U - 1) / U;
     const T* __restrict__ Xg = XG + sub * E;
     const T* __restrict__ Xp = XP + sub * E;
-    float scg[E], scp[E];
-#pragma unroll
-    for (int k = 0; k < E; ++k) {
-        scg[k] = SCALED == 1 ? sg[sub * E + k] : 1.f;
-        scp[k] = SCALED == 1 ? sp[sub * E + k] : 1.f;
+    // projection scales: shared-memory table for one block (SCALED = 1), read at use
+    __shared__ float s_scale[2][SCALED == 1 ? K : 1];
+    if (SCALED == 1) {
+        for (int k = threadIdx.x; k < K; k += kBlock) {
+            s_scale[0][k] = sg[k];
+            s_scale[1][k] = sp[k];
+        }
+        __syncthreads();
     }
     auto load_id = [&](int64_t t) -> int32_t {
         const int64_t i = t * GPW + lane;
-        return (t < ntiles && lane < GPW && i < ne) ? ids[i] : -1;
+        return (lane < GPW && i < ne) ? ids[i] : -1;
     };
     struct Edge { int32_t p, q; float w; };
     auto load_edge = [&](int32_t e) {
@@ -59,50 +67,77 @@ __global__ void __launch_bounds__(kBlock)
         if (e >= 0) { d.p = eu[e]; d.q = ev[e]; d.w = ew[e]; }
         return d;
     };
-    int64_t t = wid;
-    Edge cur = load_edge(load_id(t));
-    int32_t idn = load_id(t + nw);
-    for (; t < ntiles; t += nw) {
-        const Edge nxt = load_edge(idn);          // next tile's endpoints
-        idn = load_id(t + 2 * nw);                // ids of the tile after it
-        const int64_t i = t * GPW + grp;
-        const int64_t p = __shfl_sync(0xffffffffu, cur.p, grp);
-        const int64_t q = __shfl_sync(0xffffffffu, cur.q, grp);
-        const float w = __shfl_sync(0xffffffffu, cur.w, grp);
-        if (SCALED == 2) {
-            int lo = 0, hi = ngraphs;  // graph of row p
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (node_off[mid] <= p) lo = mid; else hi = mid;
+    int64_t g = wid;
+    Edge cur[U];
+    int32_t idn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        cur[u] = load_edge(load_id(g * U + u));
+        idn[u] = load_id((g + nw) * U + u);
+    }
+    for (; g < ngroups; g += nw) {
+        Edge nxt[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            nxt[u] = load_edge(idn[u]);            // next group's endpoints
+            idn[u] = load_id((g + 2 * nw) * U + u);  // ids of the group after it
+        }
+        uint4 rgp[U], rgq[U], rpp[U], rpq[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t p = __shfl_sync(0xffffffffu, cur[u].p, grp);
+            const int64_t q = __shfl_sync(0xffffffffu, cur[u].q, grp);
+            rgp[u] = Vec<T>::load_raw(Xg + p * K);
+            rgq[u] = Vec<T>::load_raw(Xg + q * K);
+            rpp[u] = Vec<T>::load_raw(Xp + p * K);
+            rpq[u] = Vec<T>::load_raw(Xp + q * K);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = (g * U + u) * GPW + grp;
+            const float w = __shfl_sync(0xffffffffu, cur[u].w, grp);
+            const float* sc_g = nullptr;  // this edge's scales (SCALED = 2: of its graph)
+            const float* sc_p = nullptr;
+            if (SCALED == 1) {
+                sc_g = s_scale[0] + sub * E;
+                sc_p = s_scale[1] + sub * E;
+            } else if (SCALED == 2) {
+                const int32_t p = __shfl_sync(0xffffffffu, cur[u].p, grp);
+                int lo = 0, hi = ngraphs;  // graph of row p
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (node_off[mid] <= p) lo = mid; else hi = mid;
+                }
+                sc_g = sg + (size_t)lo * K + sub * E;
+                sc_p = sp + (size_t)lo * K + sub * E;
             }
+            float gp[E], gq[E], pp[E], pq[E];
+            Vec<T>::unpack(rgp[u], gp);
+            Vec<T>::unpack(rgq[u], gq);
+            Vec<T>::unpack(rpp[u], pp);
+            Vec<T>::unpack(rpq[u], pq);
+            float dg = 0.f, dp = 0.f;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                scg[k] = sg[(size_t)lo * K + sub * E + k];
-                scp[k] = sp[(size_t)lo * K + sub * E + k];
+                float a = gp[k] - gq[k], b = pp[k] - pq[k];
+                if (SCALED) {
+                    a *= sc_g[k];
+                    b *= sc_p[k];
+                }
+                dg = fmaf(a, a, dg);
+                dp = fmaf(b, b, dp);
             }
-        }
-        float gp[E], gq[E], pp[E], pq[E];
-        Vec<T>::load(Xg + p * K, gp);
-        Vec<T>::load(Xg + q * K, gq);
-        Vec<T>::load(Xp + p * K, pp);
-        Vec<T>::load(Xp + q * K, pq);
-        float dg = 0.f, dp = 0.f;
 #pragma unroll
-        for (int k = 0; k < E; ++k) {
-            const float a = (gp[k] - gq[k]) * scg[k], b = (pp[k] - pq[k]) * scp[k];
-            dg = fmaf(a, a, dg);
-            dp = fmaf(b, b, dp);
+            for (int o = 1; o < LPR; o <<= 1) {
+                dg += __shfl_xor_sync(gm, dg, o, LPR);
+                dp += __shfl_xor_sync(gm, dp, o, LPR);
+            }
+            if (sub == 0 && i < ne) {
+                const float sgv = w * dg, spv = w * dp;
+                out[i] = mode == SFG_SCORE_G ? sgv : (mode == SFG_SCORE_P ? spv : spv / (sgv + eta));
+            }
+            cur[u] = nxt[u];
         }
-#pragma unroll
-        for (int o = 1; o < LPR; o <<= 1) {
-            dg += __shfl_xor_sync(gm, dg, o, LPR);
-            dp += __shfl_xor_sync(gm, dp, o, LPR);
-        }
-        if (sub == 0 && i < ne) {
-            const float sgv = w * dg, spv = w * dp;
-            out[i] = mode == SFG_SCORE_G ? sgv : (mode == SFG_SCORE_P ? spv : spv / (sgv + eta));
-        }
-        cur = nxt;
     }
 }
 
@@ -141,9 +176,10 @@ sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const
                         const float* sp, const int32_t* node_off, int ngraphs, float* out) {
     if (ne == 0) return SFG_OK;
     // the grid fills the SMs at the occupancy of the variant that is launched
-    const void* k = node_off ? (const void*)k_score<T, LPR, 2>
-                             : (sg ? (const void*)k_score<T, LPR, 1> : (const void*)k_score<T, LPR, 0>);
-    const int grid = sfg_grid(ctx, k, kBlock, 0, ne * LPR);
+    constexpr int U = SFG_SCORE_U;
+    const void* k = node_off ? (const void*)k_score<T, LPR, 2, U>
+                             : (sg ? (const void*)k_score<T, LPR, 1, U> : (const void*)k_score<T, LPR, 0, U>);
+    const int grid = sfg_grid(ctx, k, kBlock, 0, (ne + U - 1) / U * LPR);
     sfg_tic(ctx, "score");
     const T *xg = (const T*)XG, *xp = (const T*)XP;
     float eta = 1e-30f;
