@@ -342,6 +342,32 @@ def run_ours(args):
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_ms, sparsify_ms = (float(x) for x in t.tolist())
 
+    # sparsify time at matched kappa: plain FP32 against BF16 storage of the blocks, each with
+    # kappa(L_G, L_P) of its sparsifier from sfg_kappa (Lanczos; lambda_min certified = 1 by the
+    # component count when it applies). Rank 0 only, outside every timed region above.
+    forms = None
+    if rank == 0 and not args.no_kappa:
+        forms = {}
+        for name, storage in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+            def sp_once():
+                return S.sfg_sparsify(ctx, G, K=K, steps=T, levels=0, omega=OMEGA, seed=SEED,
+                                      budget_frac=BETA, budget_unit=0, storage=storage)[0]
+            mk = sp_once()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_iters):
+                mk = sp_once()
+            torch.cuda.synchronize()
+            ms_form = (time.perf_counter() - t0) / e2e_iters * 1e3
+            t1 = time.perf_counter()
+            kap, lmin, lmax, info = S.sfg_kappa(ctx, G, mk, steps=args.kappa_steps, seed=1, info=True)
+            forms[name] = {"sparsify_ms": ms_form, "kappa": kap, "lambda_max": lmax,
+                           "lambda_min": lmin, "lambda_min_exact": info["lambda_min_exact"],
+                           "lanczos_steps": info["steps"],
+                           "kappa_seconds": time.perf_counter() - t1}
+        forms["bf16"]["kappa_vs_fp32"] = forms["bf16"]["kappa"] / forms["fp32"]["kappa"]
+        forms["bf16"]["speedup_vs_fp32"] = forms["fp32"]["sparsify_ms"] / forms["bf16"]["sparsify_ms"]
+
     if rank != 0:
         return 0
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -360,6 +386,8 @@ def run_ours(args):
                    "what": "pinned host edge list -> H2D -> sfg_laplacian -> sfg_sparsify (flat) -> D2H mask"},
            "sparsify_ms": sparsify_ms,
            "gpu_launches": launches}
+    if forms:
+        out["sparsify_forms"] = forms
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)
@@ -373,6 +401,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-kappa", action="store_true",
+                    help="skip the sparsify-forms report (FP32 vs BF16 sparsify time and kappa)")
+    ap.add_argument("--kappa-steps", type=int, default=60)
     ap.add_argument("--profile", action="store_true",
                     help="time only the filter+score steps (for ncu launch lists and counters)")
     args = ap.parse_args()

@@ -269,6 +269,29 @@ SFG_API sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* c
                                         const sfg_params* params, uint8_t* const* masks_out,
                                         int64_t* n_selected_host);
 
+/* Relative condition number kappa(L_G, L_P) of Sec. 2.2 (Eq. eqn:ineq), the paper's measure of
+ * sparsifier quality, for P = the edges of G with mask[e] != 0 (m entries, device). kappa =
+ * lambda_max / lambda_min of L_G x = lambda L_P x on the complement of the common null space,
+ * estimated from `steps` steps of FP64 Lanczos on L_P^+ L_G in the L_P inner product with full
+ * reorthogonalisation, started from a vector seeded by `seed`; the Krylov dimension is capped at
+ * n - (number of components), at which the Ritz values are the exact eigenvalues up to FP64
+ * rounding. Each L_P solve eliminates degree <= 2 nodes exactly (parallel rounds) and solves the
+ * remaining core by preconditioned CG to a relative residual of 1e-13 of its own right-hand side
+ * or 1e-12 of the whole one (not in the paper: its experiments report kappa but not how it is
+ * computed). The iteration stops early when the Krylov space is exhausted (beta below 1e-10 of
+ * the largest alpha, a vanishing residual, or a core solve that fails after the first step, which
+ * happens only on a right-hand side made of rounding noise). kappa_host receives kappa (+infinity
+ * if P does not span every component of G; 1 if G has no edges). lambda_min is exactly 1 when
+ * G \ P has more components than G (L_G >= L_P, with equality on the vectors that are constant on
+ * the components of G \ P); that case is detected and used instead of the Ritz value. info_host
+ * (may be NULL, 6 entries) receives {lambda_min, lambda_max, Lanczos steps taken, core CG
+ * iterations in all, 1 if the last step ended on a failed core solve else 0, 1 if lambda_min = 1
+ * was certified by the component count else 0}. Deterministic. Errors: SFG_EINVAL
+ * (bad arguments), SFG_ENOMEM (it keeps 2 (steps + 1) FP64 vectors of n entries), SFG_ETIMEOUT
+ * (the core CG did not converge on the first step). Synchronises. */
+SFG_API sfg_status sfg_kappa(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int steps,
+                             uint64_t seed, double* kappa_host, double* info_host);
+
 /* ---------------------------------------------------------------------------------------------
  * Learned edge proposals (an addition to the paper's method; the paper has no learned part).
  * A small network predicts each candidate edge's score after `steps` sweeps from features of a

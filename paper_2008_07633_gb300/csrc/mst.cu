@@ -147,12 +147,18 @@ sfg_status sfg_count_mask(sfg_ctx* ctx, const uint8_t* mask, int64_t m, int64_t*
 }
 
 sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, uint8_t* mask,
-                        int64_t* n_tree) {
+                        int64_t* n_tree, int32_t* comp_out) {
     const int32_t n = g->n;
     const int64_t m = g->m;
     if (m > 0) SFG_CUDA(ctx, cudaMemsetAsync(mask, 0, m, ctx->stream));
     if (m == 0) {
         if (n_tree) *n_tree = 0;
+        if (comp_out && n > 0) {
+            k_mst_init<<<sfg_grid(ctx, (const void*)k_mst_init, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
+                n, comp_out);
+            ++ctx->launches;
+            SFG_LAUNCH_CHECK(ctx, "k_mst_init");
+        }
         return SFG_OK;
     }
     Scratch s(ctx);
@@ -178,6 +184,9 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
         SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         if (!hflag) {
             if (n_tree) SFG_TRY(sfg_count_mask(ctx, mask, m, n_tree));
+            if (comp_out)
+                SFG_CUDA(ctx, cudaMemcpyAsync(comp_out, comp, sizeof(int32_t) * n,
+                                              cudaMemcpyDeviceToDevice, ctx->stream));
             return SFG_OK;
         }
         k_mst_break<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent); ++ctx->launches;

@@ -135,8 +135,9 @@ sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
                            int32_t* fine2coarse_out);
 sfg_status sfg_subgraph_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* mask,
                              sfg_graph** out);
+// comp_out (optional, n entries): each node's component label, a node of that component.
 sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, uint8_t* mask,
-                        int64_t* n_tree);
+                        int64_t* n_tree, int32_t* comp_out = nullptr);
 sfg_status sfg_smooth_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                            uint64_t seed, sfg_dtype storage, void* X_out);
 // sg, sp (may be NULL): per-column scales applied to raw blocks (projection folded in).

@@ -28,7 +28,7 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_
            "sfg_mlp_destroy", "sfg_mlp_params", "sfg_mlp_set_params", "sfg_mlp_forward",
            "sfg_mlp_gradient", "sfg_mlp_train", "sfg_edge_features", "sfg_sparsify_learned",
            "sfg_autotune", "sfg_tune_set", "sfg_tune_table",
-           "sfg_coarsen", "sfg_backward_map", "sfg_sparsify"]
+           "sfg_coarsen", "sfg_backward_map", "sfg_sparsify", "sfg_kappa"]
 
 
 class SfgError(RuntimeError):
@@ -84,6 +84,7 @@ def lib():
             "sfg_sparsify": [_vp, _vp, ctypes.POINTER(sfg_params), _vp, _pi64],
             "sfg_sparsify_batched": [_vp, _int, ctypes.POINTER(_vp), ctypes.POINTER(sfg_params),
                                      ctypes.POINTER(_vp), _pi64],
+            "sfg_kappa": [_vp, _vp, _vp, _int, _u64, _pdbl, _pdbl],
             "sfg_mlp_create": [_vp, _u64, ctypes.POINTER(_vp)],
             "sfg_autotune": [_vp, _vp, _int, _int, ctypes.POINTER(_int), _pdbl],
             "sfg_tune_set": [_vp, _int, _int, _int, _int],
@@ -336,6 +337,21 @@ def sfg_sparsify(ctx, g, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=SFG_SC
     ns = _i64()
     ctx.check(lib().sfg_sparsify(ctx.h, g.h, ctypes.byref(p), _ptr(out), ctypes.byref(ns)))
     return out, ns.value
+
+
+def sfg_kappa(ctx, g, mask, steps=200, seed=1, info=False):
+    """kappa(L_G, L_P) for P = the masked edges of g; returns (kappa, lambda_min, lambda_max), plus
+    a dict (Lanczos steps, core CG iterations, ended on a failed core solve) when info=True."""
+    mask = mask.contiguous()
+    k = ctypes.c_double()
+    inf = (ctypes.c_double * 6)()
+    ctx.check(lib().sfg_kappa(ctx.h, g.h, _ptr(mask), steps, seed & (2**64 - 1), ctypes.byref(k),
+                              ctypes.cast(inf, _pdbl)))
+    out = (k.value, inf[0], inf[1])
+    if info:
+        return out + ({"steps": int(inf[2]), "cg_iterations": int(inf[3]),
+                       "ended_on_failed_solve": bool(inf[4]), "lambda_min_exact": bool(inf[5])},)
+    return out
 
 
 def sfg_sparsify_batched(ctx, graphs, K=16, steps=15, omega=0.7, seed=0, mode=SFG_SCORE_RATIO,

@@ -457,3 +457,51 @@ def test_kappa_lanczos_matches_dense():
         for mk in (tree, mask):
             kd, kl = O.kappa_dense(g, mk), O.kappa_lanczos(g, mk)
             assert abs(kd - kl) <= 1e-5 * kd, (kd, kl)
+
+
+def test_lambda_min_is_one_when_dropped_edges_leave_extra_components():
+    """L_G = L_P + L_Q >= L_P (Q = G minus P), and any vector constant on the components of Q but
+    not on those of G has L_G x = L_P x != 0: lambda_min(L_G, L_P) = 1 exactly when Q has more
+    components than G, and > 1 otherwise (checked on a cycle, where Q is a single edge and
+    connects nothing)."""
+    import scipy.linalg as sl
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+
+    def ncomp(n, u, v):
+        return connected_components(coo_matrix((np.ones(len(u)), (u, v)), shape=(n, n)),
+                                    directed=False)[0]
+
+    def lam_min(g, mask):
+        LG, LP = O.dense_laplacian(g), O.dense_laplacian(g, mask)
+        keep = np.arange(g.n) != 0  # connected graphs here: ground node 0
+        return sl.eigh(LG[np.ix_(keep, keep)], LP[np.ix_(keep, keep)], eigvals_only=True)[0]
+
+    seen_exact = 0
+    for spec in (gen.grid2d(12, 14, seed=1), gen.random_graph(120, 400, seed=2), gen.knn3d(150, k=6, seed=3)):
+        g = G(*spec)
+        assert ncomp(g.n, g.u, g.v) == 1
+        for mask in (O.mst(g), O.sparsify(g, K=8, steps=10, budget_frac=0.2, budget_unit=1, seed=4)[0]):
+            q = ~mask.astype(bool)
+            extra = ncomp(g.n, g.u[q], g.v[q]) > 1
+            lm = lam_min(g, mask)
+            if extra:
+                assert abs(lm - 1.0) <= 1e-9
+                seen_exact += 1
+            else:
+                assert lm > 1.0 + 1e-9
+    assert seen_exact > 0
+    n = 9  # cycle minus one edge: Q is one edge, Q has n - 1 components > 1, lambda_min = 1
+    g = G(n, np.arange(n), (np.arange(n) + 1) % n, np.ones(n))
+    mask = np.ones(g.m, np.uint8)
+    mask[0] = 0
+    assert abs(lam_min(g, mask) - 1.0) <= 1e-9
+    # complete graph K5 with P = the star at node 0: Q is K4 on the other nodes, node 0 is left
+    # alone in Q, so lambda_min = 1
+    n = 5
+    u, v = np.triu_indices(n, 1)
+    g = G(n, u, v, np.ones(len(u)))
+    star = ((g.u == 0) | (g.v == 0)).astype(np.uint8)
+    q = ~star.astype(bool)
+    assert ncomp(n, g.u[q], g.v[q]) == 2  # node 0 is isolated in Q
+    assert abs(lam_min(g, star) - 1.0) <= 1e-9
