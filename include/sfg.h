@@ -292,6 +292,25 @@ SFG_API sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* c
 SFG_API sfg_status sfg_kappa(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int steps,
                              uint64_t seed, double* kappa_host, double* info_host);
 
+/* Sparsification to a target condition number: P is sigma-similar to G when kappa(L_G, L_P) <=
+ * sigma^2 (Sec. 2.2, Eq. eqn:ineq); Sec. 3.4 builds sparsifiers for a desired kappa and
+ * Algorithm 1 takes sigma as its argument. Flat form: P starts as the maximum spanning forest of G;
+ * each round r = 0, 1, ... measures kappa(L_G, L_P) with sfg_kappa (kappa_steps Lanczos steps) and
+ * stops once it is <= kappa_target (= sigma^2) or r = max_rounds; otherwise it re-embeds G and the
+ * current P from params->seed (params->K, steps, omega, storage, mode), scores every edge of G
+ * outside P and adds the top ones, so that after round r + 1 P holds round-half-up((r + 1) *
+ * batch_frac * base) edges beyond the forest (base = n or the number of off-forest edges, per
+ * params->budget_unit; params->budget_frac is not used). Stops early when no edge is left to add.
+ * mask_out (m entries) receives P; n_selected_host, kappa_trace_host (max_rounds + 1 entries:
+ * kappa after each round, the last entry written is the final kappa) and rounds_host (rounds of
+ * additions performed) may be NULL. params->levels must be 0 (else SFG_EINVAL); kappa_target >= 1,
+ * batch_frac > 0, max_rounds >= 0, kappa_steps >= 1. Synchronises. */
+SFG_API sfg_status sfg_sparsify_to_kappa(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* params,
+                                         double kappa_target, double batch_frac, int max_rounds,
+                                         int kappa_steps, uint8_t* mask_out,
+                                         int64_t* n_selected_host, double* kappa_trace_host,
+                                         int* rounds_host);
+
 /* ---------------------------------------------------------------------------------------------
  * Learned edge proposals (an addition to the paper's method; the paper has no learned part).
  * A small network predicts each candidate edge's score after `steps` sweeps from features of a

@@ -341,3 +341,34 @@ def kappa_lanczos(g: Graph, mask) -> float:
     hi = eigsh(LG, k=1, M=LP, which="LA", return_eigenvectors=False, tol=1e-8)[0]
     inv_lo = eigsh(LP, k=1, M=LG, which="LA", return_eigenvectors=False, tol=1e-8)[0]
     return float(hi * inv_lo)
+
+
+def sparsify_to_kappa(g: Graph, kappa_target, batch_frac, max_rounds, K=8, steps=10, omega=0.7,
+                      seed=0, mode=RATIO, budget_unit=0):
+    """Flat sparsification to a target kappa (Sec. 2.2: kappa <= sigma^2; Sec. 3.4; Algorithm 1's
+    sigma): P = maximum spanning forest; each round measures kappa (dense, exact), stops when it
+    is <= kappa_target or after max_rounds rounds of additions, else embeds G and P from the same
+    seed, scores the edges outside P and adds the top ones so that P holds
+    round_half_up(r * batch_frac * base) edges beyond the forest after round r. Returns
+    (mask, kappa trace, rounds of additions)."""
+    mask = mst(g).astype(np.uint8)
+    forest = int(mask.sum())
+    base = g.n if budget_unit == 0 else g.m - forest
+    trace = []
+    r = 0
+    while True:
+        kap = kappa_dense(g, mask)
+        trace.append(kap)
+        if kap <= kappa_target or r == max_rounds:
+            break
+        target = int(np.floor((r + 1) * batch_frac * base + 0.5))
+        k = min(target - (int(mask.sum()) - forest), g.m - int(mask.sum()))
+        if k <= 0:
+            break
+        xg = smooth(g, K, steps, omega, seed)
+        xp = smooth(g.subgraph(mask), K, steps, omega, seed)
+        cand = np.nonzero(mask == 0)[0].astype(np.int32)
+        sc = score_edges(g, xg, xp, cand, mode)
+        mask[topk(sc, cand, k)] = 1
+        r += 1
+    return mask, trace, r

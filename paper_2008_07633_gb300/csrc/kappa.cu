@@ -1012,6 +1012,15 @@ sfg_status kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int
 
 }  // namespace
 
+sfg_status sfg_kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int steps,
+                          uint64_t seed, double* kappa, double* info6) {
+    double info[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    SFG_TRY(kappa_impl(ctx, G, mask, steps, seed, kappa, info));
+    if (info6)
+        for (int i = 0; i < 6; ++i) info6[i] = info[i];
+    return SFG_OK;
+}
+
 extern "C" SFG_API sfg_status sfg_kappa(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask,
                                         int steps, uint64_t seed, double* kappa_host,
                                         double* info_host) {
@@ -1019,9 +1028,5 @@ extern "C" SFG_API sfg_status sfg_kappa(sfg_ctx* ctx, const sfg_graph* G, const 
     if (!G || !kappa_host) return sfg_fail(ctx, SFG_EINVAL, "sfg_kappa: G and kappa_host are required");
     if (steps < 1) return sfg_fail(ctx, SFG_EINVAL, "sfg_kappa: steps must be >= 1");
     if (G->m > 0) SFG_TRY(sfg_check_dev(ctx, mask, "mask"));
-    double info[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    SFG_TRY(kappa_impl(ctx, G, mask, steps, seed, kappa_host, info));
-    if (info_host)
-        for (int i = 0; i < 6; ++i) info_host[i] = info[i];
-    return SFG_OK;
+    return sfg_kappa_impl(ctx, G, mask, steps, seed, kappa_host, info_host);
 }

@@ -194,6 +194,9 @@ __host__ __device__ inline uint64_t sfg_splitmix64(uint64_t x) {
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
+// kappa(L_G, L_P) for P = the masked edges of G (kappa.cu); info6 (nullable) as sfg_kappa's.
+sfg_status sfg_kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int steps,
+                          uint64_t seed, double* kappa, double* info6);
 sfg_status sfg_pointer_jump(sfg_ctx* ctx, int32_t n, const int32_t* comp, int32_t* parent);
 sfg_status sfg_count_mask(sfg_ctx* ctx, const uint8_t* mask, int64_t m, int64_t* count_host);
 sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,

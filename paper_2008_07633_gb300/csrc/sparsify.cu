@@ -246,3 +246,47 @@ extern "C" sfg_status sfg_sparsify_learned(sfg_ctx* ctx, const sfg_graph* G, con
     if (n_selected_host) SFG_TRY(sfg_count_mask(ctx, mask_out, m, n_selected_host));
     return SFG_OK;
 }
+
+// Sparsification to a target condition number (Sec. 2.2: P is sigma-similar to G when
+// kappa(L_G, L_P) <= sigma^2; Sec. 3.4 aims at a desired kappa; Algorithm 1 takes sigma). Flat:
+// P starts as the maximum spanning forest; each round measures kappa(L_G, L_P) with the Lanczos
+// estimator and stops once it is at most kappa_target, else re-embeds G and the current P from
+// the same seed, scores every edge outside P and adds the top ones, so that P holds
+// round_half_up(r * batch_frac * base) edges beyond the forest after round r.
+extern "C" sfg_status sfg_sparsify_to_kappa(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* P,
+                                            double kappa_target, double batch_frac, int max_rounds,
+                                            int kappa_steps, uint8_t* mask_out,
+                                            int64_t* n_selected_host, double* kappa_trace_host,
+                                            int* rounds_host) {
+    if (!ctx) return SFG_EINVAL;
+    if (!G || !P) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
+    if (!sfg_k_supported(P->K, P->storage))
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K,
+                        (int)P->storage);
+    if (P->steps < 0 || P->levels != 0 || !(P->omega > 0.0 && P->omega <= 1.0) ||
+        (P->budget_unit != 0 && P->budget_unit != 1) ||
+        (P->mode != SFG_SCORE_RATIO && P->mode != SFG_SCORE_G && P->mode != SFG_SCORE_P))
+        return sfg_fail(ctx, SFG_EINVAL, "invalid sfg_params (levels must be 0)");
+    if (!(kappa_target >= 1.0) || !(batch_frac > 0.0) || max_rounds < 0 || kappa_steps < 1)
+        return sfg_fail(ctx, SFG_EINVAL, "invalid kappa_target, batch_frac, max_rounds or kappa_steps");
+    if (G->m > 0) SFG_TRY(sfg_check_dev(ctx, mask_out, "mask_out"));
+    int64_t forest = 0;
+    SFG_TRY(sfg_mst_impl(ctx, G, nullptr, mask_out, &forest));
+    int r = 0;
+    for (;; ++r) {
+        double kap = 1.0;
+        SFG_TRY(sfg_kappa_impl(ctx, G, mask_out, kappa_steps, P->seed ^ 0x6b617070ull, &kap, nullptr));
+        if (kappa_trace_host) kappa_trace_host[r] = kap;
+        if (kap <= kappa_target || r == max_rounds) break;
+        int64_t before = 0, after = 0;
+        SFG_TRY(sfg_count_mask(ctx, mask_out, G->m, &before));
+        sfg_params Pr = *P;
+        Pr.budget_frac = (double)(r + 1) * batch_frac;
+        SFG_TRY(recover(ctx, G, &Pr, P->seed, forest, nullptr, mask_out));
+        SFG_TRY(sfg_count_mask(ctx, mask_out, G->m, &after));
+        if (after == before) break;  // nothing left to add
+    }
+    if (rounds_host) *rounds_host = r;
+    if (n_selected_host) SFG_TRY(sfg_count_mask(ctx, mask_out, G->m, n_selected_host));
+    return SFG_OK;
+}

@@ -28,7 +28,8 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_
            "sfg_mlp_destroy", "sfg_mlp_params", "sfg_mlp_set_params", "sfg_mlp_forward",
            "sfg_mlp_gradient", "sfg_mlp_train", "sfg_edge_features", "sfg_sparsify_learned",
            "sfg_autotune", "sfg_tune_set", "sfg_tune_table",
-           "sfg_coarsen", "sfg_backward_map", "sfg_sparsify", "sfg_kappa"]
+           "sfg_coarsen", "sfg_backward_map", "sfg_sparsify", "sfg_kappa",
+           "sfg_sparsify_to_kappa"]
 
 
 class SfgError(RuntimeError):
@@ -85,6 +86,8 @@ def lib():
             "sfg_sparsify_batched": [_vp, _int, ctypes.POINTER(_vp), ctypes.POINTER(sfg_params),
                                      ctypes.POINTER(_vp), _pi64],
             "sfg_kappa": [_vp, _vp, _vp, _int, _u64, _pdbl, _pdbl],
+            "sfg_sparsify_to_kappa": [_vp, _vp, ctypes.POINTER(sfg_params), _dbl, _dbl, _int, _int,
+                                      _vp, _pi64, _pdbl, ctypes.POINTER(_int)],
             "sfg_mlp_create": [_vp, _u64, ctypes.POINTER(_vp)],
             "sfg_autotune": [_vp, _vp, _int, _int, ctypes.POINTER(_int), _pdbl],
             "sfg_tune_set": [_vp, _int, _int, _int, _int],
@@ -352,6 +355,22 @@ def sfg_kappa(ctx, g, mask, steps=200, seed=1, info=False):
         return out + ({"steps": int(inf[2]), "cg_iterations": int(inf[3]),
                        "ended_on_failed_solve": bool(inf[4]), "lambda_min_exact": bool(inf[5])},)
     return out
+
+
+def sfg_sparsify_to_kappa(ctx, g, kappa_target, batch_frac=0.01, max_rounds=20, kappa_steps=100,
+                          K=8, steps=10, omega=0.7, seed=0, mode=SFG_SCORE_RATIO, budget_unit=0,
+                          storage=torch.float32):
+    """Add edges in batches until kappa(L_G, L_P) <= kappa_target; returns (mask, n_selected,
+    kappa trace, rounds of additions)."""
+    p = sfg_params(K, steps, 0, omega, seed & (2**64 - 1), mode, 0.0, budget_unit, _dt(storage))
+    out = torch.empty(max(g.m, 1), dtype=torch.uint8, device=ctx.device)
+    ns = _i64()
+    trace = (ctypes.c_double * (max_rounds + 1))()
+    rounds = _int()
+    ctx.check(lib().sfg_sparsify_to_kappa(ctx.h, g.h, ctypes.byref(p), kappa_target, batch_frac,
+                                          max_rounds, kappa_steps, _ptr(out), ctypes.byref(ns),
+                                          ctypes.cast(trace, _pdbl), ctypes.byref(rounds)))
+    return out[:g.m], ns.value, list(trace[:rounds.value + 1]), rounds.value
 
 
 def sfg_sparsify_batched(ctx, graphs, K=16, steps=15, omega=0.7, seed=0, mode=SFG_SCORE_RATIO,

@@ -109,3 +109,28 @@ def test_kappa_midsize_lanczos(S, ctx, name):
     print(f"\nKAPPA {name}: n={og.n} gpu={k:.6g} (lmin {lmin:.6g}, lmax {lmax:.6g}) oracle={ref:.6g}"
           f" {info}")
     assert abs(k - ref) <= 0.05 * ref
+
+
+@pytest.mark.parametrize("spec", ["grid", "knn"])
+def test_sparsify_to_kappa_matches_oracle(S, ctx, spec):
+    n, u, v, w = gen.grid2d(28, 28, seed=5) if spec == "grid" else gen.knn3d(700, k=8, seed=9)
+    og = O.canonicalize(n, u, v, w)
+    g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
+    k0 = O.kappa_dense(og, O.mst(og))
+    target = k0 / 4.0
+    om, otrace, orounds = O.sparsify_to_kappa(og, target, batch_frac=0.02, max_rounds=15, K=8,
+                                              steps=10, seed=3)
+    gm, ns, gtrace, grounds = S.sfg_sparsify_to_kappa(ctx, g, target, batch_frac=0.02, max_rounds=15,
+                                                      kappa_steps=5000, K=8, steps=10, seed=3)
+    print(f"\nTO_KAPPA {spec}: target {target:.4g}; oracle rounds {orounds} trace "
+          f"{[round(x, 3) for x in otrace]}; gpu rounds {grounds} trace {[round(x, 3) for x in gtrace]}")
+    assert abs(gtrace[0] - otrace[0]) <= 1e-7 * otrace[0]       # the spanning tree is bit-exact
+    assert abs(grounds - orounds) <= 1
+    assert gtrace[-1] <= target and ns == int(gm.sum().item())
+    # same schedule: each round brings P to the same size
+    assert ns - int(O.mst(og).sum()) == int(np.floor(grounds * 0.02 * n + 0.5))
+    # the GPU's own kappa of its final P equals the dense oracle's
+    assert abs(gtrace[-1] - O.kappa_dense(og, gm.cpu().numpy())) <= 1e-7 * gtrace[-1]
+    # and each GPU round's kappa is within the 5% kappa bar of the oracle's at the same round
+    for a, b in zip(gtrace, otrace):
+        assert abs(a - b) <= 0.05 * b

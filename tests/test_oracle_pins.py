@@ -505,3 +505,37 @@ def test_lambda_min_is_one_when_dropped_edges_leave_extra_components():
     q = ~star.astype(bool)
     assert ncomp(n, g.u[q], g.v[q]) == 2  # node 0 is isolated in Q
     assert abs(lam_min(g, star) - 1.0) <= 1e-9
+
+
+def test_sparsify_to_kappa_loop_invariants():
+    """The kappa-target loop (Sec. 2.2, Sec. 3.4): each round adds exactly the scheduled edges,
+    lambda_max(L_G, L_P) never increases as edges join P (L_P' >= L_P), and the loop stops at the
+    first kappa <= target."""
+    import scipy.linalg as sl
+
+    g = G(*gen.grid2d(24, 24, seed=5))
+    tree = O.mst(g)
+    k0 = O.kappa_dense(g, tree)
+    target = k0 / 3.0
+    mask, trace, rounds = O.sparsify_to_kappa(g, target, batch_frac=0.02, max_rounds=12, K=8,
+                                              steps=10, seed=3)
+    assert trace[0] == k0 and len(trace) == rounds + 1
+    assert trace[-1] <= target and all(k > target for k in trace[:-1])
+    forest = int(tree.sum())
+    assert int(mask.sum()) - forest == int(np.floor(rounds * 0.02 * g.n + 0.5))
+    assert np.all(mask[tree.astype(bool)] == 1)
+
+    def lam_max(m):
+        LG, LP = O.dense_laplacian(g), O.dense_laplacian(g, m)
+        keep = np.arange(g.n) != 0
+        return sl.eigh(LG[np.ix_(keep, keep)], LP[np.ix_(keep, keep)], eigvals_only=True)[-1]
+
+    # replay the rounds: lambda_max is non-increasing along the sequence of sparsifiers
+    prev = lam_max(tree)
+    m = tree.astype(np.uint8).copy()
+    for r in range(1, rounds + 1):
+        mr, _, _ = O.sparsify_to_kappa(g, 1.0, batch_frac=0.02, max_rounds=r, K=8, steps=10, seed=3)
+        assert np.all(mr[m.astype(bool)] == 1)  # rounds only add edges
+        cur = lam_max(mr)
+        assert cur <= prev * (1 + 1e-9)
+        prev, m = cur, mr
