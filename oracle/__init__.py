@@ -71,6 +71,9 @@ def _declare(L):
         "orc_jacobi": (None, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _f64, _f64p]),
         "orc_project": (None, [_i32, _int, _f64p]),
         "orc_smooth": (None, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _f64, _u64, _f64p]),
+        "orc_coloring": (_i32, [_i32, _i64, _i32p, _i32p, _f32p, _i32p]),
+        "orc_gauss_seidel": (None, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _f64, _f64p]),
+        "orc_smooth_gs": (None, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _f64, _u64, _f64p]),
         "orc_score_edges": (None, [_i32, _i64, _i32p, _i32p, _f32p, _f64p, _f64p, _int, _i32p,
                                    _i64, _int, _f64, _f64p]),
         "orc_topk": (None, [_f64p, _i32p, _i64, _i64, _i32p]),
@@ -184,6 +187,28 @@ def project(x):
 def smooth(g: Graph, K, steps, omega=0.7, seed=0):
     x = np.empty((g.n, K), np.float64)
     lib().orc_smooth(*g.args(), K, steps, omega, seed, _p(x, _f64p))
+    return x
+
+
+def coloring(g: Graph):
+    """Jones-Plassmann distance-1 colouring (priority splitmix64(0x636f6c6f72 ^ v)); returns
+    (colour per node, number of colours)."""
+    c = np.empty(g.n, np.int32)
+    nc = lib().orc_coloring(*g.args(), _p(c, _i32p))
+    return c, int(nc)
+
+
+def gauss_seidel(g: Graph, x, steps, omega=1.0):
+    """Gauss-Seidel sweeps on L x = 0 in colour order (Sec. 3.2), FP64."""
+    x = _c(x, np.float64).copy()
+    K = 1 if x.ndim == 1 else x.shape[1]
+    lib().orc_gauss_seidel(*g.args(), K, steps, omega, _p(x, _f64p))
+    return x
+
+
+def smooth_gs(g: Graph, K, steps, omega=1.0, seed=0):
+    x = np.empty((g.n, K), np.float64)
+    lib().orc_smooth_gs(*g.args(), K, steps, omega, seed, _p(x, _f64p))
     return x
 
 

@@ -429,6 +429,72 @@ void sparsify_flat(const Graph& g, const Params& P, uint64_t seed, uint8_t* mask
     recover_edges(g, xg, P, seed, mask);
 }
 
+// Distance-1 colouring by Jones-Plassmann rounds (the Gauss-Seidel smoother's parallel order).
+// Node priority: splitmix64(0x636f6c6f72 xor v), ties by the larger id. In each round every
+// uncoloured node whose priority beats all its uncoloured neighbours is selected; all selected
+// nodes then take the smallest colour not used by an already coloured neighbour. Selected nodes
+// are never adjacent, so the order inside a round does not matter.
+int32_t jp_coloring(const Laplacian& L, std::vector<int32_t>& color) {
+    const int32_t n = L.n;
+    color.assign((size_t)n, -1);
+    auto prio = [](int32_t v) { return splitmix64(0x636f6c6f72ull ^ (uint64_t)(uint32_t)v); };
+    auto beats = [&](int32_t a, int32_t b) {  // a outranks b
+        const uint64_t pa = prio(a), pb = prio(b);
+        return pa > pb || (pa == pb && a > b);
+    };
+    int32_t left = n, ncolors = 0;
+    std::vector<int32_t> sel;
+    while (left > 0) {
+        sel.clear();
+        for (int32_t v = 0; v < n; ++v) {
+            if (color[(size_t)v] >= 0) continue;
+            bool top = true;
+            for (int64_t j = L.row_ptr[(size_t)v]; j < L.row_ptr[(size_t)v + 1] && top; ++j) {
+                const int32_t u = L.col[(size_t)j];
+                if (color[(size_t)u] < 0 && beats(u, v)) top = false;
+            }
+            if (top) sel.push_back(v);
+        }
+        for (int32_t v : sel) {
+            std::vector<char> used;
+            for (int64_t j = L.row_ptr[(size_t)v]; j < L.row_ptr[(size_t)v + 1]; ++j) {
+                const int32_t c = color[(size_t)L.col[(size_t)j]];
+                if (c >= 0) {
+                    if ((size_t)c >= used.size()) used.resize((size_t)c + 1, 0);
+                    used[(size_t)c] = 1;
+                }
+            }
+            int32_t c = 0;
+            while ((size_t)c < used.size() && used[(size_t)c]) ++c;
+            color[(size_t)v] = c;
+            ncolors = std::max(ncolors, c + 1);
+        }
+        left -= (int32_t)sel.size();
+    }
+    return ncolors;
+}
+
+// Gauss-Seidel sweeps on L x = 0 (Sec. 3.2 names Gauss-Seidel relaxation), over the nodes in
+// colour order: x_p <- x_p - omega (L x)_p / D(p,p) with the current values of all neighbours
+// (omega = 1: plain Gauss-Seidel). A node with D(p,p) = 0 is left unchanged.
+void gauss_seidel(const Laplacian& L, const std::vector<int32_t>& color, int32_t ncolors, int K,
+                  int steps, double omega, std::vector<double>& x) {
+    std::vector<double> lx((size_t)K);
+    for (int t = 0; t < steps; ++t)
+        for (int32_t c = 0; c < ncolors; ++c)
+            for (int32_t p = 0; p < L.n; ++p) {
+                if (color[(size_t)p] != c) continue;
+                const double d = L.deg[(size_t)p];
+                if (d == 0.0) continue;
+                for (int k = 0; k < K; ++k) lx[(size_t)k] = d * x[(size_t)p * K + k];
+                for (int64_t j = L.row_ptr[(size_t)p]; j < L.row_ptr[(size_t)p + 1]; ++j) {
+                    const int32_t q = L.col[(size_t)j];
+                    for (int k = 0; k < K; ++k) lx[(size_t)k] -= L.a[(size_t)j] * x[(size_t)q * K + k];
+                }
+                for (int k = 0; k < K; ++k) x[(size_t)p * K + k] -= omega * lx[(size_t)k] / d;
+            }
+}
+
 }  // namespace
 
 extern "C" {
@@ -499,6 +565,38 @@ void orc_smooth(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, cons
     Laplacian L = build_laplacian(make_graph(n, m, cu, cv, cw));
     std::vector<double> xv;
     smooth(L, K, steps, omega, seed, xv);
+    std::copy(xv.begin(), xv.end(), x);
+}
+
+int32_t orc_coloring(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
+                     int32_t* color) {
+    Laplacian L = build_laplacian(make_graph(n, m, cu, cv, cw));
+    std::vector<int32_t> c;
+    const int32_t nc = jp_coloring(L, c);
+    std::copy(c.begin(), c.end(), color);
+    return nc;
+}
+
+void orc_gauss_seidel(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
+                      int K, int steps, double omega, double* x) {
+    Laplacian L = build_laplacian(make_graph(n, m, cu, cv, cw));
+    std::vector<int32_t> c;
+    const int32_t nc = jp_coloring(L, c);
+    std::vector<double> xv(x, x + (size_t)n * K);
+    gauss_seidel(L, c, nc, K, steps, omega, xv);
+    std::copy(xv.begin(), xv.end(), x);
+}
+
+// Seeded vectors, Gauss-Seidel sweeps in colour order, projection.
+void orc_smooth_gs(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
+                   int K, int steps, double omega, uint64_t seed, double* x) {
+    Laplacian L = build_laplacian(make_graph(n, m, cu, cv, cw));
+    std::vector<int32_t> c;
+    const int32_t nc = jp_coloring(L, c);
+    std::vector<double> xv;
+    init_vectors(n, K, seed, xv);
+    gauss_seidel(L, c, nc, K, steps, omega, xv);
+    project(n, K, xv);
     std::copy(xv.begin(), xv.end(), x);
 }
 

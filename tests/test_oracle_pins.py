@@ -539,3 +539,49 @@ def test_sparsify_to_kappa_loop_invariants():
         cur = lam_max(mr)
         assert cur <= prev * (1 + 1e-9)
         prev, m = cur, mr
+
+
+def test_coloring_is_proper_and_grundy():
+    for spec in (gen.grid2d(15, 17, seed=1), gen.knn3d(300, k=8, seed=2), gen.chung_lu(800, seed=3)):
+        g = G(*spec)
+        c, nc = O.coloring(g)
+        assert c.min() == 0 and c.max() == nc - 1 and np.all(c[g.u] != c[g.v])
+        c2, _ = O.coloring(g)
+        assert np.array_equal(c, c2)
+        nb = [set() for _ in range(g.n)]
+        for a, b in zip(g.u, g.v):
+            nb[a].add(int(c[b]))
+            nb[b].add(int(c[a]))
+        for v in range(g.n):  # every smaller colour is taken by some neighbour
+            assert set(range(c[v])) <= nb[v]
+
+
+def test_gauss_seidel_is_the_matrix_splitting():
+    """One sweep in colour order, x <- (D - omega A_L)^-1 ((1 - omega) D + omega A_U) x, with
+    A_L / A_U the parts of A below / above the diagonal in the (colour, id) node order; constants
+    are fixed points; the energy x^T L x never increases for 0 < omega < 2."""
+    g = G(*gen.random_graph(60, 200, seed=4))
+    c, _ = O.coloring(g)
+    order = np.lexsort((np.arange(g.n), c))
+    pos = np.empty(g.n, int)
+    pos[order] = np.arange(g.n)
+    L = O.dense_laplacian(g)
+    A = np.diag(np.diag(L)) - L
+    D = np.diag(np.diag(L))
+    P = np.eye(g.n)[order]                      # row i of P x = x[order[i]]
+    Ao = P @ A @ P.T
+    AL, AU, Do = np.tril(Ao, -1), np.triu(Ao, 1), P @ D @ P.T
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((g.n, 3))
+    for om in (1.0, 0.7, 1.4):
+        ref = P.T @ np.linalg.solve(Do - om * AL, ((1 - om) * Do + om * AU) @ (P @ x))
+        got = O.gauss_seidel(g, x, 1, om)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        e = [np.einsum("ik,ij,jk->k", x, L, x)]
+        y = x
+        for _ in range(4):
+            y = O.gauss_seidel(g, y, 1, om)
+            e.append(np.einsum("ik,ij,jk->k", y, L, y))
+        assert np.all(np.diff(np.array(e), axis=0) <= 1e-9 * e[0])
+    ones = np.ones((g.n, 2)) * 3.5
+    assert np.allclose(O.gauss_seidel(g, ones, 3, 1.0), ones, rtol=0, atol=1e-13)
