@@ -132,6 +132,25 @@ SFG_API sfg_status sfg_graph_subgraph(sfg_ctx* ctx, const sfg_graph* g, const ui
  * SFG_EUNSUPPORTED. 0 < omega <= 1, steps >= 0. */
 SFG_API sfg_status sfg_smooth(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                       uint64_t seed, sfg_dtype storage, void* X_out);
+/* Multicolour Gauss-Seidel smoothing, the paper's relaxation (Sec. 3.2: Gauss-Seidel sweeps on
+ * L x = 0 from K random vectors orthogonal to the all-one vector). Same seeded block and final
+ * projection as sfg_smooth; the sweeps visit the colour classes of a distance-1 colouring
+ * (sfg_coloring) in order, each class updated in place and in parallel:
+ * x_p <- (1 - omega) x_p + omega (A x)_p / D(p,p) with the current values of all neighbours
+ * (omega = 1: plain Gauss-Seidel; 0 < omega < 2). The result equals the sequential sweep over the
+ * nodes sorted by (colour, id). The colouring is built on first use and cached with the graph.
+ * Layout, storage and errors as sfg_smooth, except omega. */
+SFG_API sfg_status sfg_smooth_gs(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
+                                 uint64_t seed, sfg_dtype storage, void* X_out);
+
+/* Distance-1 colouring used by sfg_smooth_gs (Jones-Plassmann: node priority
+ * splitmix64(0x636f6c6f72 xor v), ties by the larger id; each round colours every uncoloured node
+ * that outranks its uncoloured neighbours with the smallest colour none of its coloured
+ * neighbours holds). color_out (n entries, device, may be NULL) receives colours 0..c-1 and
+ * ncolors_host (may be NULL) receives c. Deterministic. Synchronises. */
+SFG_API sfg_status sfg_coloring(sfg_ctx* ctx, const sfg_graph* L, int32_t* color_out,
+                                int32_t* ncolors_host);
+
 /* Only step 2 of sfg_smooth, in place on a caller-provided block (no init, no projection). */
 SFG_API sfg_status sfg_jacobi(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                       sfg_dtype storage, void* X_inout);
@@ -246,7 +265,12 @@ typedef struct {
     double budget_frac; /* beta: each level ends with round(beta * base) edges beyond a forest */
     int budget_unit;    /* 0: base = N_l; 1: base = number of off-tree edges of G_l */
     sfg_dtype storage;  /* vector block storage */
+    int smoother;       /* SFG_SMOOTH_JACOBI (omega in (0, 1]) or SFG_SMOOTH_GAUSS_SEIDEL
+                           (multicolour, sfg_smooth_gs; omega in (0, 2), 1 = plain) */
 } sfg_params;
+
+/* Smoothers of sfg_params.smoother. */
+enum { SFG_SMOOTH_JACOBI = 0, SFG_SMOOTH_GAUSS_SEIDEL = 1 };
 
 /* mask_out[e] (m entries) = 1 for the edges of the sparsifier P of G. Flat: maximum spanning
  * forest, then the top-scored off-tree edges. Multilevel: coarsen `levels` times (stopping early

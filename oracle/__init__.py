@@ -397,3 +397,22 @@ def sparsify_to_kappa(g: Graph, kappa_target, batch_frac, max_rounds, K=8, steps
         mask[topk(sc, cand, k)] = 1
         r += 1
     return mask, trace, r
+
+
+def sparsify_flat(g: Graph, K=8, steps=10, omega=0.7, seed=0, mode=RATIO, budget_frac=0.1,
+                  budget_unit=1, smoother="jacobi"):
+    """Flat Algorithm 1 (lines 13-14 on the spanning forest) with either smoother: P = maximum
+    spanning forest; embed G and P from the same seed with weighted Jacobi or Gauss-Seidel (colour
+    order), score the edges outside P, add the top round_half_up(beta * base) of them."""
+    mask = mst(g).astype(np.uint8)
+    forest = int(mask.sum())
+    base = g.n if budget_unit == 0 else g.m - forest
+    k = min(int(np.floor(budget_frac * base + 0.5)), g.m - forest)
+    if k <= 0:
+        return mask
+    sm = smooth_gs if smoother == "gs" else smooth
+    xg = sm(g, K, steps, omega, seed)
+    xp = sm(g.subgraph(mask), K, steps, omega, seed)
+    cand = np.nonzero(mask == 0)[0].astype(np.int32)
+    mask[topk(score_edges(g, xg, xp, cand, mode), cand, k)] = 1
+    return mask

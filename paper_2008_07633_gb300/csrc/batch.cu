@@ -147,6 +147,8 @@ extern "C" sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "the batched form is flat (levels = 0)");
     if (!sfg_k_supported(P->K, P->storage))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K, (int)P->storage);
+    if (P->smoother != SFG_SMOOTH_JACOBI)
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "the batched form uses the Jacobi smoother only");
     if (P->steps < 0 || !(P->omega > 0.0 && P->omega <= 1.0) || !(P->budget_frac >= 0.0) ||
         (P->budget_unit != 0 && P->budget_unit != 1) ||
         (P->mode != SFG_SCORE_RATIO && P->mode != SFG_SCORE_G && P->mode != SFG_SCORE_P))

@@ -202,7 +202,8 @@ int grid_of(sfg_ctx* ctx, K kernel, int64_t work) {
 void sfg_graph_free(sfg_graph* g) {
     if (!g) return;
     cudaStream_t s = g->stream;
-    void* ptrs[] = {g->eu, g->ev, g->ew, g->row_ptr, g->colval, g->eid, g->deg, g->invdeg};
+    void* ptrs[] = {g->eu, g->ev, g->ew, g->row_ptr, g->colval, g->eid, g->deg, g->invdeg,
+                    g->gs_color, g->gs_order};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
     delete g;

@@ -46,6 +46,11 @@ struct sfg_graph {
     int32_t* eid = nullptr;    // [2m] canonical edge id of each CSR entry
     double* deg = nullptr;     // [n]
     double* invdeg = nullptr;  // [n] 1 / deg in FP64 (0 for isolated nodes)
+    // Gauss-Seidel colouring, built on first use (color.cu): colour per node, the nodes sorted
+    // by (colour, id), and colour c's nodes at gs_order[gs_off[c], gs_off[c + 1]).
+    int32_t* gs_color = nullptr;
+    int32_t* gs_order = nullptr;
+    std::vector<int64_t> gs_off;
     cudaStream_t stream = nullptr;
 };
 
@@ -197,6 +202,15 @@ __host__ __device__ inline uint64_t sfg_splitmix64(uint64_t x) {
 // kappa(L_G, L_P) for P = the masked edges of G (kappa.cu); info6 (nullable) as sfg_kappa's.
 sfg_status sfg_kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int steps,
                           uint64_t seed, double* kappa, double* info6);
+// Build the Gauss-Seidel colouring of L once (cached on the graph; color.cu).
+sfg_status sfg_gs_prepare(sfg_ctx* ctx, const sfg_graph* L);
+// y_p = d_p - omega * (weight to nodes after p in (colour, id) order): the weights of the
+// quantity y^T x that the colour-ordered SOR sweep conserves (color.cu).
+__global__ void k_gs_weights(int32_t n, const int32_t* __restrict__ row_ptr,
+                             const int2* __restrict__ colval, const int32_t* __restrict__ color,
+                             double omega, double* __restrict__ y);
+sfg_status sfg_smooth_gs_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
+                              uint64_t seed, sfg_dtype storage, void* X_out);
 sfg_status sfg_pointer_jump(sfg_ctx* ctx, int32_t n, const int32_t* comp, int32_t* parent);
 sfg_status sfg_count_mask(sfg_ctx* ctx, const uint8_t* mask, int64_t m, int64_t* count_host);
 sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,

@@ -317,6 +317,91 @@ __global__ void __launch_bounds__(kBlock, MINB)
     if (STATS) block_column_partials<LPR, E>(s1, s2, part);
 }
 
+// One colour class of a multicolour Gauss-Seidel sweep (Sec. 3.2 relaxes L x = 0 with
+// Gauss-Seidel): rows[0, cnt) are pairwise non-adjacent, so each is updated in place from the
+// current values of its neighbours, x_p <- (1 - omega) x_p + (omega / D(p,p)) (A x)_p, which is the
+// sequential sweep restricted to this class. Same group layout and gathers as the Jacobi sweep;
+// the tile's rows come from the class list, one tile at a time. X is read and written through
+// plain pointers (rows of this class are written, only rows of other classes are gathered).
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kBlock, 4)
+    k_gs(int32_t cnt, const int32_t* __restrict__ rows, const int32_t* __restrict__ row_ptr,
+         const int2* __restrict__ colval, const float* __restrict__ coef, float a_self, T* X) {
+    constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR, C = Chunk<LPR>::C;
+    const int lane = threadIdx.x & 31, grp = lane / LPR, sub = lane % LPR;
+    const unsigned gm = group_mask<LPR>(lane);
+    const int32_t wid = (int32_t)((blockIdx.x * kBlock + threadIdx.x) >> 5);
+    const int32_t nw = (int32_t)(gridDim.x * (kBlock / 32));
+    const int32_t ntiles = (cnt + GPW - 1) / GPW;
+    const T* Xl = X + sub * E;
+    for (int32_t t = wid; t < ntiles; t += nw) {
+        const int32_t i = t * GPW + lane;
+        int32_t r = -1, lo = 0, hi = 0;
+        float cf = 0.f;
+        if (lane < GPW && i < cnt) {
+            r = rows[i];
+            lo = row_ptr[r];
+            hi = row_ptr[r + 1];
+            cf = coef[r];
+        }
+        const int32_t row = __shfl_sync(0xffffffffu, r, grp);
+        const int32_t a = __shfl_sync(0xffffffffu, lo, grp);
+        const int32_t b = __shfl_sync(0xffffffffu, hi, grp);
+        const float cp = __shfl_sync(0xffffffffu, cf, grp);
+        const bool live = row >= 0;
+        const int32_t first = __shfl_sync(0xffffffffu, r, 0);  // all lanes: the tile's first row
+        const int32_t self = live ? row : first;
+        const int32_t deg = b - a;
+        const int32_t maxdeg = __reduce_max_sync(0xffffffffu, deg);
+        Chunk<LPR> ch;
+        ch.load(colval, a, b, self, sub);
+        float acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        gather_chunk<T, LPR>(ch, min(maxdeg, C), gm, Xl, acc);
+        for (int32_t j0 = C; j0 < maxdeg; j0 += C) {
+            Chunk<LPR> cx;
+            cx.load(colval, a + j0, b, self, sub);
+            gather_chunk<T, LPR>(cx, min(maxdeg - j0, C), gm, Xl, acc);
+        }
+        if (live && deg > 0) {
+            T* xp = X + (int64_t)self * K + sub * E;
+            float xs[E], y[E];
+            Vec<T>::load(xp, xs);
+#pragma unroll
+            for (int e = 0; e < E; ++e) y[e] = fmaf(cp, acc[e], a_self * xs[e]);
+            Vec<T>::store(xp, y);
+        }
+    }
+}
+
+__global__ void k_fill(int k, float v, float* __restrict__ p) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) p[i] = v;
+}
+
+// Per-block column sums and sums of squares of a stored block (values as stored).
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kBlock) k_col_stats(int32_t n, const T* __restrict__ X,
+                                                      double* __restrict__ part) {
+    constexpr int E = Vec<T>::E, K = LPR * E;
+    const int sub = (threadIdx.x & 31) % LPR;
+    float s1[E], s2[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) s1[e] = s2[e] = 0.f;
+    const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
+    const int64_t gs = (int64_t)gridDim.x * kBlock / LPR;
+    for (int64_t r = g0; r < n; r += gs) {
+        float x[E];
+        Vec<T>::load(X + r * K + sub * E, x);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            s1[e] += x[e];
+            s2[e] = fmaf(x[e], x[e], s2[e]);
+        }
+    }
+    block_column_partials<LPR, E>(s1, s2, part);
+}
+
 // Fold the per-block partials (FP64): one CTA per column, each thread sums a fixed stride of
 // blocks, then a fixed-shape tree, so the result does not depend on scheduling.
 // proj = 0: mean only (mu = S1 / n). proj = 1: mean and scale = 1 / RMS of the centred column
@@ -622,6 +707,59 @@ struct Smoother {
         return SFG_OK;
     }
 
+    // Multicolour Gauss-Seidel smoothing: seeded block with its y-weighted column mean removed
+    // (y: the weights of the quantity the ordered sweep conserves, so the block converges to
+    // zero instead of to a constant; a constant shift commutes with the sweeps and the final
+    // projection removes it either way), `steps` sweeps of one launch per colour class in
+    // place, projection.
+    static sfg_status smooth_gs(sfg_ctx* ctx, const sfg_graph* L, int steps, double omega,
+                                uint64_t seed, T* X_out) {
+        const int32_t n = L->n;
+        SFG_TRY(sfg_gs_prepare(ctx, L));
+        const int grid = grid_jacobi(ctx, n);
+        const int gstat = sfg_grid(ctx, (const void*)k_col_stats<T, LPR>, kBlock, 0, (int64_t)n * LPR);
+        Scratch s(ctx);
+        T* buf;
+        float *coef, *mu, *scale;
+        double* part;
+        SFG_TRY(s.get(&buf, (size_t)n * K));
+        SFG_TRY(s.get(&coef, (size_t)n));
+        SFG_TRY(s.get(&mu, K));
+        SFG_TRY(s.get(&scale, K));
+        SFG_TRY(s.get(&part, (size_t)std::max(grid, gstat) * 2 * K));
+        double* yw;
+        SFG_TRY(s.get(&yw, (size_t)n));
+        k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
+            n, L->invdeg, omega, coef);
+        k_gs_weights<<<sfg_grid(ctx, (const void*)k_gs_weights, kBlock, 0, n), kBlock, 0,
+                       ctx->stream>>>(n, L->row_ptr, L->colval, L->gs_color, omega, yw);
+        k_init<T, LPR, true><<<grid, kBlock, 0, ctx->stream>>>(n, seed, yw, X_out, part);
+        k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, 2, mu, scale);
+        k_fill<<<1, 64, 0, ctx->stream>>>(K, 1.0f, scale);
+        const int gp = sfg_grid(ctx, (const void*)k_project<T, LPR>, kBlock, 0, (int64_t)n * LPR);
+        k_project<T, LPR><<<gp, kBlock, 0, ctx->stream>>>(n, X_out, buf, mu, scale);
+        ctx->launches += 6;
+        SFG_LAUNCH_CHECK(ctx, "gs init");
+        const float a_self = (float)(1.0 - omega);
+        const int ncol = (int)L->gs_off.size() - 1;
+        for (int t = 0; t < steps; ++t)
+            for (int c = 0; c < ncol; ++c) {
+                const int64_t c0 = L->gs_off[c], cnt = L->gs_off[c + 1] - c0;
+                if (cnt == 0) continue;
+                const int g = sfg_grid(ctx, (const void*)k_gs<T, LPR>, kBlock, 0, cnt * LPR);
+                k_gs<T, LPR><<<g, kBlock, 0, ctx->stream>>>((int32_t)cnt, L->gs_order + c0,
+                                                            L->row_ptr, L->colval, coef, a_self, buf);
+                ++ctx->launches;
+            }
+        SFG_LAUNCH_CHECK(ctx, "k_gs");
+        k_col_stats<T, LPR><<<gstat, kBlock, 0, ctx->stream>>>(n, buf, part);
+        k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, gstat, K, n, 1, mu, scale);
+        k_project<T, LPR><<<gp, kBlock, 0, ctx->stream>>>(n, buf, X_out, mu, scale);
+        ctx->launches += 3;
+        SFG_LAUNCH_CHECK(ctx, "gs projection");
+        return SFG_OK;
+    }
+
     // Sweeps of one Laplacian from the block x0 (not overwritten) through the ping-pong pair
     // (b0, b1); *out = the raw smoothed block, mean/scale = its projection statistics.
     static sfg_status sweeps_from(sfg_ctx* ctx, const sfg_graph* L, int steps, double omega,
@@ -874,6 +1012,14 @@ sfg_status sfg_smooth_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, d
     });
 }
 
+sfg_status sfg_smooth_gs_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
+                              uint64_t seed, sfg_dtype storage, void* X_out) {
+    return dispatch(K, storage, [&](auto S) {
+        using Sm = decltype(S);
+        return Sm::smooth_gs(ctx, L, steps, omega, seed, static_cast<typename Sm::Elem*>(X_out));
+    });
+}
+
 sfg_status sfg_filter_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
                                  int steps, double omega, uint64_t seed, sfg_dtype storage,
                                  const int32_t* ids, int64_t ne, sfg_score_mode mode,
@@ -923,6 +1069,15 @@ sfg_status sfg_smooth(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double
     if (!ctx) return SFG_EINVAL;
     SFG_TRY(check_smooth_args(ctx, L, K, steps, omega, storage, X_out));
     return sfg_smooth_impl(ctx, L, K, steps, omega, seed, storage, X_out);
+}
+
+sfg_status sfg_smooth_gs(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
+                         uint64_t seed, sfg_dtype storage, void* X_out) {
+    if (!ctx) return SFG_EINVAL;
+    if (!(omega > 0.0 && omega < 2.0))
+        return sfg_fail(ctx, SFG_EINVAL, "omega must be in (0, 2) for Gauss-Seidel");
+    SFG_TRY(check_smooth_args(ctx, L, K, steps, 1.0, storage, X_out));
+    return sfg_smooth_gs_impl(ctx, L, K, steps, omega, seed, storage, X_out);
 }
 
 sfg_status sfg_jacobi(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,

@@ -38,6 +38,20 @@ __global__ void k_f32_to_bf16(int64_t n, const float* __restrict__ x, __nv_bfloa
         y[i] = __float2bfloat16_rn(x[i]);
 }
 
+// Smoother choice and its omega range: weighted Jacobi (0, 1], Gauss-Seidel / SOR (0, 2).
+bool omega_ok(const sfg_params* P) {
+    if (P->smoother == SFG_SMOOTH_JACOBI) return P->omega > 0.0 && P->omega <= 1.0;
+    if (P->smoother == SFG_SMOOTH_GAUSS_SEIDEL) return P->omega > 0.0 && P->omega < 2.0;
+    return false;
+}
+
+sfg_status smooth_any(sfg_ctx* ctx, const sfg_params* P, const sfg_graph* g, uint64_t seed,
+                      sfg_dtype storage, void* x) {
+    if (P->smoother == SFG_SMOOTH_GAUSS_SEIDEL)
+        return sfg_smooth_gs_impl(ctx, g, P->K, P->steps, P->omega, seed, storage, x);
+    return sfg_smooth_impl(ctx, g, P->K, P->steps, P->omega, seed, storage, x);
+}
+
 uint64_t level_seed(uint64_t seed, int l) { return l == 0 ? seed : sfg_splitmix64(seed ^ (uint64_t)l); }
 
 int64_t round_half_up(double x) { return (int64_t)std::floor(x + 0.5); }
@@ -81,7 +95,19 @@ sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64
     SFG_TRY(sfg_subgraph_impl(ctx, g, mask, &pg));
     struct Guard { sfg_graph* g; ~Guard() { sfg_graph_free(g); } } guard{pg};
 
-    if (!XG_f32) {  // embed G and P from one seeded block and score in one pass
+    if (P->smoother == SFG_SMOOTH_GAUSS_SEIDEL) {  // the paper's smoother: embed both, then score
+        const size_t blk = (size_t)g->n * P->K * elem_size(P->storage);
+        void *xg, *xp;
+        SFG_TRY(s.get((char**)&xp, blk));
+        if (XG_f32 && P->storage == SFG_F32) {
+            xg = const_cast<float*>(XG_f32);
+        } else {
+            SFG_TRY(s.get((char**)&xg, blk));
+            SFG_TRY(sfg_smooth_gs_impl(ctx, g, P->K, P->steps, P->omega, seed, P->storage, xg));
+        }
+        SFG_TRY(sfg_smooth_gs_impl(ctx, pg, P->K, P->steps, P->omega, seed, P->storage, xp));
+        SFG_TRY(sfg_score_impl(ctx, g, xg, xp, P->K, P->storage, cand, ncand, P->mode, scores));
+    } else if (!XG_f32) {  // embed G and P from one seeded block and score in one pass
         SFG_TRY(sfg_filter_score_impl(ctx, g, pg, P->K, P->steps, P->omega, seed, P->storage, cand,
                                       ncand, P->mode, scores));
     } else {  // reuse the level's cached FP32 embedding of G
@@ -125,7 +151,7 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
     if (!sfg_k_supported(P->K, P->storage) || !sfg_k_supported(P->K, SFG_F32))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K,
                         (int)P->storage);
-    if (P->steps < 0 || P->levels < 0 || !(P->omega > 0.0 && P->omega <= 1.0) ||
+    if (P->steps < 0 || P->levels < 0 || !omega_ok(P) ||
         !(P->budget_frac >= 0.0) || (P->budget_unit != 0 && P->budget_unit != 1) ||
         (P->mode != SFG_SCORE_RATIO && P->mode != SFG_SCORE_G && P->mode != SFG_SCORE_P))
         return sfg_fail(ctx, SFG_EINVAL, "invalid sfg_params");
@@ -146,8 +172,7 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
         Level& f = lv.back();
         if (f.g->m == 0) break;
         SFG_TRY(s.get(&f.xg, (size_t)f.g->n * P->K));
-        SFG_TRY(sfg_smooth_impl(ctx, f.g, P->K, P->steps, P->omega, level_seed(P->seed, l - 1),
-                                SFG_F32, f.xg));
+        SFG_TRY(smooth_any(ctx, P, f.g, level_seed(P->seed, l - 1), SFG_F32, f.xg));
         Level c;
         SFG_TRY(s.get(&c.agg, f.g->n));
         SFG_TRY(s.get(&c.f2c, f.g->m));
@@ -188,6 +213,8 @@ extern "C" sfg_status sfg_sparsify_learned(sfg_ctx* ctx, const sfg_graph* G, con
     if (!ctx) return SFG_EINVAL;
     if (!G || !P) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
     if (P->levels != 0) return sfg_fail(ctx, SFG_EUNSUPPORTED, "learned proposals are flat (levels = 0)");
+    if (P->smoother != SFG_SMOOTH_JACOBI)
+        return sfg_fail(ctx, SFG_EUNSUPPORTED, "learned proposals use the Jacobi smoother only");
     if (!net || !(propose_frac < 1.0)) return sfg_sparsify(ctx, G, P, mask_out, n_selected_host);
     if (!sfg_k_supported(P->K, P->storage))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K, (int)P->storage);
@@ -263,7 +290,7 @@ extern "C" sfg_status sfg_sparsify_to_kappa(sfg_ctx* ctx, const sfg_graph* G, co
     if (!sfg_k_supported(P->K, P->storage))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K,
                         (int)P->storage);
-    if (P->steps < 0 || P->levels != 0 || !(P->omega > 0.0 && P->omega <= 1.0) ||
+    if (P->steps < 0 || P->levels != 0 || !omega_ok(P) ||
         (P->budget_unit != 0 && P->budget_unit != 1) ||
         (P->mode != SFG_SCORE_RATIO && P->mode != SFG_SCORE_G && P->mode != SFG_SCORE_P))
         return sfg_fail(ctx, SFG_EINVAL, "invalid sfg_params (levels must be 0)");

@@ -29,7 +29,7 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_
            "sfg_mlp_gradient", "sfg_mlp_train", "sfg_edge_features", "sfg_sparsify_learned",
            "sfg_autotune", "sfg_tune_set", "sfg_tune_table",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify", "sfg_kappa",
-           "sfg_sparsify_to_kappa"]
+           "sfg_sparsify_to_kappa", "sfg_smooth_gs", "sfg_coloring"]
 
 
 class SfgError(RuntimeError):
@@ -42,7 +42,10 @@ class sfg_params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("steps", ctypes.c_int), ("levels", ctypes.c_int),
                 ("omega", ctypes.c_double), ("seed", ctypes.c_uint64), ("mode", ctypes.c_int),
                 ("budget_frac", ctypes.c_double), ("budget_unit", ctypes.c_int),
-                ("storage", ctypes.c_int)]
+                ("storage", ctypes.c_int), ("smoother", ctypes.c_int)]
+
+
+SFG_SMOOTH_JACOBI, SFG_SMOOTH_GAUSS_SEIDEL = 0, 1
 
 
 _lib = None
@@ -74,6 +77,8 @@ def lib():
             "sfg_graph_subgraph": [_vp, _vp, _vp, ctypes.POINTER(_vp)],
             "sfg_smooth": [_vp, _vp, _int, _int, _dbl, _u64, _int, _vp],
             "sfg_jacobi": [_vp, _vp, _int, _int, _dbl, _int, _vp],
+            "sfg_smooth_gs": [_vp, _vp, _int, _int, _dbl, _u64, _int, _vp],
+            "sfg_coloring": [_vp, _vp, _vp, _pi32],
             "sfg_score_edges": [_vp, _vp, _vp, _vp, _int, _int, _vp, _i64, _int, _vp],
             "sfg_select_topk": [_vp, _vp, _vp, _i64, _i64, _vp],
             "sfg_filter_score": [_vp, _vp, _vp, _int, _int, _dbl, _u64, _int, _vp, _i64, _int, _vp],
@@ -256,6 +261,23 @@ def sfg_smooth(ctx, g, K, steps, omega=0.7, seed=0, storage=torch.float32, out=N
     return out
 
 
+def sfg_smooth_gs(ctx, g, K, steps, omega=1.0, seed=0, storage=torch.float32, out=None):
+    """Multicolour Gauss-Seidel smoothing; returns the projected n x K block."""
+    if out is None:
+        out = torch.empty((g.n, K), dtype=storage, device=ctx.device)
+    ctx.check(lib().sfg_smooth_gs(ctx.h, g.h, K, steps, omega, seed & (2**64 - 1), _dt(storage),
+                                  _ptr(out)))
+    return out
+
+
+def sfg_coloring(ctx, g):
+    """(colour per node, number of colours) of the Gauss-Seidel colouring."""
+    c = torch.empty(max(g.n, 1), dtype=torch.int32, device=ctx.device)
+    nc = _i32()
+    ctx.check(lib().sfg_coloring(ctx.h, g.h, _ptr(c), ctypes.byref(nc)))
+    return c[:g.n], nc.value
+
+
 def sfg_jacobi(ctx, g, X, steps, omega=0.7):
     assert X.is_contiguous()
     ctx.check(lib().sfg_jacobi(ctx.h, g.h, X.shape[1], steps, omega, _dt(X.dtype), _ptr(X)))
@@ -332,9 +354,10 @@ def sfg_backward_map(ctx, fine, agg, f2c, coarse, pmask_c):
 
 
 def sfg_sparsify(ctx, g, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=SFG_SCORE_RATIO,
-                 budget_frac=0.1, budget_unit=1, storage=torch.float32, out=None):
+                 budget_frac=0.1, budget_unit=1, storage=torch.float32, out=None,
+                 smoother=SFG_SMOOTH_JACOBI):
     p = sfg_params(K, steps, levels, omega, seed & (2**64 - 1), mode, budget_frac, budget_unit,
-                   _dt(storage))
+                   _dt(storage), smoother)
     if out is None:
         out = torch.empty(g.m, dtype=torch.uint8, device=ctx.device)
     ns = _i64()
@@ -359,10 +382,11 @@ def sfg_kappa(ctx, g, mask, steps=200, seed=1, info=False):
 
 def sfg_sparsify_to_kappa(ctx, g, kappa_target, batch_frac=0.01, max_rounds=20, kappa_steps=100,
                           K=8, steps=10, omega=0.7, seed=0, mode=SFG_SCORE_RATIO, budget_unit=0,
-                          storage=torch.float32):
+                          storage=torch.float32, smoother=SFG_SMOOTH_JACOBI):
     """Add edges in batches until kappa(L_G, L_P) <= kappa_target; returns (mask, n_selected,
     kappa trace, rounds of additions)."""
-    p = sfg_params(K, steps, 0, omega, seed & (2**64 - 1), mode, 0.0, budget_unit, _dt(storage))
+    p = sfg_params(K, steps, 0, omega, seed & (2**64 - 1), mode, 0.0, budget_unit, _dt(storage),
+                   smoother)
     out = torch.empty(max(g.m, 1), dtype=torch.uint8, device=ctx.device)
     ns = _i64()
     trace = (ctypes.c_double * (max_rounds + 1))()

@@ -67,7 +67,9 @@ def test_host_side_status_without_gpu(lib):
 def test_params_struct_layout():
     import paper_2008_07633_gb300.sfg as S
 
-    # C layout of sfg_params on LP64: 3 ints, pad, double, uint64, enum, pad, double, int, enum
-    assert ctypes.sizeof(S.sfg_params) == 56
+    # C layout of sfg_params on LP64: 3 ints, pad, double, uint64, enum, pad, double, int, enum,
+    # int, pad
+    assert ctypes.sizeof(S.sfg_params) == 64
     assert S.sfg_params.omega.offset == 16 and S.sfg_params.seed.offset == 24
     assert S.sfg_params.budget_frac.offset == 40 and S.sfg_params.storage.offset == 52
+    assert S.sfg_params.smoother.offset == 56

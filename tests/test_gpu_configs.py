@@ -252,7 +252,7 @@ def test_sparsify_batched_kappa_vs_oracle(S, ctx):
 def test_sparsify_batched_rejects_multilevel(S, ctx):
     n, u, v, w = gen.grid2d(8, 8)
     g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
-    p = S.sfg_params(16, 5, 1, 0.7, 0, 0, 0.1, 0, 0)
+    p = S.sfg_params(16, 5, 1, 0.7, 0, 0, 0.1, 0, 0, 0)
     m = torch.empty(g.m, dtype=torch.uint8, device=DEV)
     import ctypes
     st = S.lib().sfg_sparsify_batched(ctx.h, 1, (ctypes.c_void_p * 1)(g.h), ctypes.byref(p),

@@ -585,3 +585,26 @@ def test_gauss_seidel_is_the_matrix_splitting():
         assert np.all(np.diff(np.array(e), axis=0) <= 1e-9 * e[0])
     ones = np.ones((g.n, 2)) * 3.5
     assert np.allclose(O.gauss_seidel(g, ones, 3, 1.0), ones, rtol=0, atol=1e-13)
+
+
+def test_gauss_seidel_conserves_the_ordered_weighted_sum():
+    """A colour-ordered SOR sweep keeps y^T x with y_p = d_p - omega * (weight to nodes after p in
+    (colour, id) order): y^T = 1^T (D - omega A_L) is the left fixed vector of the sweep matrix.
+    (This is why the GPU removes the y-weighted mean before Gauss-Seidel sweeps.)"""
+    g = G(*gen.chung_lu(600, seed=7))
+    c, _ = O.coloring(g)
+    rank = np.lexsort((np.arange(g.n), c))
+    pos = np.empty(g.n, int)
+    pos[rank] = np.arange(g.n)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((g.n, 4))
+    for om in (1.0, 0.7, 1.4):
+        y = np.zeros(g.n)
+        for a, b, w in zip(g.u, g.v, g.w.astype(np.float64)):
+            y[a] += w
+            y[b] += w
+            earlier = a if pos[a] < pos[b] else b  # its edge to the other endpoint goes later
+            y[earlier] -= om * w
+        before = y @ x
+        after = y @ O.gauss_seidel(g, x, 3, om)
+        assert np.allclose(after, before, rtol=1e-10, atol=1e-10 * np.abs(x).sum())
