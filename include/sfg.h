@@ -335,6 +335,21 @@ SFG_API sfg_status sfg_sparsify_to_kappa(sfg_ctx* ctx, const sfg_graph* G, const
                                          int64_t* n_selected_host, double* kappa_trace_host,
                                          int* rounds_host);
 
+/* Solve L_G x = b by conjugate gradients preconditioned with the sparsifier P = the edges of G
+ * with mask[e] != 0 (the use the paper makes of its sparsifiers in its PCG experiments, Table 3):
+ * each iteration applies L_P^+ exactly (the elimination solver of sfg_kappa: degree <= 2 nodes
+ * eliminated in rounds, the core by CG to 1e-13). mask == NULL selects the diagonal (Jacobi)
+ * preconditioner instead, as a baseline. b (n entries, FP64, device, read only) is first
+ * projected onto the range of L_G (its mean removed on every connected component); x (n entries,
+ * FP64, device) receives the solution with mean zero on every component. Stops when
+ * ||r||_2 <= tol ||b_projected||_2 or after maxit iterations; iters_host and relres_host (may be
+ * NULL) receive the iterations taken and the final relative residual (recursive). All sums run
+ * in a fixed order: deterministic. Errors: SFG_EINVAL (bad arguments, or P does not span the
+ * components of G), SFG_ENOMEM, SFG_ETIMEOUT (a core solve did not converge). Synchronises. */
+SFG_API sfg_status sfg_solve_pcg(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask,
+                                 const double* b, double tol, int maxit, double* x, int* iters_host,
+                                 double* relres_host);
+
 /* ---------------------------------------------------------------------------------------------
  * Learned edge proposals (an addition to the paper's method; the paper has no learned part).
  * A small network predicts each candidate edge's score after `steps` sweeps from features of a

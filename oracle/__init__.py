@@ -416,3 +416,31 @@ def sparsify_flat(g: Graph, K=8, steps=10, omega=0.7, seed=0, mode=RATIO, budget
     cand = np.nonzero(mask == 0)[0].astype(np.int32)
     mask[topk(score_edges(g, xg, xp, cand, mode), cand, k)] = 1
     return mask
+
+
+def solve_laplacian(g: Graph, b):
+    """x with L_G x = b (b first projected onto the range of L_G: its mean removed on every
+    connected component) and mean zero on every component: grounded sparse direct solve (SuperLU
+    through scipy, a library primitive), then the per-component mean removed."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    from scipy.sparse.linalg import spsolve
+
+    b = np.asarray(b, np.float64).copy()
+    A = sp.coo_matrix((np.ones(g.m), (g.u, g.v)), shape=(g.n, g.n))
+    nc, lab = connected_components(A, directed=False)
+    for c in range(nc):
+        sel = lab == c
+        b[sel] -= b[sel].mean()
+    LG = _grounded_sparse(g)
+    first = np.full(nc, g.n)
+    np.minimum.at(first, lab, np.arange(g.n))
+    keep = np.ones(g.n, bool)
+    keep[first] = False
+    x = np.zeros(g.n)
+    if keep.any():
+        x[keep] = spsolve(LG.tocsc(), b[keep])
+    for c in range(nc):
+        sel = lab == c
+        x[sel] -= x[sel].mean()
+    return x

@@ -836,6 +836,91 @@ struct Solver {
 
 
 
+// Per-component means in a fixed order: nodes sorted by (component label, id); small components
+// are summed by one thread each in that order, large ones by one CTA each with a fixed
+// assignment and tree (deterministic either way).
+__global__ void k_comp_keys(int32_t n, const int32_t* __restrict__ root, uint64_t* __restrict__ key,
+                            uint32_t* __restrict__ val) {
+    for (int64_t v = blockIdx.x * (int64_t)kBlock + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * kBlock) {
+        key[v] = ((uint64_t)(uint32_t)root[v] << 32) | (uint32_t)v;
+        val[v] = (uint32_t)v;
+    }
+}
+
+__global__ void k_comp_heads(int32_t n, const uint64_t* __restrict__ key, uint8_t* __restrict__ head) {
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kBlock)
+        head[i] = i == 0 || (key[i] >> 32) != (key[i - 1] >> 32);
+}
+
+__global__ void k_comp_segs(int32_t n, const uint64_t* __restrict__ key, const uint8_t* __restrict__ head,
+                            const int64_t* __restrict__ hpos, int64_t* __restrict__ seg_start) {
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kBlock)
+        if (head[i]) seg_start[hpos[i]] = i;
+}
+
+constexpr int64_t kBigSeg = 2048;  // components at least this large get one CTA each
+
+// Small components: one thread each, members summed in order.
+__global__ void k_comp_mean(int64_t nseg, const int64_t* __restrict__ seg_start,
+                            const uint32_t* __restrict__ order, const int32_t* __restrict__ root,
+                            const double* __restrict__ x, double* __restrict__ mean_by_root) {
+    for (int64_t s = blockIdx.x * (int64_t)kBlock + threadIdx.x; s < nseg;
+         s += (int64_t)gridDim.x * kBlock) {
+        const int64_t a = seg_start[s], b = seg_start[s + 1];
+        if (b - a >= kBigSeg) continue;
+        double acc = 0.0;
+        for (int64_t i = a; i < b; ++i) acc += x[order[i]];
+        mean_by_root[root[order[a]]] = acc / (double)(b - a);
+    }
+}
+
+// Large components: one CTA each, a fixed thread-stride assignment and a fixed-shape tree.
+__global__ void k_comp_mean_big(const int64_t* __restrict__ big, const int64_t* __restrict__ seg_start,
+                                const uint32_t* __restrict__ order, const int32_t* __restrict__ root,
+                                const double* __restrict__ x, double* __restrict__ mean_by_root) {
+    __shared__ double sh[kBlock / 32];
+    const int64_t s = big[blockIdx.x];
+    const int64_t a = seg_start[s], b = seg_start[s + 1];
+    double acc = 0.0;
+    for (int64_t i = a + threadIdx.x; i < b; i += kBlock) acc += x[order[i]];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) mean_by_root[root[order[a]]] = acc / (double)(b - a);
+}
+
+__global__ void k_sub_mean(int32_t n, const int32_t* __restrict__ root,
+                           const double* __restrict__ mean_by_root, double* __restrict__ x) {
+    for (int64_t v = blockIdx.x * (int64_t)kBlock + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * kBlock)
+        x[v] -= mean_by_root[root[v]];
+}
+
+__global__ void k_pcg_update(int64_t n, double alpha, const double* __restrict__ p,
+                             const double* __restrict__ q, double* __restrict__ x,
+                             double* __restrict__ r) {
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kBlock) {
+        x[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+    }
+}
+
+__global__ void k_pcg_dir(int64_t n, double beta, const double* __restrict__ z, double* __restrict__ p) {
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kBlock)
+        p[i] = z[i] + beta * p[i];
+}
+
+// Diagonal preconditioner (the baseline): z = r / d, 0 where d = 0.
+__global__ void k_pcg_diag(int32_t n, const double* __restrict__ deg, const double* __restrict__ r,
+                           double* __restrict__ z) {
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kBlock)
+        z[i] = deg[i] > 0.0 ? r[i] / deg[i] : 0.0;
+}
+
 struct GraphGuard {
     sfg_graph* g = nullptr;
     ~GraphGuard() { sfg_graph_free(g); }
@@ -1010,6 +1095,176 @@ sfg_status kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int
     return SFG_OK;
 }
 
+// Mean removal per component of G (labels = component representatives).
+struct CompMean {
+    int32_t n = 0;
+    const int32_t* root = nullptr;
+    uint32_t* order = nullptr;
+    int64_t* seg_start = nullptr;
+    int64_t nseg = 0;
+    double* mean_by_root = nullptr;
+    int64_t* big = nullptr;  // indices of the components with >= kBigSeg members
+    int64_t nbig = 0;
+
+    sfg_status init(sfg_ctx* ctx, Scratch& s, int32_t n_, const int32_t* root_) {
+        n = n_;
+        root = root_;
+        cudaStream_t st = ctx->stream;
+        Scratch t(ctx);
+        uint64_t *k1, *k2;
+        uint32_t* v2;
+        uint8_t* head;
+        int64_t* hpos;
+        SFG_TRY(t.get(&k1, n));
+        SFG_TRY(t.get(&k2, n));
+        SFG_TRY(s.get(&order, n));
+        SFG_TRY(t.get(&v2, n));
+        SFG_TRY(t.get(&head, n));
+        SFG_TRY(t.get(&hpos, (size_t)n + 1));
+        SFG_TRY(s.get(&mean_by_root, n));
+        k_comp_keys<<<grid_of(ctx, k_comp_keys, n), kBlock, 0, st>>>(n, root, k1, order);
+        ++ctx->launches;
+        uint32_t* const alt = v2;
+        SFG_TRY(sfg_radix_sort_pairs(ctx, &k1, &order, &k2, &v2, n, 64));
+        if (order == alt) {  // sorted values ended in the temporary buffer: keep it with s
+            t.release(alt);
+            s.ptrs.push_back(alt);
+        }
+        k_comp_heads<<<grid_of(ctx, k_comp_heads, n), kBlock, 0, st>>>(n, k1, head);
+        ++ctx->launches;
+        SFG_TRY(sfg_scan_u8(ctx, head, hpos, n));
+        SFG_TRY(sfg_read_i64(ctx, hpos + n, &nseg));
+        SFG_TRY(s.get(&seg_start, nseg + 1));
+        k_comp_segs<<<grid_of(ctx, k_comp_segs, n), kBlock, 0, st>>>(n, k1, head, hpos, seg_start);
+        ++ctx->launches;
+        const int64_t nn = n;
+        SFG_CUDA(ctx, cudaMemcpyAsync(seg_start + nseg, &nn, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        std::vector<int64_t> hs(nseg + 1), hb;
+        SFG_CUDA(ctx, cudaMemcpyAsync(hs.data(), seg_start, sizeof(int64_t) * (nseg + 1),
+                                      cudaMemcpyDeviceToHost, st));
+        SFG_CUDA(ctx, cudaStreamSynchronize(st));
+        SFG_LAUNCH_CHECK(ctx, "component segments");
+        for (int64_t i = 0; i < nseg; ++i)
+            if (hs[i + 1] - hs[i] >= kBigSeg) hb.push_back(i);
+        nbig = (int64_t)hb.size();
+        if (nbig > 0) {
+            SFG_TRY(s.get(&big, nbig));
+            SFG_CUDA(ctx, cudaMemcpyAsync(big, hb.data(), sizeof(int64_t) * nbig,
+                                          cudaMemcpyHostToDevice, st));
+            SFG_CUDA(ctx, cudaStreamSynchronize(st));
+        }
+        return SFG_OK;
+    }
+
+    sfg_status remove(sfg_ctx* ctx, double* x) {
+        k_comp_mean<<<grid_of(ctx, k_comp_mean, nseg), kBlock, 0, ctx->stream>>>(
+            nseg, seg_start, order, root, x, mean_by_root);
+        if (nbig > 0)
+            k_comp_mean_big<<<(unsigned)nbig, kBlock, 0, ctx->stream>>>(big, seg_start, order, root,
+                                                                        x, mean_by_root);
+        k_sub_mean<<<grid_of(ctx, k_sub_mean, n), kBlock, 0, ctx->stream>>>(n, root, mean_by_root, x);
+        ctx->launches += nbig > 0 ? 3 : 2;
+        SFG_LAUNCH_CHECK(ctx, "component means");
+        return SFG_OK;
+    }
+};
+
+sfg_status pcg_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, const double* b,
+                    double tol, int maxit, double* x, int* iters, double* relres) {
+    const int32_t n = G->n;
+    cudaStream_t st = ctx->stream;
+    *iters = 0;
+    *relres = 0.0;
+    if (n == 0) return SFG_OK;
+    Scratch s(ctx);
+    int32_t* root;
+    uint8_t* tm;
+    SFG_TRY(s.get(&root, n));
+    SFG_TRY(s.get(&tm, G->m > 0 ? G->m : 1));
+    int64_t tg = 0;
+    SFG_TRY(sfg_mst_impl(ctx, G, nullptr, tm, &tg, root));
+    GraphGuard P;
+    Factor F;
+    Solver* S = nullptr;
+    struct Del { Solver** p; ~Del() { delete *p; } } del{&S};
+    if (mask) {
+        SFG_TRY(sfg_subgraph_impl(ctx, G, mask, &P.g));
+        int64_t tp = 0;
+        SFG_TRY(sfg_mst_impl(ctx, P.g, nullptr, tm, &tp));
+        if (tp < tg) return sfg_fail(ctx, SFG_EINVAL, "sfg_solve_pcg: P does not span G's components");
+        SFG_TRY(factorise(ctx, s, P.g, F));
+        S = new Solver(ctx, F);
+        SFG_TRY(S->init(s));
+    }
+    CompMean cm;
+    SFG_TRY(cm.init(ctx, s, n, root));
+    double *r, *z, *p, *q, *part, *sc;
+    SFG_TRY(s.get(&r, n));
+    SFG_TRY(s.get(&z, n));
+    SFG_TRY(s.get(&p, n));
+    SFG_TRY(s.get(&q, n));
+    SFG_TRY(s.get(&part, kRedBlocks));
+    SFG_TRY(s.get(&sc, 4));
+    const int gv = grid_of(ctx, k_lap_mul, n);
+    const int gd = std::min(kRedBlocks, grid_of(ctx, k_multidot, n));
+    auto dot = [&](const double* a, const double* c, double* out_host) -> sfg_status {
+        k_multidot<<<gd, kBlock, 0, st>>>(n, 1, a, c, part);
+        k_fold_many<<<1, kBlock, 0, st>>>(part, gd, sc);
+        ctx->launches += 2;
+        SFG_LAUNCH_CHECK(ctx, "dot");
+        SFG_CUDA(ctx, cudaMemcpyAsync(out_host, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SFG_CUDA(ctx, cudaStreamSynchronize(st));
+        return SFG_OK;
+    };
+    // The recursive residual drifts off range(L_G) by rounding while it shrinks, which would make
+    // the core system inconsistent relative to its size: project it before every application.
+    auto precond = [&](double* rr, double* zz) -> sfg_status {
+        SFG_TRY(cm.remove(ctx, rr));
+        if (S) {
+            SFG_TRY(S->solve(rr, zz));
+        } else {
+            k_pcg_diag<<<gv, kBlock, 0, st>>>(n, G->deg, rr, zz);
+            ++ctx->launches;
+        }
+        return cm.remove(ctx, zz);
+    };
+    // r = b projected onto range(L_G); x = 0
+    SFG_CUDA(ctx, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    SFG_TRY(cm.remove(ctx, r));
+    SFG_CUDA(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    double bb = 0.0;
+    SFG_TRY(dot(r, r, &bb));
+    if (bb == 0.0) return SFG_OK;
+    SFG_TRY(precond(r, z));
+    SFG_CUDA(ctx, cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    double rz = 0.0, rr = bb;
+    SFG_TRY(dot(r, z, &rz));
+    int it = 0;
+    while (it < maxit && rr > tol * tol * bb) {
+        k_lap_mul<<<gv, kBlock, 0, st>>>(n, G->row_ptr, G->colval, G->deg, p, q);
+        ++ctx->launches;
+        double pq = 0.0;
+        SFG_TRY(dot(p, q, &pq));
+        if (!(pq > 0.0)) break;
+        const double alpha = rz / pq;
+        k_pcg_update<<<gv, kBlock, 0, st>>>(n, alpha, p, q, x, r);
+        ++ctx->launches;
+        ++it;
+        SFG_TRY(dot(r, r, &rr));
+        if (rr <= tol * tol * bb) break;
+        SFG_TRY(precond(r, z));
+        double rz2 = 0.0;
+        SFG_TRY(dot(r, z, &rz2));
+        k_pcg_dir<<<gv, kBlock, 0, st>>>(n, rz2 / rz, z, p);
+        ++ctx->launches;
+        rz = rz2;
+    }
+    SFG_TRY(cm.remove(ctx, x));
+    *iters = it;
+    *relres = std::sqrt(rr / bb);
+    return SFG_OK;
+}
+
 }  // namespace
 
 sfg_status sfg_kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int steps,
@@ -1029,4 +1284,23 @@ extern "C" SFG_API sfg_status sfg_kappa(sfg_ctx* ctx, const sfg_graph* G, const 
     if (steps < 1) return sfg_fail(ctx, SFG_EINVAL, "sfg_kappa: steps must be >= 1");
     if (G->m > 0) SFG_TRY(sfg_check_dev(ctx, mask, "mask"));
     return sfg_kappa_impl(ctx, G, mask, steps, seed, kappa_host, info_host);
+}
+
+extern "C" SFG_API sfg_status sfg_solve_pcg(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask,
+                                            const double* b, double tol, int maxit, double* x,
+                                            int* iters_host, double* relres_host) {
+    if (!ctx) return SFG_EINVAL;
+    if (!G) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
+    if (!(tol > 0.0) || maxit < 0) return sfg_fail(ctx, SFG_EINVAL, "tol must be > 0 and maxit >= 0");
+    if (G->n > 0) {
+        SFG_TRY(sfg_check_dev(ctx, b, "b"));
+        SFG_TRY(sfg_check_dev(ctx, x, "x"));
+    }
+    if (mask && G->m > 0) SFG_TRY(sfg_check_dev(ctx, mask, "mask"));
+    int it = 0;
+    double rel = 0.0;
+    SFG_TRY(pcg_impl(ctx, G, mask, b, tol, maxit, x, &it, &rel));
+    if (iters_host) *iters_host = it;
+    if (relres_host) *relres_host = rel;
+    return SFG_OK;
 }

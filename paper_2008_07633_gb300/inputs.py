@@ -49,6 +49,28 @@ def grid3d(s, seed=2, weights="logu", lo=-2.0, hi=2.0):
     return s ** 3, u.astype(np.int32), v.astype(np.int32), _weights(rng, u.size, weights, lo, hi)
 
 
+def thermal3d(nx, ny, nz, seed=10, k_lo=-1.0, k_hi=2.0, jitter=0.1):
+    """Thermal-like layered 3-D mesh (a stand-in for finite-volume thermal grids of stacked
+    materials): nx x ny x nz 6-neighbour grid, node id = (z*ny + y)*nx + x. Layer z has a
+    conductivity k_z = 10^U[k_lo, k_hi); a lateral edge in layer z has conductance k_z and a vertical
+    edge between layers z and z+1 the series value 2 k_z k_{z+1} / (k_z + k_{z+1}); every edge is
+    then scaled by U[1 - jitter, 1 + jitter)."""
+    rng = _rng(seed)
+    k = np.power(10.0, rng.uniform(k_lo, k_hi, nz))
+    idx = np.arange(nx * ny * nz, dtype=np.int64).reshape(nz, ny, nx)
+    ux, vx = idx[:, :, :-1].ravel(), idx[:, :, 1:].ravel()
+    uy, vy = idx[:, :-1, :].ravel(), idx[:, 1:, :].ravel()
+    uz, vz = idx[:-1, :, :].ravel(), idx[1:, :, :].ravel()
+    kx = np.repeat(k, ny * (nx - 1))
+    ky = np.repeat(k, (ny - 1) * nx)
+    kv = 2 * k[:-1] * k[1:] / (k[:-1] + k[1:])
+    kz = np.repeat(kv, ny * nx)
+    u = np.concatenate([ux, uy, uz])
+    v = np.concatenate([vx, vy, vz])
+    w = np.concatenate([kx, ky, kz]) * rng.uniform(1 - jitter, 1 + jitter, u.size)
+    return nx * ny * nz, u.astype(np.int32), v.astype(np.int32), w.astype(np.float32)
+
+
 def power_grid(side, seed=3, via_frac=0.01, radius=8, sigma=1.5):
     """Circuit-like power-grid mesh: side x side 4-neighbour grid plus round(via_frac*N) "via"
     edges joining a uniform node to a node at a uniform lattice offset inside the Euclidean disk of

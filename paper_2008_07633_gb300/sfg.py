@@ -29,7 +29,7 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_
            "sfg_mlp_gradient", "sfg_mlp_train", "sfg_edge_features", "sfg_sparsify_learned",
            "sfg_autotune", "sfg_tune_set", "sfg_tune_table",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify", "sfg_kappa",
-           "sfg_sparsify_to_kappa", "sfg_smooth_gs", "sfg_coloring"]
+           "sfg_sparsify_to_kappa", "sfg_smooth_gs", "sfg_coloring", "sfg_solve_pcg"]
 
 
 class SfgError(RuntimeError):
@@ -91,6 +91,7 @@ def lib():
             "sfg_sparsify_batched": [_vp, _int, ctypes.POINTER(_vp), ctypes.POINTER(sfg_params),
                                      ctypes.POINTER(_vp), _pi64],
             "sfg_kappa": [_vp, _vp, _vp, _int, _u64, _pdbl, _pdbl],
+            "sfg_solve_pcg": [_vp, _vp, _vp, _vp, _dbl, _int, _vp, ctypes.POINTER(_int), _pdbl],
             "sfg_sparsify_to_kappa": [_vp, _vp, ctypes.POINTER(sfg_params), _dbl, _dbl, _int, _int,
                                       _vp, _pi64, _pdbl, ctypes.POINTER(_int)],
             "sfg_mlp_create": [_vp, _u64, ctypes.POINTER(_vp)],
@@ -395,6 +396,19 @@ def sfg_sparsify_to_kappa(ctx, g, kappa_target, batch_frac=0.01, max_rounds=20, 
                                           max_rounds, kappa_steps, _ptr(out), ctypes.byref(ns),
                                           ctypes.cast(trace, _pdbl), ctypes.byref(rounds)))
     return out[:g.m], ns.value, list(trace[:rounds.value + 1]), rounds.value
+
+
+def sfg_solve_pcg(ctx, g, b, mask=None, tol=1e-8, maxit=1000, out=None):
+    """x with L_G x = b (projected), by PCG preconditioned with the sparsifier `mask` (None:
+    diagonal preconditioner); returns (x, iterations, relative residual)."""
+    b = b.contiguous().to(torch.float64)
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.float64, device=ctx.device)
+    it = _int()
+    rel = ctypes.c_double()
+    ctx.check(lib().sfg_solve_pcg(ctx.h, g.h, None if mask is None else _ptr(mask.contiguous()),
+                                  _ptr(b), tol, maxit, _ptr(out), ctypes.byref(it), ctypes.byref(rel)))
+    return out, it.value, rel.value
 
 
 def sfg_sparsify_batched(ctx, graphs, K=16, steps=15, omega=0.7, seed=0, mode=SFG_SCORE_RATIO,

@@ -1,0 +1,75 @@
+"""kappa-versus-budget curves on a synthetic thermal-like layered mesh (the paper's Figs. on
+thermal grids have no data; this reports the same quantities on a stand-in): flat and multilevel
+sparsifiers at several budgets, kappa from sfg_kappa. Gated only by what must hold: flat
+sparsifiers are nested in the budget (top-k of one score list), so lambda_max, hence kappa with
+lambda_min certified = 1, cannot increase; and at a small size the GPU kappa equals the oracle's."""
+import os
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2008_07633_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2008_07633_gb300.sfg as S
+
+    S.lib()
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    c = S.sfg_ctx_create(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def test_thermal_small_matches_oracle(S, ctx):
+    n, u, v, w = gen.thermal3d(14, 12, 6, seed=3)
+    og = O.canonicalize(n, u, v, w)
+    g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
+    mask, _ = S.sfg_sparsify(ctx, g, K=16, steps=10, seed=2, budget_frac=0.05, budget_unit=0)
+    m = mask.cpu().numpy()
+    k, _, _ = S.sfg_kappa(ctx, g, mask, steps=5000)
+    assert abs(k - O.kappa_dense(og, m)) <= 1e-7 * k
+    ref = O.sparsify(og, K=16, steps=10, seed=2, budget_frac=0.05, budget_unit=0)[0]
+    assert abs(k - O.kappa_dense(og, ref)) <= 0.05 * O.kappa_dense(og, ref)
+
+
+def test_kappa_versus_budget_thermal(S, ctx):
+    n, u, v, w = gen.thermal3d(48, 48, 24, seed=10)
+    g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
+    budgets = (0.01, 0.02, 0.05, 0.1, 0.2)
+    rows, flat = [], []
+    for levels in (0, 1, 2):
+        for beta in budgets:
+            kw = dict(K=32, steps=20, levels=levels, seed=5, budget_frac=beta, budget_unit=0)
+            mask, cnt = S.sfg_sparsify(ctx, g, **kw)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mask, cnt = S.sfg_sparsify(ctx, g, **kw)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+            k, lmin, lmax, info = S.sfg_kappa(ctx, g, mask, steps=100, info=True)
+            rows.append(f"levels={levels} beta={beta}: kappa {k:.1f} ({ms:.1f} ms, {cnt} edges)")
+            if levels == 0:
+                flat.append((k, info["lambda_min_exact"]))
+    report = f"KAPPA_BUDGET thermal3d 48x48x24 (n={n}, m={g.m}), K=32, T=20: " + "; ".join(rows)
+    print("\n" + report)
+    if os.path.isdir("gpurun_out"):
+        open("gpurun_out/kappa_budget_report.txt", "w").write(report + "\n")
+    for (k0, e0), (k1, e1) in zip(flat, flat[1:]):
+        if e0 and e1:
+            assert k1 <= k0 * (1 + 1e-6)

@@ -608,3 +608,31 @@ def test_gauss_seidel_conserves_the_ordered_weighted_sum():
         before = y @ x
         after = y @ O.gauss_seidel(g, x, 3, om)
         assert np.allclose(after, before, rtol=1e-10, atol=1e-10 * np.abs(x).sum())
+
+
+def test_solve_laplacian_closed_forms():
+    """Unit path: L x = e_0 - e_{n-1} is solved by a ramp with slope -1 (flow 1 through unit
+    resistors); weighted path: the drop across edge i is 1 / w_i; any b: L x = b - mean(b) on each
+    component, x has mean zero on each component."""
+    n = 9
+    g = G(n, np.arange(n - 1), np.arange(1, n), np.ones(n - 1))
+    b = np.zeros(n)
+    b[0], b[-1] = 1.0, -1.0
+    x = O.solve_laplacian(g, b)
+    assert np.allclose(np.diff(x), -1.0, atol=1e-12) and abs(x.mean()) < 1e-12
+    w = np.linspace(0.5, 4.0, n - 1)
+    g = G(n, np.arange(n - 1), np.arange(1, n), w)
+    x = O.solve_laplacian(g, b)
+    assert np.allclose(-np.diff(x), 1.0 / g.w.astype(np.float64), rtol=1e-10)
+    g = G(*gen.random_graph(200, 320, seed=9, connected=False))
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal(g.n)
+    x = O.solve_laplacian(g, b)
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    _, lab = connected_components(coo_matrix((np.ones(g.m), (g.u, g.v)), shape=(g.n, g.n)), directed=False)
+    bp = b.copy()
+    for c in np.unique(lab):
+        bp[lab == c] -= bp[lab == c].mean()
+        assert abs(x[lab == c].mean()) < 1e-12
+    assert np.abs(O.laplacian_apply(g, x) - bp).max() < 1e-9 * np.abs(bp).max()
