@@ -74,6 +74,8 @@ def _declare(L):
         "orc_coloring": (_i32, [_i32, _i64, _i32p, _i32p, _f32p, _i32p]),
         "orc_gauss_seidel": (None, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _f64, _f64p]),
         "orc_smooth_gs": (None, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _f64, _u64, _f64p]),
+        "orc_smooth_gs_colored": (None, [_i32, _i64, _i32p, _i32p, _f32p, _i32p, _i32, _int, _int,
+                                         _f64, _u64, _f64p]),
         "orc_score_edges": (None, [_i32, _i64, _i32p, _i32p, _f32p, _f64p, _f64p, _int, _i32p,
                                    _i64, _int, _f64, _f64p]),
         "orc_topk": (None, [_f64p, _i32p, _i64, _i64, _i32p]),
@@ -206,9 +208,16 @@ def gauss_seidel(g: Graph, x, steps, omega=1.0):
     return x
 
 
-def smooth_gs(g: Graph, K, steps, omega=1.0, seed=0):
+def smooth_gs(g: Graph, K, steps, omega=1.0, seed=0, coloring=None):
+    """Gauss-Seidel smoothing in the order of g's own colouring, or of `coloring` = (colour per
+    node, number of colours) when given (it must be proper for g)."""
     x = np.empty((g.n, K), np.float64)
-    lib().orc_smooth_gs(*g.args(), K, steps, omega, seed, _p(x, _f64p))
+    if coloring is None:
+        lib().orc_smooth_gs(*g.args(), K, steps, omega, seed, _p(x, _f64p))
+    else:
+        c = _c(coloring[0], np.int32)
+        lib().orc_smooth_gs_colored(*g.args(), _p(c, _i32p), int(coloring[1]), K, steps, omega, seed,
+                                    _p(x, _f64p))
     return x
 
 
@@ -402,17 +411,22 @@ def sparsify_to_kappa(g: Graph, kappa_target, batch_frac, max_rounds, K=8, steps
 def sparsify_flat(g: Graph, K=8, steps=10, omega=0.7, seed=0, mode=RATIO, budget_frac=0.1,
                   budget_unit=1, smoother="jacobi"):
     """Flat Algorithm 1 (lines 13-14 on the spanning forest) with either smoother: P = maximum
-    spanning forest; embed G and P from the same seed with weighted Jacobi or Gauss-Seidel (colour
-    order), score the edges outside P, add the top round_half_up(beta * base) of them."""
+    spanning forest; embed G and P from the same seed with weighted Jacobi or Gauss-Seidel (both in
+    the order of G's colouring, which is proper for P), score the edges outside P, add the top
+    round_half_up(beta * base) of them."""
     mask = mst(g).astype(np.uint8)
     forest = int(mask.sum())
     base = g.n if budget_unit == 0 else g.m - forest
     k = min(int(np.floor(budget_frac * base + 0.5)), g.m - forest)
     if k <= 0:
         return mask
-    sm = smooth_gs if smoother == "gs" else smooth
-    xg = sm(g, K, steps, omega, seed)
-    xp = sm(g.subgraph(mask), K, steps, omega, seed)
+    if smoother == "gs":  # P sweeps in G's colour order (proper for P, a subgraph of G)
+        col = coloring(g)
+        xg = smooth_gs(g, K, steps, omega, seed)
+        xp = smooth_gs(g.subgraph(mask), K, steps, omega, seed, coloring=col)
+    else:
+        xg = smooth(g, K, steps, omega, seed)
+        xp = smooth(g.subgraph(mask), K, steps, omega, seed)
     cand = np.nonzero(mask == 0)[0].astype(np.int32)
     mask[topk(score_edges(g, xg, xp, cand, mode), cand, k)] = 1
     return mask

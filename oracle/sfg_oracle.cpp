@@ -600,6 +600,20 @@ void orc_smooth_gs(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, c
     std::copy(xv.begin(), xv.end(), x);
 }
 
+// Gauss-Seidel smoothing in a given colour order (a proper colouring of the graph, e.g. the
+// colouring of a supergraph on the same nodes).
+void orc_smooth_gs_colored(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv,
+                           const float* cw, const int32_t* color, int32_t ncolors, int K,
+                           int steps, double omega, uint64_t seed, double* x) {
+    Laplacian L = build_laplacian(make_graph(n, m, cu, cv, cw));
+    std::vector<int32_t> c(color, color + n);
+    std::vector<double> xv;
+    init_vectors(n, K, seed, xv);
+    gauss_seidel(L, c, ncolors, K, steps, omega, xv);
+    project(n, K, xv);
+    std::copy(xv.begin(), xv.end(), x);
+}
+
 void orc_score_edges(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
                      const double* xg, const double* xp, int K, const int32_t* ids, int64_t ne,
                      int mode, double eta, double* out) {

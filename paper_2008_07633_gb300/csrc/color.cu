@@ -158,11 +158,14 @@ sfg_status sfg_gs_prepare(sfg_ctx* ctx, const sfg_graph* Lc) {
         k_iota_neg<<<g, kBlock, 0, st>>>(n, color);
         SFG_CUDA(ctx, cudaMemsetAsync(maxc, 0, sizeof(int), st));
         ++ctx->launches;
-        for (int round = 0;; ++round) {
+        // rounds in batches of 4 between completion checks (a round after the last is a no-op)
+        for (int round = 0;; round += 4) {
             if (round > n) return sfg_fail(ctx, SFG_ETIMEOUT, "colouring did not finish");
-            k_jp_select<<<g, kBlock, 0, st>>>(n, L->row_ptr, L->colval, color, sel, left);
-            k_jp_assign<<<g, kBlock, 0, st>>>(n, L->row_ptr, L->colval, sel, color, maxc);
-            ctx->launches += 2;
+            for (int r = 0; r < 4; ++r) {
+                k_jp_select<<<g, kBlock, 0, st>>>(n, L->row_ptr, L->colval, color, sel, left);
+                k_jp_assign<<<g, kBlock, 0, st>>>(n, L->row_ptr, L->colval, sel, color, maxc);
+            }
+            ctx->launches += 8;
             SFG_LAUNCH_CHECK(ctx, "colouring round");
             int64_t remaining = 0;
             SFG_TRY(sfg_count_mask(ctx, left, n, &remaining));
@@ -198,6 +201,38 @@ sfg_status sfg_gs_prepare(sfg_ctx* ctx, const sfg_graph* Lc) {
     L->gs_color = color;
     L->gs_order = order;
     L->gs_off = off;
+    return SFG_OK;
+}
+
+// P shares G's nodes and has a subset of its edges, so G's colouring is a proper colouring of P:
+// copy it (and its class order) instead of colouring P again.
+sfg_status sfg_gs_inherit(sfg_ctx* ctx, const sfg_graph* Pc, const sfg_graph* G) {
+    sfg_graph* P = const_cast<sfg_graph*>(Pc);
+    if (P->gs_order) return SFG_OK;
+    SFG_TRY(sfg_gs_prepare(ctx, G));
+    const int32_t n = P->n;
+    int32_t *color = nullptr, *order = nullptr;
+    SFG_TRY(sfg_alloc(ctx, (void**)&color, sizeof(int32_t) * (n > 0 ? n : 1)));
+    sfg_status s = sfg_alloc(ctx, (void**)&order, sizeof(int32_t) * (n > 0 ? n : 1));
+    if (s != SFG_OK) {
+        sfg_free(ctx, color);
+        return s;
+    }
+    if (n > 0) {
+        cudaError_t e = cudaMemcpyAsync(color, G->gs_color, sizeof(int32_t) * n,
+                                        cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(order, G->gs_order, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                ctx->stream);
+        if (e != cudaSuccess) {
+            sfg_free(ctx, color);
+            sfg_free(ctx, order);
+            return sfg_cuda_fail(ctx, e, "colouring copy");
+        }
+    }
+    P->gs_color = color;
+    P->gs_order = order;
+    P->gs_off = G->gs_off;
     return SFG_OK;
 }
 

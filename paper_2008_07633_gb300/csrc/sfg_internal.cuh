@@ -204,6 +204,8 @@ sfg_status sfg_kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask,
                           uint64_t seed, double* kappa, double* info6);
 // Build the Gauss-Seidel colouring of L once (cached on the graph; color.cu).
 sfg_status sfg_gs_prepare(sfg_ctx* ctx, const sfg_graph* L);
+// Give P (a subgraph of G on the same nodes) G's colouring, which is proper for P too.
+sfg_status sfg_gs_inherit(sfg_ctx* ctx, const sfg_graph* P, const sfg_graph* G);
 // y_p = d_p - omega * (weight to nodes after p in (colour, id) order): the weights of the
 // quantity y^T x that the colour-ordered SOR sweep conserves (color.cu).
 __global__ void k_gs_weights(int32_t n, const int32_t* __restrict__ row_ptr,

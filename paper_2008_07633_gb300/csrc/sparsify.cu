@@ -96,6 +96,8 @@ sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64
     struct Guard { sfg_graph* g; ~Guard() { sfg_graph_free(g); } } guard{pg};
 
     if (P->smoother == SFG_SMOOTH_GAUSS_SEIDEL) {  // the paper's smoother: embed both, then score
+        // P sweeps in G's colour order (a proper colouring of P as well): no second colouring
+        SFG_TRY(sfg_gs_inherit(ctx, pg, g));
         const size_t blk = (size_t)g->n * P->K * elem_size(P->storage);
         void *xg, *xp;
         SFG_TRY(s.get((char**)&xp, blk));
