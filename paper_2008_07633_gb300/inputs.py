@@ -128,6 +128,12 @@ def knn3d(n, k=10, seed=4):
     return n, a.astype(np.int32), b.astype(np.int32), w
 
 
+def batch_sizes(ng=512, lo=1e3, hi=2e5, seed=3):
+    """Node counts of a batch of graphs: n_g = round(exp(U[ln lo, ln hi)))."""
+    rng = _rng(seed)
+    return np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), ng))).astype(np.int64)
+
+
 def chung_lu(n, avg_deg=16.0, gamma=2.3, seed=5, i0=1.0, lcc=True):
     """Chung-Lu power-law graph: expected degrees theta_i proportional to (i + i0)^(-1/(gamma-1)),
     scaled to the given mean and capped at sqrt(sum theta); n*avg_deg/2 endpoint pairs drawn with

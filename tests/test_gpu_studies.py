@@ -73,3 +73,52 @@ def test_kappa_versus_budget_thermal(S, ctx):
     for (k0, e0), (k1, e1) in zip(flat, flat[1:]):
         if e0 and e1:
             assert k1 <= k0 * (1 + 1e-6)
+
+
+def _knn_graph(args):
+    from paper_2008_07633_gb300 import inputs as g
+
+    n, seed = args
+    return g.knn3d(int(n), k=10, seed=seed)
+
+
+def test_batch_of_512_knn_graphs(S, ctx):
+    """The batching configuration: 512 symmetrised 10-NN graphs with n log-uniform in [1e3, 2e5)
+    (sum about 19M nodes), K = 16, 15 sweeps, flat, 5% budget: graphs per second for the batched
+    call against one sfg_sparsify per graph, and kappa of a sample of the batched sparsifiers
+    (GPU Lanczos; the smallest four also against the oracle's ARPACK value)."""
+    import multiprocessing as mp
+
+    sizes = gen.batch_sizes(512, seed=3)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        specs = pool.map(_knn_graph, [(int(n), 3000 + i) for i, n in enumerate(sizes)])
+    graphs = [S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w)) for n, u, v, w in specs]
+    kw = dict(K=16, steps=15, seed=7, budget_frac=0.05, budget_unit=0)
+    masks, counts = S.sfg_sparsify_batched(ctx, graphs, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        masks, counts = S.sfg_sparsify_batched(ctx, graphs, **kw)
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / 3
+    t0 = time.perf_counter()
+    for g in graphs:
+        S.sfg_sparsify(ctx, g, levels=0, **kw)
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    sample = sorted(range(len(graphs)), key=lambda i: sizes[i])[::16]   # 32 graphs across sizes
+    kap = {i: S.sfg_kappa(ctx, graphs[i], masks[i], steps=200)[0] for i in sample}
+    small = sample[:4]
+    for i in small:
+        n, u, v, w = specs[i]
+        ref = O.kappa_lanczos(O.canonicalize(n, u, v, w), masks[i].cpu().numpy())
+        assert abs(kap[i] - ref) <= 0.05 * ref, (i, kap[i], ref)
+    ks = np.array(list(kap.values()))
+    report = (f"BATCH_REPORT 512 10-NN graphs (sum n = {int(sizes.sum())}): batched "
+              f"{t_batch * 1e3:.1f} ms = {512 / t_batch:.0f} graphs/s; one call per graph "
+              f"{t_loop * 1e3:.1f} ms = {512 / t_loop:.0f} graphs/s ({t_loop / t_batch:.1f}x); "
+              f"kappa over a 32-graph sample: median {np.median(ks):.1f}, max {ks.max():.1f}")
+    print("\n" + report)
+    if os.path.isdir("gpurun_out"):
+        open("gpurun_out/batch_report.txt", "w").write(report + "\n")
+    assert sum(counts) == sum(int(m.sum().item()) for m in masks)
