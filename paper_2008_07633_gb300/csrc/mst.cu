@@ -4,7 +4,7 @@
 // Boruvka rounds under the strict order (weight descending, edge id ascending): every edge key is
 // (FP32 weight bits << 32) | ~id, unique and ordered like that order, so the forest is unique and
 // equal to Kruskal's. A round: (1) each component takes the largest key among edges leaving it
-// (64-bit atomicMax), (2) marks that edge and hooks to the component across it, (3) the 2-cycles
+// (per node over its CSR row, then one 64-bit atomicMax per node), (2) marks that edge and hooks to the component across it, (3) the 2-cycles
 // that mutual choices create are broken toward the smaller label, (4) pointer jumping flattens the
 // hook forest, (5) nodes are relabelled. Rounds repeat until no component has an outgoing edge.
 #include "sfg_internal.cuh"
@@ -26,18 +26,27 @@ __global__ void k_mst_reset(int32_t n, unsigned long long* __restrict__ best, in
     if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 0;
 }
 
-__global__ void k_mst_edges(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-                            const float* __restrict__ ew, const uint8_t* __restrict__ allow,
-                            const int32_t* __restrict__ comp, unsigned long long* __restrict__ best) {
-    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * kBlock) {
-        if (allow && !allow[e]) continue;
-        const int32_t a = comp[eu[e]], b = comp[ev[e]];
-        if (a == b) continue;
-        const unsigned long long key =
-            ((unsigned long long)__float_as_uint(ew[e]) << 32) | (unsigned long long)(~(uint32_t)e);
-        atomicMax(&best[a], key);
-        atomicMax(&best[b], key);
+// Each component's largest key among the edges leaving it, from the CSR rows: a node takes the
+// largest key among its entries that leave its component and issues one atomicMax for its
+// component. Every edge leaving a component sits in the row of its endpoint inside it.
+__global__ void k_mst_rows(int32_t n, const int32_t* __restrict__ row_ptr,
+                           const int2* __restrict__ colval, const int32_t* __restrict__ eid,
+                           const uint8_t* __restrict__ allow, const int32_t* __restrict__ comp,
+                           unsigned long long* __restrict__ best) {
+    for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * kBlock) {
+        const int32_t cp = comp[p];
+        unsigned long long local = 0ull;
+        for (int32_t j = row_ptr[p]; j < row_ptr[p + 1]; ++j) {
+            const int2 cv = colval[j];
+            if (comp[cv.x] == cp) continue;
+            const int32_t e = eid[j];
+            if (allow && !allow[e]) continue;
+            const unsigned long long key =
+                ((unsigned long long)(uint32_t)cv.y << 32) | (unsigned long long)(~(uint32_t)e);
+            local = key > local ? key : local;
+        }
+        if (local) atomicMax(&best[cp], local);
     }
 }
 
@@ -170,13 +179,12 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
     SFG_TRY(s.get(&best, n));
     SFG_TRY(s.get(&flag, 1));
     const int gn = sfg_grid(ctx, (const void*)k_mst_hook, kBlock, 0, n);
-    const int gm = sfg_grid(ctx, (const void*)k_mst_edges, kBlock, 0, m);
     k_mst_init<<<gn, kBlock, 0, ctx->stream>>>(n, comp); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_mst_init");
     // each round at least halves the number of components that still have outgoing edges
     for (int round = 0; round < 64; ++round) {
         k_mst_reset<<<gn, kBlock, 0, ctx->stream>>>(n, best, flag); ++ctx->launches;
-        k_mst_edges<<<gm, kBlock, 0, ctx->stream>>>(m, g->eu, g->ev, g->ew, allow, comp, best); ++ctx->launches;
+        k_mst_rows<<<gn, kBlock, 0, ctx->stream>>>(n, g->row_ptr, g->colval, g->eid, allow, comp, best); ++ctx->launches;
         k_mst_hook<<<gn, kBlock, 0, ctx->stream>>>(n, g->eu, g->ev, comp, best, parent, mask, flag); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_mst_round");
         int hflag = 0;
