@@ -209,6 +209,20 @@ def test_precision_powergrid_bf16_vs_fp32(S, ctx):
     print(f"\nC3 precision: fp32 rel err {e32:.2e}, bf16 rel err {e16:.2e} (rows {rows.size})")
     assert e32 < 1e-5
     assert e16 < 3e-2
+    # and on kappa: the flat sparsifier (5% of N) with FP32 and with BF16 blocks
+    kap = {}
+    for name, st in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+        mask, _ = S.sfg_sparsify(ctx, g, K=K, steps=T, levels=0, seed=51, budget_frac=0.05,
+                                 budget_unit=0, storage=st)
+        kap[name] = S.sfg_kappa(ctx, g, mask, steps=100)[0]
+    print(f"C3 kappa: fp32 {kap['fp32']:.1f}, bf16 {kap['bf16']:.1f} "
+          f"(ratio {kap['bf16'] / kap['fp32']:.4f})")
+    import os
+    if os.path.isdir("gpurun_out"):
+        open("gpurun_out/precision_report.txt", "w").write(
+            f"C3 2048^2 power grid, K=64, T=20: rows rel err fp32 {e32:.2e}, bf16 {e16:.2e}; "
+            f"kappa fp32 {kap['fp32']:.1f}, bf16 {kap['bf16']:.1f}\n")
+    assert abs(kap["bf16"] - kap["fp32"]) <= 0.25 * kap["fp32"]
 
 
 # ------------------------------------------------------------------ batched form ---------------
