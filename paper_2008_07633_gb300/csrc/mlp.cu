@@ -1,8 +1,9 @@
 // Learned edge-proposal scorer (an addition to the paper's method; the plain method stays the
 // judge): per-edge features from a short embedding, a 16 -> 64 -> 64 -> 1 ReLU network evaluated
-// and trained on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation), Adam in FP32.
+// on the tcgen05 tensor cores (inference, k_mlp_forward_tc below) and trained on BF16 warp-level
+// tensor-core MMA (mma.sync m16n8k16, FP32 accumulation), Adam in FP32.
 //
-// Forward, per warp and 16 edges: the feature rows are the A operand; layer outputs stay in the
+// Training forward, per warp and 16 edges: the feature rows are the A operand; layer outputs stay in the
 // accumulator fragments, whose layout is exactly the A-operand layout of the next layer once two
 // n-tiles are packed to BF16, so hidden activations never leave registers. The last layer (64 -> 1)
 // is a dot product folded across the four lanes that share a row.
@@ -108,20 +109,186 @@ __device__ __forceinline__ void forward_tile(const Net& net, const float* __rest
     T.y1 = y1 + net.theta[OFF_B3];
 }
 
-__global__ void __launch_bounds__(kMlpBlock) k_mlp_forward(Net net, const float* __restrict__ x,
-                                                           int64_t ne, float* __restrict__ out) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int64_t w = ((int64_t)blockIdx.x * kMlpBlock + threadIdx.x) >> 5;
-    const int64_t nw = (int64_t)gridDim.x * (kMlpBlock / 32);
-    for (int64_t e0 = w * 16; e0 < ne; e0 += nw * 16) {
-        Tile T;
-        forward_tile(net, x, e0, ne, T);
-        if (t == 0) {
-            if (e0 + g < ne) out[e0 + g] = T.y0;
-            if (e0 + g + 8 < ne) out[e0 + g + 8] = T.y1;
-        }
-    }
+// ---- inference on the 5th-generation tensor cores (tcgen05, accumulators in TMEM) ----
+// One CTA of 128 threads takes 128 edges at a time (the M of one MMA). Layer 1: the BF16 feature
+// tile and W1 sit in shared memory in the K-major, non-swizzled core-matrix layout (8 rows x 16
+// bytes per core matrix; LBO = byte step along K, SBO = byte step between 8-row groups); one
+// 128x64x16 tcgen05.mma writes x W1 to 64 TMEM columns. Each thread reads its row back
+// (tcgen05.ld, 32 lanes per warp), adds b1, applies ReLU, rounds to BF16 and writes the row as
+// layer 2's A operand; four K = 16 MMAs accumulate H1 W2 in the same columns; the thread adds b2,
+// applies ReLU and folds the 64 -> 1 layer as a dot product in FP32. BF16 rounding points are
+// those of the warp-level kernel (features, W1, W2, H1). Completion of each MMA group is signalled
+// through an mbarrier by tcgen05.commit; every wait on it is bounded.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);  // version 1, no swizzle
+}
+
+// kind::f16 instruction descriptor: D = F32 (bits 4-5), A = B = BF16 (bits 7-9, 10-12), both
+// K-major, N / 8 at bit 17, M / 16 at bit 24.
+constexpr uint32_t kIdescM128N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
+                                   ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(kIdescM128N64), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it)
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
+                 "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+                 "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+                   "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+                   "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+                   "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+                   "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_sync() {  // order tensor-core work and thread work across the CTA
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// bf16 index of element (row, k) of an R x KDIM K-major operand in the core-matrix layout
+template <int KDIM>
+__device__ __forceinline__ int core_idx(int row, int k) {
+    return ((row >> 3) * (KDIM / 8) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+__global__ void __launch_bounds__(128) k_mlp_forward_tc(const float* __restrict__ theta,
+                                                         const float* __restrict__ x, int64_t ne,
+                                                         float* __restrict__ out, int* __restrict__ err) {
+    __shared__ __align__(1024) __nv_bfloat16 sA1[128 * kF];   // features, 4 KB
+    __shared__ __align__(1024) __nv_bfloat16 sA2[128 * kH];   // H1, 16 KB
+    __shared__ __align__(1024) __nv_bfloat16 sB1[kH * kF];    // W1 as N x K, 2 KB
+    __shared__ __align__(1024) __nv_bfloat16 sB2[kH * kH];    // W2 as N x K, 8 KB
+    __shared__ float sb1[kH], sb2[kH], sw3[kH];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_base)), "r"(64) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < kH * kF; i += 128) {  // W1[f][h] -> (n = h, k = f)
+        const int h = i / kF, f = i % kF;
+        sB1[core_idx<kF>(h, f)] = __float2bfloat16_rn(theta[OFF_W1 + f * kH + h]);
+    }
+    for (int i = tid; i < kH * kH; i += 128) {  // W2[i][j] -> (n = j, k = i)
+        const int j = i / kH, k = i % kH;
+        sB2[core_idx<kH>(j, k)] = __float2bfloat16_rn(theta[OFF_W2 + k * kH + j]);
+    }
+    for (int i = tid; i < kH; i += 128) {
+        sb1[i] = theta[OFF_B1 + i];
+        sb2[i] = theta[OFF_B2 + i];
+        sw3[i] = theta[OFF_W3 + i];
+    }
+    const float b3 = theta[OFF_B3];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint64_t dA1 = umma_desc(smem_u32(sA1), 128, 256), dB1 = umma_desc(smem_u32(sB1), 128, 256);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t ntiles = (ne + 127) / 128;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t row = tile * 128 + tid;
+        const float* xr = x + min(row, ne - 1) * kF;
+        // features -> BF16 rows of the layer-1 A operand (two 16-byte chunks along K)
+        uint4 q[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float4 f0 = *reinterpret_cast<const float4*>(xr + 8 * c);
+            const float4 f1 = *reinterpret_cast<const float4*>(xr + 8 * c + 4);
+            q[c] = make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
+                              pack_bf16(f1.z, f1.w));
+            *reinterpret_cast<uint4*>(&sA1[core_idx<kF>(tid, 8 * c)]) = q[c];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+        if (tid == 0) {
+            umma_f16(tmem, dA1, dB1, 0);
+            umma_commit(&mbar);
+        }
+        ok = __syncthreads_and(mbar_wait(&mbar, phase));  // one decision for the whole CTA
+        phase ^= 1;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float v[64];
+        tmem_ld64(taddr, v);
+        // H1 = BF16(ReLU(x W1 + b1)) -> rows of the layer-2 A operand
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                w[e] = pack_bf16(fmaxf(v[8 * c + 2 * e] + sb1[8 * c + 2 * e], 0.f),
+                                 fmaxf(v[8 * c + 2 * e + 1] + sb1[8 * c + 2 * e + 1], 0.f));
+            *reinterpret_cast<uint4*>(&sA2[core_idx<kH>(tid, 8 * c)]) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+        if (tid == 0) {
+#pragma unroll
+            for (int s2 = 0; s2 < kH / 16; ++s2)
+                umma_f16(tmem, umma_desc(smem_u32(sA2) + 256 * s2, 128, 1024),
+                         umma_desc(smem_u32(sB2) + 256 * s2, 128, 1024), s2 > 0);
+            umma_commit(&mbar);
+        }
+        ok = __syncthreads_and(mbar_wait(&mbar, phase));
+        phase ^= 1;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem_ld64(taddr, v);
+        float y = 0.f;
+#pragma unroll
+        for (int j = 0; j < kH; ++j) y = fmaf(fmaxf(v[j] + sb2[j], 0.f), sw3[j], y);
+        if (row < ne) out[row] = y + b3;
+        tc_sync();  // every row read before the next tile's MMA overwrites the columns
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    tc_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(64) : "memory");
+}
+
 
 constexpr int kS64 = 72;  // shared-memory row stride (BF16) of the 64-wide tiles
 constexpr int kS16 = 24;  // and of the 16-wide feature tile
@@ -433,12 +600,21 @@ static sfg_status mlp_grad(sfg_ctx* ctx, sfg_mlp* n, const float* feats, const f
 sfg_status sfg_mlp_forward_impl(sfg_ctx* ctx, const sfg_mlp* net, const float* feats, int64_t ne,
                                 float* out) {
     if (ne == 0) return SFG_OK;
-    const int grid = sfg_grid(ctx, (const void*)k_mlp_forward, kMlpBlock, 0, (ne + 15) / 16 * 32);
+    Scratch s(ctx);
+    int* err;
+    SFG_TRY(s.get(&err, 1));
+    SFG_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+    const int64_t ntiles = (ne + 127) / 128;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 4);
     sfg_tic(ctx, "mlp_forward");
-    k_mlp_forward<<<grid, kMlpBlock, 0, ctx->stream>>>(net_of(net), feats, ne, out);
+    k_mlp_forward_tc<<<grid, 128, 0, ctx->stream>>>(net->theta, feats, ne, out, err);
     sfg_toc(ctx);
     ++ctx->launches;
-    SFG_LAUNCH_CHECK(ctx, "k_mlp_forward");
+    SFG_LAUNCH_CHECK(ctx, "k_mlp_forward_tc");
+    int h = 0;
+    SFG_CUDA(ctx, cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h) return sfg_fail(ctx, SFG_ETIMEOUT, "MLP forward: a tensor-core completion wait ran out");
     return SFG_OK;
 }
 
