@@ -69,6 +69,8 @@ KERNEL_SOURCES = {
     "k_jacobi": ("smooth.cu", "template <typename V>\n__device__ __forceinline__ V ldmeta",
                  "// One colour class of a multicolour Gauss-Seidel sweep", ["vec.cuh"]),
     "k_score": ("score.cu", "// Scorer, warp-tile schedule", "// ||X_p||^2 in FP64", ["vec.cuh"]),
+    "k_mlp_forward_tc": ("mlp.cu", "// ---- inference on the 5th-generation tensor cores",
+                         "constexpr int kS64 = 72;", []),
 }
 
 
@@ -100,6 +102,55 @@ def ncu_traffic(kernel, summary):
     if any(h != cur for h in shas):
         return None
     return sum(vals) / len(vals)
+
+
+def summary_value(summary, key, kernel):
+    """A per-unit figure from a committed ncu summary, or None once the kernel's source changed."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    shas = re.findall(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m = re.search(key + r":\s*([0-9.eE+]+)", text)
+    if not m or not shas or any(h != kernel_source_hash(kernel) for h in shas):
+        return None
+    return float(m.group(1))
+
+
+# Learned-scorer inference (16 -> 64 -> 64 -> 1, ReLU): FLOPs and HBM bytes per feature row
+MLP_FLOP_PER_ROW = 2 * (16 * 64 + 64 * 64 + 64)
+MLP_BYTES_PER_ROW = 16 * 4 + 4
+
+
+def mlp_report(S, ctx, dev, rows, iters):
+    """Throughput of sfg_mlp_forward (the tcgen05 kernel) over `rows` FP32 feature rows, timed by
+    the context's CUDA events around each launch on its own stream."""
+    import torch
+
+    net = S.sfg_mlp_create(ctx, seed=7)
+    gen_ = torch.Generator(device=dev)
+    gen_.manual_seed(5)
+    X = torch.randn(rows, S.MLP_NFEAT, device=dev, generator=gen_)
+    out = torch.empty(rows, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        S.sfg_mlp_forward(ctx, net, X, out=out)
+    S.sfg_ctx_timing(ctx, True)
+    for _ in range(iters):
+        S.sfg_mlp_forward(ctx, net, X, out=out)
+    n, ms = S.sfg_ctx_kernel_time(ctx, "mlp_forward")
+    S.sfg_ctx_timing(ctx, False)
+    net.close()
+    ms /= max(n, 1)
+    peak, peak_kind = load_peaks()
+    gbs = rows * MLP_BYTES_PER_ROW / (ms * 1e-3) / 1e9
+    per_row = summary_value("k_mlp_forward_tc_rows4M.txt", "dram_bytes_per_row", "k_mlp_forward_tc")
+    return {"kernel": "k_mlp_forward_tc", "rows": rows, "launches": n, "avg_launch_ms": ms,
+            "rows_per_s": rows / (ms * 1e-3),
+            "tflops": rows * MLP_FLOP_PER_ROW / (ms * 1e-3) / 1e12,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "peak_kind": peak_kind,
+                         "traffic": per_row * rows if per_row else None,
+                         "bytes_per_row": MLP_BYTES_PER_ROW, "flop_per_row": MLP_FLOP_PER_ROW}}
 
 
 class ClockSampler:
@@ -244,6 +295,11 @@ def run_ours(args):
             pg.barrier()
         torch.cuda.synchronize()
 
+    if args.mlp_only:  # ncu captures of the tensor-core inference kernel alone
+        ctx = S.sfg_ctx_create(local)
+        if rank == 0:
+            print(json.dumps({"mlp_forward": mlp_report(S, ctx, dev, args.mlp_rows, 3)}), flush=True)
+        return 0
     n, u, v, w = gen.grid3d(SIDE, seed=2)
     ctx = S.sfg_ctx_create(local)
     U, V, W = (torch.from_numpy(a).to(dev) for a in (u, v, w))
@@ -303,6 +359,7 @@ def run_ours(args):
 
     # sparsify time (device-resident G) and the end-to-end number through the public API with
     # host buffers: H2D of the edge list, Laplacian, flat sparsify, D2H of the mask
+    mlp = mlp_report(S, ctx, dev, args.mlp_rows, 10) if args.mlp_rows > 0 else None
     if args.profile:  # launch-list / counter captures: the filter+score steps only
         if rank == 0:
             print(json.dumps({"profile": True, "ms_per_step": ms, "value": value,
@@ -405,6 +462,8 @@ def run_ours(args):
            "gpu_launches": launches}
     if forms:
         out["sparsify_forms"] = forms
+    if mlp:
+        out["mlp_forward"] = mlp
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)
@@ -423,6 +482,10 @@ def main():
     ap.add_argument("--kappa-steps", type=int, default=200)
     ap.add_argument("--profile", action="store_true",
                     help="time only the filter+score steps (for ncu launch lists and counters)")
+    ap.add_argument("--mlp-rows", type=int, default=28_000_000,
+                    help="feature rows for the learned-scorer inference report (0 skips it)")
+    ap.add_argument("--mlp-only", action="store_true",
+                    help="run only the inference report (for ncu captures of its kernel)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

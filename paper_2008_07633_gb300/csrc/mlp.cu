@@ -1,5 +1,5 @@
-// Learned edge-proposal scorer (an addition to the paper's method; the plain method stays the
-// judge): per-edge features from a short embedding, a 16 -> 64 -> 64 -> 1 ReLU network evaluated
+// Learned edge-proposal scorer (an addition to the paper's method; the proposals it makes are
+// rescored by the plain method before selection): per-edge features from a short embedding, a 16 -> 64 -> 64 -> 1 ReLU network evaluated
 // on the tcgen05 tensor cores (inference, k_mlp_forward_tc below) and trained on BF16 warp-level
 // tensor-core MMA (mma.sync m16n8k16, FP32 accumulation), Adam in FP32.
 //
@@ -110,15 +110,20 @@ __device__ __forceinline__ void forward_tile(const Net& net, const float* __rest
 }
 
 // ---- inference on the 5th-generation tensor cores (tcgen05, accumulators in TMEM) ----
-// One CTA of 128 threads takes 128 edges at a time (the M of one MMA). Layer 1: the BF16 feature
-// tile and W1 sit in shared memory in the K-major, non-swizzled core-matrix layout (8 rows x 16
-// bytes per core matrix; LBO = byte step along K, SBO = byte step between 8-row groups); one
-// 128x64x16 tcgen05.mma writes x W1 to 64 TMEM columns. Each thread reads its row back
-// (tcgen05.ld, 32 lanes per warp), adds b1, applies ReLU, rounds to BF16 and writes the row as
-// layer 2's A operand; four K = 16 MMAs accumulate H1 W2 in the same columns; the thread adds b2,
-// applies ReLU and folds the 64 -> 1 layer as a dot product in FP32. BF16 rounding points are
-// those of the warp-level kernel (features, W1, W2, H1). Completion of each MMA group is signalled
-// through an mbarrier by tcgen05.commit; every wait on it is bounded.
+// One CTA of 128 threads takes 128 edges at a time (the M of one MMA); each thread owns one row.
+// Operands sit in shared memory in the K-major, non-swizzled core-matrix layout (8 rows x 16 bytes
+// per core matrix; LBO = byte step along K, SBO = byte step between 8-row groups), as K = 16
+// chunks. The A tile has five chunks: chunks 0-3 hold H1 (64 columns) and chunk 4 a constant
+// (1, 1, 0, ..., 0) per row; chunk 0 also holds the BF16 features while layer 1 runs (H1 is
+// written only after layer 1 has completed). The biases ride in the MMAs: the B rows facing the
+// two constant columns hold b = hi + lo as two BF16 numbers (hi = BF16(b), lo = BF16(b - hi)), so
+// the accumulator receives x W + b with b good to about 2^-16 relative.
+//   layer 1: D = [x | 1 1 0..] [W1 ; b1_hi ; b1_lo ; 0..]           (2 MMAs, 128 x 64 x 16)
+//   H1 = BF16(ReLU(D)) in one cvt.rn.relu.bf16x2 per column pair, written over chunks 0-3
+//   layer 2: D = [H1 | 1 1 0..] [W2 ; b2_hi ; b2_lo ; 0..]          (5 MMAs)
+//   y = sum_j ReLU(D_j) w3_j + b3 in FP32 by the owning thread.
+// BF16 rounding points: features, W1, W2, H1 (as in the warp-level kernel). Completion of each MMA
+// group is signalled through an mbarrier by tcgen05.commit; every wait on it is bounded.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -153,25 +158,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
     return done != 0;
 }
 
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-    uint32_t r[64];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                  "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
-                 "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
-                 "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                    "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
                    "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-                   "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-                   "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-                   "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-                   "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                  : "r"(taddr) : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tc_sync() {  // order tensor-core work and thread work across the CTA
@@ -186,14 +186,23 @@ __device__ __forceinline__ int core_idx(int row, int k) {
     return ((row >> 3) * (KDIM / 8) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
 }
 
-__global__ void __launch_bounds__(128) k_mlp_forward_tc(const float* __restrict__ theta,
+// BF16(ReLU(lo)) in the low half, BF16(ReLU(hi)) in the high half, round to nearest even
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+constexpr int kKA = 80;  // K of the A tile: H1 (64) + the constant chunk (16)
+constexpr int kKB1 = 32; // K of layer 1's B: W1 (16) + bias chunk (16)
+
+__global__ void __launch_bounds__(128, 6) k_mlp_forward_tc(const float* __restrict__ theta,
                                                          const float* __restrict__ x, int64_t ne,
                                                          float* __restrict__ out, int* __restrict__ err) {
-    __shared__ __align__(1024) __nv_bfloat16 sA1[128 * kF];   // features, 4 KB
-    __shared__ __align__(1024) __nv_bfloat16 sA2[128 * kH];   // H1, 16 KB
-    __shared__ __align__(1024) __nv_bfloat16 sB1[kH * kF];    // W1 as N x K, 2 KB
-    __shared__ __align__(1024) __nv_bfloat16 sB2[kH * kH];    // W2 as N x K, 8 KB
-    __shared__ float sb1[kH], sb2[kH], sw3[kH];
+    __shared__ __align__(1024) __nv_bfloat16 sA[128 * kKA];   // 20 KB
+    __shared__ __align__(1024) __nv_bfloat16 sB1[kH * kKB1];  // W1 and b1 as N x K, 4 KB
+    __shared__ __align__(1024) __nv_bfloat16 sB2[kH * kKA];   // W2 and b2 as N x K, 10 KB
+    __shared__ __align__(16) float sw3[kH];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -206,82 +215,106 @@ __global__ void __launch_bounds__(128) k_mlp_forward_tc(const float* __restrict_
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar)), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = tid; i < kH * kF; i += 128) {  // W1[f][h] -> (n = h, k = f)
-        const int h = i / kF, f = i % kF;
-        sB1[core_idx<kF>(h, f)] = __float2bfloat16_rn(theta[OFF_W1 + f * kH + h]);
+    // B operands: (n, k) = (output unit, input unit); the bias rows sit at k = K0 and K0 + 1
+    auto split = [](float b, bool lo) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+        return lo ? __float2bfloat16_rn(b - __bfloat162float(hi)) : hi;
+    };
+    for (int i = tid; i < kH * kKB1; i += 128) {
+        const int h = i / kKB1, k = i % kKB1;
+        sB1[core_idx<kKB1>(h, k)] = k < kF ? __float2bfloat16_rn(theta[OFF_W1 + k * kH + h])
+                                  : k < kF + 2 ? split(theta[OFF_B1 + h], k == kF + 1)
+                                               : __float2bfloat16_rn(0.f);
     }
-    for (int i = tid; i < kH * kH; i += 128) {  // W2[i][j] -> (n = j, k = i)
-        const int j = i / kH, k = i % kH;
-        sB2[core_idx<kH>(j, k)] = __float2bfloat16_rn(theta[OFF_W2 + k * kH + j]);
+    for (int i = tid; i < kH * kKA; i += 128) {
+        const int j = i / kKA, k = i % kKA;
+        sB2[core_idx<kKA>(j, k)] = k < kH ? __float2bfloat16_rn(theta[OFF_W2 + k * kH + j])
+                                 : k < kH + 2 ? split(theta[OFF_B2 + j], k == kH + 1)
+                                              : __float2bfloat16_rn(0.f);
     }
-    for (int i = tid; i < kH; i += 128) {
-        sb1[i] = theta[OFF_B1 + i];
-        sb2[i] = theta[OFF_B2 + i];
-        sw3[i] = theta[OFF_W3 + i];
+    if (tid < kH) sw3[tid] = theta[OFF_W3 + tid];
+    {   // this row's constant chunk (1, 1, 0, ..., 0)
+        const uint32_t one2 = pack_bf16(1.f, 1.f);
+        *reinterpret_cast<uint4*>(&sA[core_idx<kKA>(tid, kH)]) = make_uint4(one2, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(&sA[core_idx<kKA>(tid, kH + 8)]) = make_uint4(0u, 0u, 0u, 0u);
     }
     const float b3 = theta[OFF_B3];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
     const uint32_t tmem = tmem_base;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint64_t dA1 = umma_desc(smem_u32(sA1), 128, 256), dB1 = umma_desc(smem_u32(sB1), 128, 256);
+    const uint32_t a0 = smem_u32(sA), b10 = smem_u32(sB1), b20 = smem_u32(sB2);
+    constexpr uint32_t kSboA = kKA / 8 * 128, kSboB1 = kKB1 / 8 * 128;
     uint32_t phase = 0;
     bool ok = true;
     const int64_t ntiles = (ne + 127) / 128;
+    // this thread's feature row of the next tile, loaded one tile ahead so that the global
+    // latency overlaps the current tile's MMAs
+    float4 f[4];
+    auto load_row = [&](int64_t tile) {
+        const float4* xr = reinterpret_cast<const float4*>(x + min(tile * 128 + tid, ne - 1) * kF);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) f[c] = xr[c];
+    };
+    if ((int64_t)blockIdx.x < ntiles) load_row(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t row = tile * 128 + tid;
-        const float* xr = x + min(row, ne - 1) * kF;
-        // features -> BF16 rows of the layer-1 A operand (two 16-byte chunks along K)
-        uint4 q[2];
+        // features -> BF16 in chunk 0 (the previous tile's layer 2 has completed)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const float4 f0 = *reinterpret_cast<const float4*>(xr + 8 * c);
-            const float4 f1 = *reinterpret_cast<const float4*>(xr + 8 * c + 4);
-            q[c] = make_uint4(pack_bf16(f0.x, f0.y), pack_bf16(f0.z, f0.w), pack_bf16(f1.x, f1.y),
-                              pack_bf16(f1.z, f1.w));
-            *reinterpret_cast<uint4*>(&sA1[core_idx<kF>(tid, 8 * c)]) = q[c];
-        }
+        for (int c = 0; c < 2; ++c)
+            *reinterpret_cast<uint4*>(&sA[core_idx<kKA>(tid, 8 * c)]) =
+                make_uint4(pack_bf16(f[2 * c].x, f[2 * c].y), pack_bf16(f[2 * c].z, f[2 * c].w),
+                           pack_bf16(f[2 * c + 1].x, f[2 * c + 1].y), pack_bf16(f[2 * c + 1].z, f[2 * c + 1].w));
+        if (tile + gridDim.x < ntiles) load_row(tile + gridDim.x);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_sync();
+        tc_sync();  // also orders the previous tile's TMEM reads before this tile's MMAs
         if (tid == 0) {
-            umma_f16(tmem, dA1, dB1, 0);
+            umma_f16(tmem, umma_desc(a0, 128, kSboA), umma_desc(b10, 128, kSboB1), 0);
+            umma_f16(tmem, umma_desc(a0 + 256 * 4, 128, kSboA), umma_desc(b10 + 256, 128, kSboB1), 1);
             umma_commit(&mbar);
         }
         ok = __syncthreads_and(mbar_wait(&mbar, phase));  // one decision for the whole CTA
         phase ^= 1;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float v[64];
-        tmem_ld64(taddr, v);
-        // H1 = BF16(ReLU(x W1 + b1)) -> rows of the layer-2 A operand
+        // H1 = BF16(ReLU(x W1 + b1)) over chunks 0-3, 32 columns at a time
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            uint32_t w[4];
+        for (int half = 0; half < 2; ++half) {
+            float v[32];
+            tmem_ld32(taddr + 32 * half, v);
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                w[e] = pack_bf16(fmaxf(v[8 * c + 2 * e] + sb1[8 * c + 2 * e], 0.f),
-                                 fmaxf(v[8 * c + 2 * e + 1] + sb1[8 * c + 2 * e + 1], 0.f));
-            *reinterpret_cast<uint4*>(&sA2[core_idx<kH>(tid, 8 * c)]) = make_uint4(w[0], w[1], w[2], w[3]);
+            for (int c = 0; c < 4; ++c)
+                *reinterpret_cast<uint4*>(&sA[core_idx<kKA>(tid, 32 * half + 8 * c)]) =
+                    make_uint4(relu_bf16x2(v[8 * c], v[8 * c + 1]), relu_bf16x2(v[8 * c + 2], v[8 * c + 3]),
+                               relu_bf16x2(v[8 * c + 4], v[8 * c + 5]), relu_bf16x2(v[8 * c + 6], v[8 * c + 7]));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_sync();
         if (tid == 0) {
 #pragma unroll
-            for (int s2 = 0; s2 < kH / 16; ++s2)
-                umma_f16(tmem, umma_desc(smem_u32(sA2) + 256 * s2, 128, 1024),
-                         umma_desc(smem_u32(sB2) + 256 * s2, 128, 1024), s2 > 0);
+            for (int c = 0; c < kKA / 16; ++c)
+                umma_f16(tmem, umma_desc(a0 + 256 * c, 128, kSboA), umma_desc(b20 + 256 * c, 128, kSboA), c > 0);
             umma_commit(&mbar);
         }
         ok = __syncthreads_and(mbar_wait(&mbar, phase));
         phase ^= 1;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        tmem_ld64(taddr, v);
         float y = 0.f;
 #pragma unroll
-        for (int j = 0; j < kH; ++j) y = fmaf(fmaxf(v[j] + sb2[j], 0.f), sw3[j], y);
+        for (int half = 0; half < 2; ++half) {
+            float v[32];
+            tmem_ld32(taddr + 32 * half, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                const float4 w = *reinterpret_cast<const float4*>(&sw3[32 * half + j]);
+                y = fmaf(fmaxf(v[j], 0.f), w.x, y);
+                y = fmaf(fmaxf(v[j + 1], 0.f), w.y, y);
+                y = fmaf(fmaxf(v[j + 2], 0.f), w.z, y);
+                y = fmaf(fmaxf(v[j + 3], 0.f), w.w, y);
+            }
+        }
         if (row < ne) out[row] = y + b3;
-        tc_sync();  // every row read before the next tile's MMA overwrites the columns
     }
     if (!ok && tid == 0) atomicExch(err, 1);
     tc_sync();
@@ -605,7 +638,24 @@ sfg_status sfg_mlp_forward_impl(sfg_ctx* ctx, const sfg_mlp* net, const float* f
     SFG_TRY(s.get(&err, 1));
     SFG_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
     const int64_t ntiles = (ne + 127) / 128;
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 4);
+    // One wave of resident CTAs, counted from the kernel's registers and static shared memory
+    // (each CTA also holds 64 of the SM's 512 TMEM columns, so at most 8 fit).
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        SFG_CUDA(ctx, cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxShared));
+        cudaFuncAttributes fa;
+        SFG_CUDA(ctx, cudaFuncGetAttributes(&fa, k_mlp_forward_tc));
+        int regs_sm = 0, smem_sm = 0, smem_rsv = 0;
+        SFG_CUDA(ctx, cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, ctx->device));
+        SFG_CUDA(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+        SFG_CUDA(ctx, cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
+        const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
+        const int by_regs = regs_sm / (warp_regs * 4);
+        const int by_smem = smem_sm / ((int)fa.sharedSizeBytes + smem_rsv);
+        per_sm = std::max(1, std::min({by_regs, by_smem, 512 / 64}));
+    }
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * per_sm);
     sfg_tic(ctx, "mlp_forward");
     k_mlp_forward_tc<<<grid, 128, 0, ctx->stream>>>(net->theta, feats, ne, out, err);
     sfg_toc(ctx);

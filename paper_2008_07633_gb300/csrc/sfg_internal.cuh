@@ -51,6 +51,14 @@ struct sfg_graph {
     int32_t* gs_color = nullptr;
     int32_t* gs_order = nullptr;
     std::vector<int64_t> gs_off;
+    // Rows with more entries than the sweep's heavy-row threshold, built on the first sweep
+    // (smooth.cu): hv_n rows (-1 = not built yet) at hv_rows, row h's segments at
+    // hv_seg[hv_soff[h], hv_soff[h + 1]), each (row, first entry, end entry, 0).
+    int32_t hv_n = -1;
+    int64_t hv_nseg = 0;
+    int32_t* hv_rows = nullptr;
+    int32_t* hv_soff = nullptr;
+    int4* hv_seg = nullptr;
     cudaStream_t stream = nullptr;
 };
 

@@ -188,10 +188,12 @@ __device__ __forceinline__ void gather_chunk(const Chunk<LPR>& ch, int need, uns
 // one coalesced load per lane and are handed out by shuffles; each group holds its row's first
 // chunk of (column, weight) entries. The next tile's metadata is loaded before this tile's
 // gathers are issued and its chunks right after, so one gather round is the only exposed latency
-// per tile. Gathers go in warp-uniform batches sized by the tile's longest row.
+// per tile. Gathers go in warp-uniform batches sized by the tile's longest row. Rows with more
+// than hmax entries are left to the heavy-row kernels below (their group idles through the tile
+// and stores nothing), so one hub row cannot serialise a warp for the whole sweep.
 template <typename T, int LPR, bool SUB_MU, bool STATS, int TPI, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB)
-    k_jacobi(int32_t n, const int32_t* __restrict__ row_ptr, const int2* __restrict__ colval,
+    k_jacobi(int32_t n, int32_t hmax, const int32_t* __restrict__ row_ptr, const int2* __restrict__ colval,
              const float* __restrict__ coef, float a_self, const T* __restrict__ X,
              T* __restrict__ Y, const float* __restrict__ mu, double* __restrict__ part) {
     constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR, C = Chunk<LPR>::C;
@@ -215,6 +217,13 @@ __global__ void __launch_bounds__(kBlock, MINB)
     // Metadata of tile t, one value per lane: lo = row_ptr[r0 + lane], hi = row_ptr[r0 + lane + 1]
     // (both clamped at n; hi only when GPW = 32), cf = D^-1 of row r0 + lane.
     struct Meta { int32_t lo, hi; float cf; };
+    // this group's row bounds in tile metadata mt; a heavy row gets b = a - 1 (no entries, and
+    // deg < 0 marks it as not stored here)
+    auto bounds = [&](const Meta& mt, int32_t& a, int32_t& b) {
+        a = __shfl_sync(0xffffffffu, mt.lo, grp);
+        b = GPW == 32 ? mt.hi : __shfl_sync(0xffffffffu, mt.lo, grp + 1);
+        if (b - a > hmax) b = a - 1;
+    };
     auto load_meta = [&](int32_t t) {
         Meta mt{0, 0, 0.f};
         const int32_t r = t * GPW + lane;
@@ -227,9 +236,9 @@ __global__ void __launch_bounds__(kBlock, MINB)
     // store and the projection statistics.
     auto row_tile = [&](int32_t t, const Chunk<LPR>& ch, int32_t a, int32_t b, float cp, auto&& mid) {
         const int32_t r = t * GPW + grp;
-        const bool live = r < n;
-        const int32_t self = live ? r : 0;
+        const int32_t self = r < n ? r : 0;
         const int32_t deg = b - a;
+        const bool live = r < n && deg >= 0;
         const int32_t maxdeg = __reduce_max_sync(0xffffffffu, deg);
         float acc[E];
         const uint4 xr = Vec<T>::load_raw(Xl + (int64_t)self * K);  // widened at use
@@ -271,23 +280,23 @@ __global__ void __launch_bounds__(kBlock, MINB)
         int32_t t = wid * TPI;
         const Meta mt0 = load_meta(t);
         Meta mt1 = load_meta(next_tile(t));
-        int32_t a = __shfl_sync(0xffffffffu, mt0.lo, grp);
-        int32_t b = GPW == 32 ? mt0.hi : __shfl_sync(0xffffffffu, mt0.lo, grp + 1);
+        int32_t a, b;
+        bounds(mt0, a, b);
         float cp = __shfl_sync(0xffffffffu, mt0.cf, grp);
         Chunk<LPR> ch;
         ch.load(colval, a, b, min(t * GPW + grp, n - 1), sub);
         while (t < ntiles) {
             const int32_t t1 = next_tile(t);
+            int32_t a1, b1;
+            bounds(mt1, a1, b1);
             Chunk<LPR> ch1;
-            ch1.load(colval, __shfl_sync(0xffffffffu, mt1.lo, grp),
-                     GPW == 32 ? mt1.hi : __shfl_sync(0xffffffffu, mt1.lo, grp + 1),
-                     min(t1 * GPW + grp, n - 1), sub);
+            ch1.load(colval, a1, b1, min(t1 * GPW + grp, n - 1), sub);
             const Meta mt2 = load_meta(next_tile(t1));
             row_tile(t, ch, a, b, cp, [] {});
             t = t1;
             ch = ch1;
-            a = __shfl_sync(0xffffffffu, mt1.lo, grp);
-            b = GPW == 32 ? mt1.hi : __shfl_sync(0xffffffffu, mt1.lo, grp + 1);
+            a = a1;
+            b = b1;
             cp = __shfl_sync(0xffffffffu, mt1.cf, grp);
             mt1 = mt2;
         }
@@ -296,8 +305,8 @@ __global__ void __launch_bounds__(kBlock, MINB)
         // metadata is loaded and its chunk follows the gather round (measured faster at this shape).
         int32_t t = wid * TPI;
         Meta mt = load_meta(t);
-        int32_t a = __shfl_sync(0xffffffffu, mt.lo, grp);
-        int32_t b = GPW == 32 ? mt.hi : __shfl_sync(0xffffffffu, mt.lo, grp + 1);
+        int32_t a, b;
+        bounds(mt, a, b);
         Chunk<LPR> ch;
         ch.load(colval, a, b, min(t * GPW + grp, n - 1), sub);
         for (; t < ntiles;) {
@@ -306,8 +315,7 @@ __global__ void __launch_bounds__(kBlock, MINB)
             const int32_t a0 = a, b0 = b;
             const Chunk<LPR> ch0 = ch;
             row_tile(t, ch0, a0, b0, __shfl_sync(0xffffffffu, mt.cf, grp), [&] {
-                a = __shfl_sync(0xffffffffu, mt1.lo, grp);
-                b = GPW == 32 ? mt1.hi : __shfl_sync(0xffffffffu, mt1.lo, grp + 1);
+                bounds(mt1, a, b);
                 ch.load(colval, a, b, min(t1 * GPW + grp, n - 1), sub);
             });
             mt = mt1;
@@ -315,6 +323,173 @@ __global__ void __launch_bounds__(kBlock, MINB)
         }
     }
     if (STATS) block_column_partials<LPR, E>(s1, s2, part);
+}
+
+// Rows longer than kHeavy entries (the hubs of power-law graphs) are swept apart from the tiles:
+// each is cut into segments of kSeg consecutive entries, one lane group per segment forms the
+// partial sum of w * X[col] over its segment (k_heavy_part), and one group per row adds the row's
+// partials in segment order and applies the update (k_heavy_final). The segmentation is fixed per
+// graph, so the result does not depend on the schedule. The lists are built once per graph.
+constexpr int32_t kHeavy = 256, kSeg = 128;
+constexpr int kHeavyGrid = 64;  // CTAs of k_heavy_final: its statistics take as many part slots
+
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kBlock) k_heavy_part(int64_t nseg, const int4* __restrict__ seg,
+                                                       const int2* __restrict__ colval,
+                                                       const T* __restrict__ X,
+                                                       float* __restrict__ partial) {
+    constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR, C = Chunk<LPR>::C;
+    const int lane = threadIdx.x & 31, grp = lane / LPR, sub = lane % LPR;
+    const unsigned gm = group_mask<LPR>(lane);
+    const int64_t w0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
+    const T* __restrict__ Xl = X + sub * E;
+    for (int64_t s0 = w0 * GPW; s0 < nseg; s0 += nw * GPW) {
+        const int64_t sid = s0 + grp;
+        const bool live = sid < nseg;
+        const int4 sg = live ? seg[sid] : make_int4(0, 0, 0, 0);  // (row, begin, end, -)
+        float acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        // the same trip count for every group: slots past a segment's end gather the row itself
+        // with weight zero
+#pragma unroll 1
+        for (int32_t j0 = 0; j0 < kSeg; j0 += C) {
+            Chunk<LPR> ch;
+            ch.load(colval, sg.y + j0, sg.z, sg.x, sub);
+#pragma unroll
+            for (int q = 0; q < C; q += 8) gather_slots<T, LPR, 8>(ch, q, gm, Xl, acc);
+        }
+        if (live) {
+            float* pr = partial + sid * K + sub * E;
+#pragma unroll
+            for (int e = 0; e < E; e += 4)
+                *reinterpret_cast<float4*>(pr + e) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+        }
+    }
+}
+
+template <typename T, int LPR, bool SUB_MU, bool STATS>
+__global__ void __launch_bounds__(kBlock) k_heavy_final(int32_t nh, const int32_t* __restrict__ hrow,
+                                                        const int32_t* __restrict__ hsoff,
+                                                        const float* __restrict__ partial,
+                                                        const float* __restrict__ coef, float a_self,
+                                                        const T* __restrict__ X, T* __restrict__ Y,
+                                                        const float* __restrict__ mu,
+                                                        double* __restrict__ part) {
+    constexpr int E = Vec<T>::E, K = LPR * E;
+    const int sub = (threadIdx.x & 31) % LPR;
+    const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
+    const int64_t ng = (int64_t)gridDim.x * kBlock / LPR;
+    float m[E], s1[E], s2[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        m[e] = SUB_MU ? mu[sub * E + e] : 0.f;
+        s1[e] = s2[e] = 0.f;
+    }
+    for (int64_t h = g0; h < nh; h += ng) {
+        const int32_t r = hrow[h];
+        float acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        for (int32_t sid = hsoff[h]; sid < hsoff[h + 1]; ++sid) {
+            const float* pr = partial + (int64_t)sid * K + sub * E;
+#pragma unroll
+            for (int e = 0; e < E; e += 4) {
+                const float4 q = *reinterpret_cast<const float4*>(pr + e);
+                acc[e] += q.x;
+                acc[e + 1] += q.y;
+                acc[e + 2] += q.z;
+                acc[e + 3] += q.w;
+            }
+        }
+        float xs[E], y[E];
+        Vec<T>::unpack(Vec<T>::load_raw(X + (int64_t)r * K + sub * E), xs);
+        const float cp = coef[r];
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] = fmaf(cp, acc[e], a_self * xs[e]) - m[e];
+        Vec<T>::store(Y + (int64_t)r * K + sub * E, y);
+        if (STATS)
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const float q = Vec<T>::round(y[e]);
+                s1[e] += q;
+                s2[e] = fmaf(q, q, s2[e]);
+            }
+    }
+    if (STATS) block_column_partials<LPR, E>(s1, s2, part);
+}
+
+__global__ void k_heavy_mark(int32_t n, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ heavy,
+                             int32_t* __restrict__ nseg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = row_ptr[r + 1] - row_ptr[r];
+        heavy[r] = d > kHeavy;
+        nseg[r] = d > kHeavy ? (d + kSeg - 1) / kSeg : 0;
+    }
+}
+
+__global__ void k_heavy_fill(int32_t n, const int32_t* __restrict__ row_ptr, const int64_t* __restrict__ hoff,
+                             const int64_t* __restrict__ soff, int32_t* __restrict__ hrow,
+                             int32_t* __restrict__ hsoff, int4* __restrict__ seg) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        if (r == 0) hsoff[hoff[n]] = (int32_t)soff[n];
+        if (hoff[r + 1] == hoff[r]) continue;
+        const int64_t h = hoff[r];
+        hrow[h] = (int32_t)r;
+        hsoff[h] = (int32_t)soff[r];
+        const int32_t a = row_ptr[r], b = row_ptr[r + 1];
+        int64_t o = soff[r];
+        for (int32_t j = a; j < b; j += kSeg) seg[o++] = make_int4((int32_t)r, j, min(j + kSeg, b), 0);
+    }
+}
+
+// Heavy-row lists of L (a cache of the graph, built on its first sweep).
+sfg_status heavy_prepare(sfg_ctx* ctx, const sfg_graph* Lc) {
+    sfg_graph* L = const_cast<sfg_graph*>(Lc);
+    if (L->hv_n >= 0) return SFG_OK;
+    const int32_t n = L->n;
+    if (n == 0) {
+        L->hv_n = 0;
+        return SFG_OK;
+    }
+    Scratch s(ctx);
+    int32_t *heavy, *nseg;
+    int64_t *hoff, *soff;
+    SFG_TRY(s.get(&heavy, (size_t)n));
+    SFG_TRY(s.get(&nseg, (size_t)n));
+    SFG_TRY(s.get(&hoff, (size_t)n + 1));
+    SFG_TRY(s.get(&soff, (size_t)n + 1));
+    const int g = sfg_grid(ctx, (const void*)k_heavy_mark, kBlock, 0, n);
+    k_heavy_mark<<<g, kBlock, 0, ctx->stream>>>(n, L->row_ptr, heavy, nseg);
+    ++ctx->launches;
+    SFG_LAUNCH_CHECK(ctx, "k_heavy_mark");
+    SFG_TRY(sfg_scan_i32(ctx, heavy, hoff, n));
+    SFG_TRY(sfg_scan_i32(ctx, nseg, soff, n));
+    int64_t nh = 0, ns = 0;
+    SFG_TRY(sfg_read_i64(ctx, hoff + n, &nh));
+    SFG_TRY(sfg_read_i64(ctx, soff + n, &ns));
+    if (nh > 0) {
+        int32_t *hrow = nullptr, *hsoff = nullptr;
+        int4* seg = nullptr;
+        sfg_status st = sfg_alloc(ctx, (void**)&hrow, sizeof(int32_t) * nh);
+        if (st == SFG_OK) st = sfg_alloc(ctx, (void**)&hsoff, sizeof(int32_t) * (nh + 1));
+        if (st == SFG_OK) st = sfg_alloc(ctx, (void**)&seg, sizeof(int4) * ns);
+        if (st != SFG_OK) {
+            for (void* q : {(void*)hrow, (void*)hsoff, (void*)seg})
+                if (q) sfg_free(ctx, q);
+            return st;
+        }
+        L->hv_rows = hrow;  // owned by the graph from here on
+        L->hv_soff = hsoff;
+        L->hv_seg = seg;
+        k_heavy_fill<<<g, kBlock, 0, ctx->stream>>>(n, L->row_ptr, hoff, soff, hrow, hsoff, seg);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_heavy_fill");
+    }
+    L->hv_nseg = ns;
+    L->hv_n = (int32_t)nh;
+    return SFG_OK;
 }
 
 // One colour class of a multicolour Gauss-Seidel sweep (Sec. 3.2 relaxes L x = 0 with
@@ -636,10 +811,17 @@ struct Smoother {
         return sfg_grid(ctx, kern<false, false>(), kBlock, 0, (int64_t)n * LPR);
     }
 
+    // Statistics slots a sweep of L with `grid` tile CTAs writes (the heavy rows add theirs).
+    static int part_slots(const sfg_graph* L, int grid) {
+        return grid + (L->hv_n > 0 ? kHeavyGrid : 0);
+    }
+
     static sfg_status sweep(sfg_ctx* ctx, const sfg_graph* L, const float* coef, float a_self,
                             const T* X, T* Y, const float* mu, double* part, bool sub_mu,
                             bool stats, int grid) {
         const int32_t n = L->n;
+        SFG_TRY(heavy_prepare(ctx, L));
+        const int32_t hmax = L->hv_n > 0 ? kHeavy : INT32_MAX;
         void* k = sub_mu ? (stats ? kern<true, true>() : kern<true, false>())
                          : (stats ? kern<false, true>() : kern<false, false>());
         int g = grid;
@@ -650,13 +832,36 @@ struct Smoother {
                 g = sfg_grid(ctx, k, kBlock, 0, (int64_t)n * LPR);
             }
         }
-        void* args[] = {(void*)&n, (void*)&L->row_ptr, (void*)&L->colval, (void*)&coef,
+        void* args[] = {(void*)&n, (void*)&hmax, (void*)&L->row_ptr, (void*)&L->colval, (void*)&coef,
                         (void*)&a_self, (void*)&X, (void*)&Y, (void*)&mu, (void*)&part};
         sfg_tic(ctx, "jacobi");
         ++ctx->launches;
         const cudaError_t e = cudaLaunchKernel(k, dim3(g), dim3(kBlock), args, 0, ctx->stream);
         sfg_toc(ctx);
         if (e != cudaSuccess) return sfg_cuda_fail(ctx, e, "k_jacobi");
+        if (L->hv_n > 0) {
+            Scratch sc(ctx);
+            float* partial;
+            SFG_TRY(sc.get(&partial, (size_t)L->hv_nseg * K));
+            const int gp = sfg_grid(ctx, (const void*)k_heavy_part<T, LPR>, kBlock, 0,
+                                    L->hv_nseg * LPR);
+            sfg_tic(ctx, "jacobi_heavy");
+            k_heavy_part<T, LPR><<<gp, kBlock, 0, ctx->stream>>>(L->hv_nseg, L->hv_seg, L->colval, X,
+                                                                 partial);
+            double* hp = part ? part + (size_t)grid * 2 * K : nullptr;
+            const int32_t nh = L->hv_n;
+            if (sub_mu)
+                (stats ? k_heavy_final<T, LPR, true, true> : k_heavy_final<T, LPR, true, false>)
+                    <<<kHeavyGrid, kBlock, 0, ctx->stream>>>(nh, L->hv_rows, L->hv_soff, partial, coef,
+                                                             a_self, X, Y, mu, hp);
+            else
+                (stats ? k_heavy_final<T, LPR, false, true> : k_heavy_final<T, LPR, false, false>)
+                    <<<kHeavyGrid, kBlock, 0, ctx->stream>>>(nh, L->hv_rows, L->hv_soff, partial, coef,
+                                                             a_self, X, Y, mu, hp);
+            sfg_toc(ctx);
+            ctx->launches += 2;
+            SFG_LAUNCH_CHECK(ctx, "heavy rows");
+        }
         return SFG_OK;
     }
 
@@ -672,7 +877,7 @@ struct Smoother {
         SFG_TRY(s.get(&coef, (size_t)n));
         SFG_TRY(s.get(&mu, K));
         SFG_TRY(s.get(&scale, K));
-        SFG_TRY(s.get(&part, (size_t)grid * 2 * K));
+        SFG_TRY(s.get(&part, (size_t)(grid + kHeavyGrid) * 2 * K));
         k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
             n, L->invdeg, omega, coef); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_coef");
@@ -695,7 +900,7 @@ struct Smoother {
             std::swap(cur, nxt);
         }
         if (steps > 0) {
-            k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, 1, mu, scale); ++ctx->launches;
+            k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, part_slots(L, grid), K, n, 1, mu, scale); ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_finalize");
         }
         sfg_tic(ctx, "project");
@@ -780,7 +985,7 @@ struct Smoother {
             nxt = (nxt == b0) ? b1 : b0;
         }
         if (steps > 0) {
-            k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, 1, mean, scale);
+            k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, part_slots(L, grid), K, n, 1, mean, scale);
             ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_finalize");
         }
@@ -811,7 +1016,7 @@ struct Smoother {
         SFG_TRY(s.get(&sg, K));
         SFG_TRY(s.get(&mp, K));
         SFG_TRY(s.get(&sp, K));
-        SFG_TRY(s.get(&part, (size_t)grid * 2 * K));
+        SFG_TRY(s.get(&part, (size_t)(grid + kHeavyGrid) * 2 * K));
         sfg_tic(ctx, "init");
         // the D-weighted mean is taken on L_G; L_P has the same nodes, and any constant left in
         // the block is removed by the projection in exact arithmetic
@@ -905,7 +1110,7 @@ struct Smoother {
         SFG_TRY(s.get(&x, (size_t)n * K));
         SFG_TRY(s.get(&y, (size_t)n * K));
         SFG_TRY(s.get(&coef, (size_t)n));
-        SFG_TRY(s.get(&part, (size_t)grid * 2 * K));
+        SFG_TRY(s.get(&part, (size_t)(grid + kHeavyGrid) * 2 * K));
         k_init<T, LPR, false><<<grid, kBlock, 0, ctx->stream>>>(n, 12345, L->deg, x, part);
         k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
             n, L->invdeg, 0.7, coef);
@@ -914,6 +1119,8 @@ struct Smoother {
         cudaEvent_t e0, e1;
         SFG_CUDA(ctx, cudaEventCreate(&e0));
         SFG_CUDA(ctx, cudaEventCreate(&e1));
+        SFG_TRY(heavy_prepare(ctx, L));  // the tile kernel is timed as the sweep runs it
+        const int32_t hmax = L->hv_n > 0 ? kHeavy : INT32_MAX;
         int best = kJDefault;
         float best_ms = 1e30f;
         const float a_self = 0.3f;
@@ -924,7 +1131,7 @@ struct Smoother {
             const int g = sfg_grid(ctx, k, kBlock, 0, (int64_t)n * LPR);
             const T* X = x;
             T* Y = y;
-            void* args[] = {(void*)&n, (void*)&L->row_ptr, (void*)&L->colval, (void*)&coef,
+            void* args[] = {(void*)&n, (void*)&hmax, (void*)&L->row_ptr, (void*)&L->colval, (void*)&coef,
                             (void*)&a_self, (void*)&X, (void*)&Y, (void*)&mu, (void*)&pp};
             for (int r = 0; r < 4; ++r) {  // one warm-up, three timed
                 if (r == 1) cudaEventRecord(e0, ctx->stream);
