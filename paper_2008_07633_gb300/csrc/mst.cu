@@ -4,7 +4,8 @@
 // Boruvka rounds under the strict order (weight descending, edge id ascending): every edge key is
 // (FP32 weight bits << 32) | ~id, unique and ordered like that order, so the forest is unique and
 // equal to Kruskal's. A round: (1) each component takes the largest key among edges leaving it
-// (per node over its CSR row, then one 64-bit atomicMax per node), (2) marks that edge and hooks to the component across it, (3) the 2-cycles
+// (per row over its CSR entries, then one 64-bit atomicMax per row or per segment of a long
+// row), (2) marks that edge and hooks to the component across it, (3) the 2-cycles
 // that mutual choices create are broken toward the smaller label, (4) pointer jumping flattens the
 // hook forest, (5) nodes are relabelled. Rounds repeat until no component has an outgoing edge.
 #include "sfg_internal.cuh"
@@ -26,18 +27,40 @@ __global__ void k_mst_reset(int32_t n, unsigned long long* __restrict__ best, in
     if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 0;
 }
 
-// Each component's largest key among the edges leaving it, from the CSR rows: a node takes the
-// largest key among its entries that leave its component and issues one atomicMax for its
-// component. Every edge leaving a component sits in the row of its endpoint inside it.
-__global__ void k_mst_rows(int32_t n, const int32_t* __restrict__ row_ptr,
-                           const int2* __restrict__ colval, const int32_t* __restrict__ eid,
-                           const uint8_t* __restrict__ allow, const int32_t* __restrict__ comp,
-                           unsigned long long* __restrict__ best) {
-    for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * kBlock) {
-        const int32_t cp = comp[p];
+// Each component's largest key among the edges leaving it, from the CSR rows: a group of 8 lanes
+// takes a row (a warp, 4 rows), its lanes stride over the row's entries, the group folds the
+// largest key that leaves the row's component and issues one atomicMax for that component. Every
+// edge leaving a component sits in the row of its endpoint inside it. SEG = false: rows
+// [0, n), skipping rows longer than SFG_HEAVY_ROW; SEG = true: the fixed segments of those rows.
+constexpr int kMstLanes = 8;
+
+template <bool SEG>
+__global__ void __launch_bounds__(kBlock) k_mst_rows(int64_t nitems, const int32_t* __restrict__ row_ptr,
+                                                     const int4* __restrict__ seg,
+                                                     const int2* __restrict__ colval,
+                                                     const int32_t* __restrict__ eid,
+                                                     const uint8_t* __restrict__ allow,
+                                                     const int32_t* __restrict__ comp,
+                                                     unsigned long long* __restrict__ best) {
+    const int sub = threadIdx.x % kMstLanes;
+    const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kMstLanes;
+    const int64_t ng = (int64_t)gridDim.x * kBlock / kMstLanes;
+    // the same trip count for the whole warp, so the group folds below run converged
+    for (int64_t i0 = g0 - g0 % (32 / kMstLanes); i0 < nitems; i0 += ng) {
+        const int64_t it = i0 + (g0 % (32 / kMstLanes));
+        int32_t p = 0, a = 0, b = 0;
+        if (it < nitems) {
+            if (SEG) {
+                const int4 sg = seg[it];
+                p = sg.x, a = sg.y, b = sg.z;
+            } else {
+                p = (int32_t)it, a = row_ptr[it], b = row_ptr[it + 1];
+                if (b - a > SFG_HEAVY_ROW) b = a;  // swept by segments
+            }
+        }
+        const int32_t cp = it < nitems ? comp[p] : 0;
         unsigned long long local = 0ull;
-        for (int32_t j = row_ptr[p]; j < row_ptr[p + 1]; ++j) {
+        for (int32_t j = a + sub; j < b; j += kMstLanes) {
             const int2 cv = colval[j];
             if (comp[cv.x] == cp) continue;
             const int32_t e = eid[j];
@@ -46,7 +69,12 @@ __global__ void k_mst_rows(int32_t n, const int32_t* __restrict__ row_ptr,
                 ((unsigned long long)(uint32_t)cv.y << 32) | (unsigned long long)(~(uint32_t)e);
             local = key > local ? key : local;
         }
-        if (local) atomicMax(&best[cp], local);
+#pragma unroll
+        for (int o = 1; o < kMstLanes; o <<= 1) {
+            const unsigned long long q = __shfl_xor_sync(0xffffffffu, local, o);
+            local = q > local ? q : local;
+        }
+        if (sub == 0 && local) atomicMax(&best[cp], local);
     }
 }
 
@@ -179,12 +207,24 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
     SFG_TRY(s.get(&best, n));
     SFG_TRY(s.get(&flag, 1));
     const int gn = sfg_grid(ctx, (const void*)k_mst_hook, kBlock, 0, n);
+    SFG_TRY(sfg_heavy_prepare(ctx, g));
+    const int gr = sfg_grid(ctx, (const void*)k_mst_rows<false>, kBlock, 0, (int64_t)n * kMstLanes);
+    const int gs = g->hv_n > 0 ? sfg_grid(ctx, (const void*)k_mst_rows<true>, kBlock, 0,
+                                          g->hv_nseg * kMstLanes)
+                               : 0;
     k_mst_init<<<gn, kBlock, 0, ctx->stream>>>(n, comp); ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_mst_init");
     // each round at least halves the number of components that still have outgoing edges
     for (int round = 0; round < 64; ++round) {
         k_mst_reset<<<gn, kBlock, 0, ctx->stream>>>(n, best, flag); ++ctx->launches;
-        k_mst_rows<<<gn, kBlock, 0, ctx->stream>>>(n, g->row_ptr, g->colval, g->eid, allow, comp, best); ++ctx->launches;
+        k_mst_rows<false><<<gr, kBlock, 0, ctx->stream>>>(n, g->row_ptr, nullptr, g->colval, g->eid,
+                                                          allow, comp, best);
+        ++ctx->launches;
+        if (gs > 0) {
+            k_mst_rows<true><<<gs, kBlock, 0, ctx->stream>>>(g->hv_nseg, nullptr, g->hv_seg, g->colval,
+                                                             g->eid, allow, comp, best);
+            ++ctx->launches;
+        }
         k_mst_hook<<<gn, kBlock, 0, ctx->stream>>>(n, g->eu, g->ev, comp, best, parent, mask, flag); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_mst_round");
         int hflag = 0;

@@ -212,6 +212,10 @@ sfg_status sfg_kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask,
                           uint64_t seed, double* kappa, double* info6);
 // Build the Gauss-Seidel colouring of L once (cached on the graph; color.cu).
 sfg_status sfg_gs_prepare(sfg_ctx* ctx, const sfg_graph* L);
+// Rows with more than SFG_HEAVY_ROW entries and their SFG_HEAVY_SEG-entry segments (hv_* of the
+// graph), built once per graph (smooth.cu); the sweep and the spanning-forest rounds use them.
+constexpr int32_t SFG_HEAVY_ROW = 256, SFG_HEAVY_SEG = 128;
+sfg_status sfg_heavy_prepare(sfg_ctx* ctx, const sfg_graph* L);
 // Give P (a subgraph of G on the same nodes) G's colouring, which is proper for P too.
 sfg_status sfg_gs_inherit(sfg_ctx* ctx, const sfg_graph* P, const sfg_graph* G);
 // y_p = d_p - omega * (weight to nodes after p in (colour, id) order): the weights of the

@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kBlock, MINB)
 // partial sum of w * X[col] over its segment (k_heavy_part), and one group per row adds the row's
 // partials in segment order and applies the update (k_heavy_final). The segmentation is fixed per
 // graph, so the result does not depend on the schedule. The lists are built once per graph.
-constexpr int32_t kHeavy = 256, kSeg = 128;
+constexpr int32_t kHeavy = SFG_HEAVY_ROW, kSeg = SFG_HEAVY_SEG;
 constexpr int kHeavyGrid = 64;  // CTAs of k_heavy_final: its statistics take as many part slots
 
 template <typename T, int LPR>
@@ -1204,6 +1204,8 @@ sfg_status dispatch(int K, sfg_dtype dt, F&& f) {
 }
 
 }  // namespace
+
+sfg_status sfg_heavy_prepare(sfg_ctx* ctx, const sfg_graph* L) { return heavy_prepare(ctx, L); }
 
 bool sfg_k_supported(int K, sfg_dtype dt) {
     if (dt == SFG_F32) return K == 4 || K == 8 || K == 16 || K == 32 || K == 64;
