@@ -67,7 +67,7 @@ def load_peaks():
 # the committed ncu counters stay valid while this text is unchanged.
 KERNEL_SOURCES = {
     "k_jacobi": ("smooth.cu", "template <typename V>\n__device__ __forceinline__ V ldmeta",
-                 "// One colour class of a multicolour Gauss-Seidel sweep", ["vec.cuh"]),
+                 "// Rows longer than kHeavy entries", ["vec.cuh"]),
     "k_score": ("score.cu", "// Scorer, warp-tile schedule", "// ||X_p||^2 in FP64", ["vec.cuh"]),
     "k_mlp_forward_tc": ("mlp.cu", "// ---- inference on the 5th-generation tensor cores",
                          "constexpr int kS64 = 72;", []),
@@ -310,7 +310,9 @@ def run_ours(args):
     e_off = off.numel()
     # deployment-time tuning of the sweep's tile shape for each Laplacian (outside the timed
     # region; the choice is recorded per degree bucket and the result is bit-identical)
-    tuned = {"G": S.sfg_autotune(ctx, G, K), "P": S.sfg_autotune(ctx, P, K)}
+    # (--profile keeps the default shape: under a profiler the tuner's timings mean nothing)
+    tuned = ({"G": (1, None), "P": (1, None)} if args.profile else
+             {"G": S.sfg_autotune(ctx, G, K), "P": S.sfg_autotune(ctx, P, K)})
     kk = int(np.floor(BETA * n + 0.5))
     scores = torch.empty(e_off, dtype=torch.float32, device=dev)
     sel = torch.empty(kk, dtype=torch.int32, device=dev)
@@ -359,7 +361,7 @@ def run_ours(args):
 
     # sparsify time (device-resident G) and the end-to-end number through the public API with
     # host buffers: H2D of the edge list, Laplacian, flat sparsify, D2H of the mask
-    mlp = mlp_report(S, ctx, dev, args.mlp_rows, 10) if args.mlp_rows > 0 else None
+    mlp = mlp_report(S, ctx, dev, args.mlp_rows, 10) if args.mlp_rows > 0 and not args.profile else None
     if args.profile:  # launch-list / counter captures: the filter+score steps only
         if rank == 0:
             print(json.dumps({"profile": True, "ms_per_step": ms, "value": value,

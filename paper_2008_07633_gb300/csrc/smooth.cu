@@ -421,12 +421,16 @@ __global__ void __launch_bounds__(kBlock) k_heavy_final(int32_t nh, const int32_
 }
 
 __global__ void k_heavy_mark(int32_t n, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ heavy,
-                             int32_t* __restrict__ nseg) {
+                             int32_t* __restrict__ nseg, int* __restrict__ count) {
+    int c = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t d = row_ptr[r + 1] - row_ptr[r];
         heavy[r] = d > kHeavy;
         nseg[r] = d > kHeavy ? (d + kSeg - 1) / kSeg : 0;
+        c += d > kHeavy;
     }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
 __global__ void k_heavy_fill(int32_t n, const int32_t* __restrict__ row_ptr, const int64_t* __restrict__ hoff,
@@ -456,14 +460,25 @@ sfg_status heavy_prepare(sfg_ctx* ctx, const sfg_graph* Lc) {
     Scratch s(ctx);
     int32_t *heavy, *nseg;
     int64_t *hoff, *soff;
+    int* count;
     SFG_TRY(s.get(&heavy, (size_t)n));
     SFG_TRY(s.get(&nseg, (size_t)n));
-    SFG_TRY(s.get(&hoff, (size_t)n + 1));
-    SFG_TRY(s.get(&soff, (size_t)n + 1));
+    SFG_TRY(s.get(&count, 1));
+    SFG_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int), ctx->stream));
     const int g = sfg_grid(ctx, (const void*)k_heavy_mark, kBlock, 0, n);
-    k_heavy_mark<<<g, kBlock, 0, ctx->stream>>>(n, L->row_ptr, heavy, nseg);
+    k_heavy_mark<<<g, kBlock, 0, ctx->stream>>>(n, L->row_ptr, heavy, nseg, count);
     ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_heavy_mark");
+    int hcount = 0;
+    SFG_CUDA(ctx, cudaMemcpyAsync(&hcount, count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (hcount == 0) {  // the common case on meshes: one pass over row_ptr, one readback
+        L->hv_nseg = 0;
+        L->hv_n = 0;
+        return SFG_OK;
+    }
+    SFG_TRY(s.get(&hoff, (size_t)n + 1));
+    SFG_TRY(s.get(&soff, (size_t)n + 1));
     SFG_TRY(sfg_scan_i32(ctx, heavy, hoff, n));
     SFG_TRY(sfg_scan_i32(ctx, nseg, soff, n));
     int64_t nh = 0, ns = 0;
