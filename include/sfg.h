@@ -67,7 +67,15 @@ typedef struct sfg_graph sfg_graph; /* canonical edge list + CSR Laplacian, devi
  * the legacy default stream). The stream is borrowed: it must outlive the context and every
  * graph created through it. */
 SFG_API sfg_status sfg_ctx_create(sfg_ctx** out, int device, void* cuda_stream);
+/* Destroys the context and returns the unused memory of the library's pool to the device
+ * (graphs and networks made through it stay valid until they are destroyed). */
 SFG_API void sfg_ctx_destroy(sfg_ctx* ctx);
+/* Device memory: every allocation of the library (graphs, scratch) comes stream-ordered from one
+ * pool per device, shared by the contexts on that device and kept for the life of the process,
+ * which holds freed memory for reuse instead of returning it at each synchronisation.
+ * sfg_ctx_trim synchronises the context stream and returns the pool's unused memory to the
+ * device (an allocation that fails also trims and retries once). */
+SFG_API sfg_status sfg_ctx_trim(sfg_ctx* ctx);
 SFG_API sfg_status sfg_ctx_set_stream(sfg_ctx* ctx, void* cuda_stream);
 /* Text of the last error on this context ("" if none). Valid until the next call on ctx. */
 SFG_API const char* sfg_last_error(const sfg_ctx* ctx);

@@ -2,6 +2,7 @@
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "sfg_internal.cuh"
 
@@ -32,11 +33,18 @@ sfg_status sfg_alloc(sfg_ctx* ctx, void** p, size_t bytes) {
     if (ctx->fail_alloc_at >= 0 && ctx->alloc_count == ctx->fail_alloc_at)
         return sfg_fail(ctx, SFG_ENOMEM, "injected allocation failure (allocation %lld)",
                         (long long)ctx->alloc_count);
-    cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
+    if (e == cudaErrorMemoryAllocation) {
+        // the pool keeps freed memory; hand it back to the device and try once more
+        cudaGetLastError();
+        cudaStreamSynchronize(ctx->stream);
+        cudaMemPoolTrimTo(ctx->pool, 0);
+        e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
-        return sfg_fail(ctx, SFG_ENOMEM, "cudaMallocAsync(%zu bytes) failed: %s", bytes,
+        return sfg_fail(ctx, SFG_ENOMEM, "cudaMallocFromPoolAsync(%zu bytes) failed: %s", bytes,
                         cudaGetErrorString(e));
     }
     return SFG_OK;
@@ -119,6 +127,33 @@ void sfg_tune_record(sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L, int 
 
 extern "C" {
 
+// The library's memory pool on `device`: created on first use and kept for the life of the
+// process, shared by every context on the device, with a release threshold that keeps freed
+// memory mapped (the device's default pool returns everything at each synchronisation, and the
+// next large block then pays for mapping it again). Graphs and networks may outlive the context
+// that made them, so the pool is never destroyed; contexts only trim it.
+static cudaMemPool_t device_pool(int device) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(device);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &pp) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[device] = pool;
+    return pool;
+}
+
 sfg_status sfg_ctx_create(sfg_ctx** out, int device, void* cuda_stream) {
     if (!out) return SFG_EINVAL;
     *out = nullptr;
@@ -134,7 +169,19 @@ sfg_status sfg_ctx_create(sfg_ctx** out, int device, void* cuda_stream) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (c->num_sms < 1) c->num_sms = 1;
     if (const char* f = std::getenv("SFG_FAULT_ALLOC")) c->fail_alloc_at = std::atoll(f);
+    c->pool = device_pool(device);
+    if (!c->pool) {
+        delete c;
+        return SFG_ECUDA;
+    }
     *out = c;
+    return SFG_OK;
+}
+
+sfg_status sfg_ctx_trim(sfg_ctx* ctx) {
+    if (!ctx) return SFG_EINVAL;
+    SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    SFG_CUDA(ctx, cudaMemPoolTrimTo(ctx->pool, 0));
     return SFG_OK;
 }
 
@@ -145,6 +192,11 @@ void sfg_ctx_destroy(sfg_ctx* ctx) {
         cudaEventDestroy(r.stop);
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->pool) {
+        // unused memory goes back to the device; memory of live graphs stays valid
+        cudaStreamSynchronize(ctx->stream);
+        cudaMemPoolTrimTo(ctx->pool, 0);
+    }
     delete ctx;
 }
 

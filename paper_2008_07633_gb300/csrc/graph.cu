@@ -322,6 +322,13 @@ sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
             SFG_LAUNCH_CHECK(ctx, "k_lap_f2c");
         }
     }
+    // the sweep's heavy-row lists are built with the graph, so that later calls (which may be
+    // captured into a CUDA graph) never synchronise for them
+    const sfg_status hs = sfg_heavy_prepare(ctx, g);
+    if (hs != SFG_OK) {
+        sfg_graph_free(g);
+        return hs;
+    }
     *out = g;
     return SFG_OK;
 }
@@ -367,6 +374,11 @@ sfg_status sfg_subgraph_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* ma
         k_lap_deg<<<grid_of(ctx, k_lap_deg, g->n), kBlock, 0, ctx->stream>>>(p->row_ptr, p->colval,
                                                                              g->n, p->deg, p->invdeg); ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_lap_deg");
+    }
+    const sfg_status hs = sfg_heavy_prepare(ctx, p);
+    if (hs != SFG_OK) {
+        sfg_graph_free(p);
+        return hs;
     }
     *out = p;
     return SFG_OK;

@@ -24,6 +24,7 @@ struct sfg_timer_rec {
 struct sfg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;          // the device's stream-ordered pool of the library
     int num_sms = 0;
     std::string last_error;
     bool timing = false;

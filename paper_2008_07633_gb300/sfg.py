@@ -20,7 +20,7 @@ STATUS = {0: "SFG_OK", 1: "SFG_EINVAL", 2: "SFG_ENOMEM", 3: "SFG_ECUDA", 4: "SFG
           5: "SFG_ECAPACITY", 6: "SFG_EUNSUPPORTED"}
 
 # Every symbol declared in include/sfg.h.
-EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_set_stream", "sfg_last_error",
+EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_trim", "sfg_ctx_set_stream", "sfg_last_error",
            "sfg_ctx_timing", "sfg_ctx_kernel_time", "sfg_ctx_launches", "sfg_laplacian", "sfg_graph_destroy",
            "sfg_graph_info", "sfg_graph_edges", "sfg_graph_csr", "sfg_graph_subgraph", "sfg_smooth",
            "sfg_jacobi", "sfg_score_edges", "sfg_select_topk", "sfg_spanning_tree", "sfg_affinity",
@@ -64,6 +64,7 @@ def lib():
         sig = {
             "sfg_ctx_create": [ctypes.POINTER(_vp), _int, _vp],
             "sfg_ctx_destroy": [_vp],
+            "sfg_ctx_trim": [_vp],
             "sfg_ctx_set_stream": [_vp, _vp],
             "sfg_last_error": [_vp],
             "sfg_ctx_timing": [_vp, _int],
@@ -148,6 +149,10 @@ class Context:
     def check(self, st):
         if st != 0:
             raise SfgError(st, lib().sfg_last_error(self.h).decode())
+
+    def trim(self):
+        """Return the context pool's unused device memory to the device."""
+        self.check(lib().sfg_ctx_trim(self.h))
 
     def set_stream(self, stream):
         self._stream = stream

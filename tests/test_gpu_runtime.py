@@ -120,3 +120,17 @@ def test_argument_errors_leave_context_usable(S):
     x = S.sfg_smooth(ctx, g, 8, 3)
     torch.cuda.synchronize()
     assert torch.isfinite(x).all()
+
+
+def test_pool_trim_keeps_context_usable(S):
+    ctx = S.sfg_ctx_create(0)
+    n, u, v, w = gen.grid2d(40, 40, seed=2)
+    g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
+    a = S.sfg_smooth(ctx, g, 16, 5, 0.7, seed=4)
+    torch.cuda.synchronize()
+    ctx.trim()
+    b = S.sfg_smooth(ctx, g, 16, 5, 0.7, seed=4)   # allocations after a trim map memory again
+    assert torch.equal(a, b)
+    del g
+    ctx.close()
+
