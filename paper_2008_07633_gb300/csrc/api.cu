@@ -54,6 +54,13 @@ void sfg_free(sfg_ctx* ctx, void* p) {
     if (p) cudaFreeAsync(p, ctx->stream);
 }
 
+sfg_status sfg_host_word(sfg_ctx* ctx, int slot, int** out) {
+    if (!ctx->host_word)
+        SFG_CUDA(ctx, cudaMallocHost((void**)&ctx->host_word, sizeof(int) * kSfgHostWords));
+    *out = ctx->host_word + slot;
+    return SFG_OK;
+}
+
 sfg_status sfg_check_dev(sfg_ctx* ctx, const void* p, const char* what) {
     if (!p) return sfg_fail(ctx, SFG_EINVAL, "%s is NULL", what);
     cudaPointerAttributes a;
@@ -192,6 +199,10 @@ void sfg_ctx_destroy(sfg_ctx* ctx) {
         cudaEventDestroy(r.stop);
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->host_word) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFreeHost(ctx->host_word);
+    }
     if (ctx->pool) {
         // unused memory goes back to the device; memory of live graphs stays valid
         cudaStreamSynchronize(ctx->stream);

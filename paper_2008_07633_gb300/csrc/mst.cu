@@ -28,11 +28,30 @@ __global__ void k_mst_reset(int32_t n, unsigned long long* __restrict__ best, in
 }
 
 // Each component's largest key among the edges leaving it, from the CSR rows: a group of 8 lanes
-// takes a row (a warp, 4 rows), its lanes stride over the row's entries, the group folds the
-// largest key that leaves the row's component and issues one atomicMax for that component. Every
+// takes kMstItems rows at a time, its lanes stride over each row's entries (the first entry of all
+// rows is loaded before any later one), the group folds the largest key that leaves the row's
+// component and issues one atomicMax for that component. Every
 // edge leaving a component sits in the row of its endpoint inside it. SEG = false: rows
 // [0, n), skipping rows longer than SFG_HEAVY_ROW; SEG = true: the fixed segments of those rows.
-constexpr int kMstLanes = 8;
+constexpr int kMstLanes = 8, kMstItems = 4;
+
+struct MstItem {
+    int32_t a, b, cp;
+    unsigned long long best;
+};
+
+// Candidate key of CSR entry j of a row in component cp (0 if the entry stays inside it or the
+// edge is not allowed).
+__device__ __forceinline__ unsigned long long mst_key(int32_t j, int32_t cp, const int2* __restrict__ colval,
+                                                      const int32_t* __restrict__ eid,
+                                                      const uint8_t* __restrict__ allow,
+                                                      const int32_t* __restrict__ comp) {
+    const int2 cv = colval[j];
+    if (comp[cv.x] == cp) return 0ull;
+    const int32_t e = eid[j];
+    if (allow && !allow[e]) return 0ull;
+    return ((unsigned long long)(uint32_t)cv.y << 32) | (unsigned long long)(~(uint32_t)e);
+}
 
 template <bool SEG>
 __global__ void __launch_bounds__(kBlock) k_mst_rows(int64_t nitems, const int32_t* __restrict__ row_ptr,
@@ -45,36 +64,62 @@ __global__ void __launch_bounds__(kBlock) k_mst_rows(int64_t nitems, const int32
     const int sub = threadIdx.x % kMstLanes;
     const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kMstLanes;
     const int64_t ng = (int64_t)gridDim.x * kBlock / kMstLanes;
-    // the same trip count for the whole warp, so the group folds below run converged
-    for (int64_t i0 = g0 - g0 % (32 / kMstLanes); i0 < nitems; i0 += ng) {
-        const int64_t it = i0 + (g0 % (32 / kMstLanes));
-        int32_t p = 0, a = 0, b = 0;
-        if (it < nitems) {
-            if (SEG) {
-                const int4 sg = seg[it];
-                p = sg.x, a = sg.y, b = sg.z;
-            } else {
-                p = (int32_t)it, a = row_ptr[it], b = row_ptr[it + 1];
-                if (b - a > SFG_HEAVY_ROW) b = a;  // swept by segments
+    const int64_t lg = g0 % (32 / kMstLanes);
+    // kMstItems rows per group and iteration, so that as many independent load chains are in
+    // flight; the same trip count for the whole warp, so the group folds below run converged
+    for (int64_t i0 = g0 - lg; i0 < nitems; i0 += ng * kMstItems) {
+        MstItem it[kMstItems];
+        int32_t p[kMstItems];
+#pragma unroll
+        for (int u = 0; u < kMstItems; ++u) {
+            const int64_t k = i0 + lg + (int64_t)u * ng;
+            it[u].a = it[u].b = 0;
+            p[u] = 0;
+            if (k < nitems) {
+                if (SEG) {
+                    const int4 sg = seg[k];
+                    p[u] = sg.x, it[u].a = sg.y, it[u].b = sg.z;
+                } else {
+                    p[u] = (int32_t)k, it[u].a = row_ptr[k], it[u].b = row_ptr[k + 1];
+                    if (it[u].b - it[u].a > SFG_HEAVY_ROW) it[u].b = it[u].a;  // swept by segments
+                }
             }
         }
-        const int32_t cp = it < nitems ? comp[p] : 0;
-        unsigned long long local = 0ull;
-        for (int32_t j = a + sub; j < b; j += kMstLanes) {
-            const int2 cv = colval[j];
-            if (comp[cv.x] == cp) continue;
-            const int32_t e = eid[j];
-            if (allow && !allow[e]) continue;
-            const unsigned long long key =
-                ((unsigned long long)(uint32_t)cv.y << 32) | (unsigned long long)(~(uint32_t)e);
-            local = key > local ? key : local;
+        // the row's own label and its first entry (most rows of meshes and k-NN graphs have no
+        // second) with the entry's edge id, all issued before any of them is used: the chain is
+        // row bounds -> entry -> neighbour's label
+        int2 cv[kMstItems];
+        int32_t e[kMstItems];
+#pragma unroll
+        for (int u = 0; u < kMstItems; ++u) {
+            it[u].cp = comp[p[u]];
+            const int32_t j = it[u].a + sub;
+            cv[u] = j < it[u].b ? colval[j] : make_int2(p[u], 0);
+            e[u] = j < it[u].b ? eid[j] : 0;
         }
 #pragma unroll
-        for (int o = 1; o < kMstLanes; o <<= 1) {
-            const unsigned long long q = __shfl_xor_sync(0xffffffffu, local, o);
-            local = q > local ? q : local;
+        for (int u = 0; u < kMstItems; ++u) {
+            const bool out = comp[cv[u].x] != it[u].cp && (!allow || allow[e[u]]);
+            it[u].best = out ? ((unsigned long long)(uint32_t)cv[u].y << 32) |
+                                   (unsigned long long)(~(uint32_t)e[u])
+                             : 0ull;
         }
-        if (sub == 0 && local) atomicMax(&best[cp], local);
+#pragma unroll
+        for (int u = 0; u < kMstItems; ++u)
+            for (int32_t j = it[u].a + sub + kMstLanes; j < it[u].b; j += kMstLanes) {
+                const unsigned long long key = mst_key(j, it[u].cp, colval, eid, allow, comp);
+                it[u].best = key > it[u].best ? key : it[u].best;
+            }
+#pragma unroll
+        for (int u = 0; u < kMstItems; ++u) {
+            unsigned long long local = it[u].best;
+#pragma unroll
+            for (int o = 1; o < kMstLanes; o <<= 1) {
+                const unsigned long long q = __shfl_xor_sync(0xffffffffu, local, o);
+                local = q > local ? q : local;
+            }
+            if (sub == 0 && local) atomicMax(&best[it[u].cp], local);
+        }
     }
 }
 
@@ -108,17 +153,29 @@ __global__ void k_mst_break(int32_t n, const int32_t* __restrict__ comp, int32_t
     }
 }
 
-// One synchronous pointer-jumping step on a forest: out[r] = in[in[r]]; flag set while any
-// node still moves. Only component labels take part when comp != NULL.
-__global__ void k_jump_step(int32_t n, const int32_t* __restrict__ comp,
-                            const int32_t* __restrict__ in, int32_t* __restrict__ out,
-                            int* __restrict__ flag) {
+// Pointer jumping in place on a forest (roots point to themselves): every node climbs up to
+// kHops parents and stores the ancestor it reached; flag set while some node does not point at
+// a root yet. Other threads' stores are read as they land: every stored value is an ancestor of
+// its node, so any mix of old and new values is a valid forest with the same roots, and a node
+// whose ancestors were already shortened climbs further (the reach grows geometrically from one
+// launch to the next). Only component labels take part when comp != NULL.
+constexpr int kHops = 8;
+
+__global__ void k_jump_inplace(int32_t n, const int32_t* __restrict__ comp, int32_t* parent,
+                               int* __restrict__ flag) {
+    volatile int32_t* par = parent;
     for (int64_t r = (int64_t)blockIdx.x * kBlock + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * kBlock) {
         if (comp && comp[r] != r) continue;
-        const int32_t p = in[r], pp = in[p];
-        out[r] = pp;
-        if (pp != p) *flag = 1;
+        int32_t p = par[r];
+#pragma unroll 1
+        for (int h = 0; h < kHops; ++h) {
+            const int32_t pp = par[p];
+            if (pp == p) break;
+            p = pp;
+        }
+        par[r] = p;
+        if (par[p] != p) *flag = 1;
     }
 }
 
@@ -141,31 +198,25 @@ __global__ void k_count_u8(int64_t m, const uint8_t* __restrict__ mask,
 }  // namespace
 
 // Flatten a forest given by parent pointers (roots point to themselves) so that every entry
-// points at its root: synchronous doubling steps, convergence checked every fourth step.
+// points at its root: in-place jumping launches until no node moves (one launch when no path is
+// longer than kHops; the reach multiplies by about kHops per launch otherwise).
 sfg_status sfg_pointer_jump(sfg_ctx* ctx, int32_t n, const int32_t* comp, int32_t* parent) {
     if (n <= 0) return SFG_OK;
     Scratch s(ctx);
-    int32_t* tmp;
     int* flag;
-    SFG_TRY(s.get(&tmp, n));
     SFG_TRY(s.get(&flag, 1));
-    const int grid = sfg_grid(ctx, (const void*)k_jump_step, kBlock, 0, n);
-    int32_t* a = parent;
-    int32_t* b = tmp;
+    int* h = nullptr;
+    SFG_TRY(sfg_host_word(ctx, 1, &h));
+    const int grid = sfg_grid(ctx, (const void*)k_jump_inplace, kBlock, 0, n);
     for (int it = 0; it < 64; ++it) {
-        for (int k = 0; k < 4; ++k) {
-            if (k == 3) SFG_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-            k_jump_step<<<grid, kBlock, 0, ctx->stream>>>(n, comp, a, b, flag); ++ctx->launches;
-            std::swap(a, b);
-        }
-        SFG_LAUNCH_CHECK(ctx, "k_jump_step");
-        int h = 0;
-        SFG_CUDA(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        SFG_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+        sfg_tic(ctx, "jump");
+        k_jump_inplace<<<grid, kBlock, 0, ctx->stream>>>(n, comp, parent, flag); ++ctx->launches;
+        sfg_toc(ctx);
+        SFG_LAUNCH_CHECK(ctx, "k_jump_inplace");
+        SFG_CUDA(ctx, cudaMemcpyAsync(h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        if (!h) {
-            // after an even number of steps the result is back in `parent`
-            return SFG_OK;
-        }
+        if (!*h) return SFG_OK;
     }
     return sfg_fail(ctx, SFG_ETIMEOUT, "pointer jumping did not converge");
 }
@@ -206,6 +257,8 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
     SFG_TRY(s.get(&parent, n));
     SFG_TRY(s.get(&best, n));
     SFG_TRY(s.get(&flag, 1));
+    int* hflag = nullptr;  // pinned, written by the stream, read after a synchronisation
+    SFG_TRY(sfg_host_word(ctx, 0, &hflag));
     const int gn = sfg_grid(ctx, (const void*)k_mst_hook, kBlock, 0, n);
     SFG_TRY(sfg_heavy_prepare(ctx, g));
     const int gr = sfg_grid(ctx, (const void*)k_mst_rows<false>, kBlock, 0, (int64_t)n * kMstLanes);
@@ -216,7 +269,10 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
     SFG_LAUNCH_CHECK(ctx, "k_mst_init");
     // each round at least halves the number of components that still have outgoing edges
     for (int round = 0; round < 64; ++round) {
+        sfg_tic(ctx, "mst_reset");
         k_mst_reset<<<gn, kBlock, 0, ctx->stream>>>(n, best, flag); ++ctx->launches;
+        sfg_toc(ctx);
+        sfg_tic(ctx, "mst_rows");
         k_mst_rows<false><<<gr, kBlock, 0, ctx->stream>>>(n, g->row_ptr, nullptr, g->colval, g->eid,
                                                           allow, comp, best);
         ++ctx->launches;
@@ -225,21 +281,29 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
                                                              g->eid, allow, comp, best);
             ++ctx->launches;
         }
+        sfg_toc(ctx);
+        sfg_tic(ctx, "mst_hook");
         k_mst_hook<<<gn, kBlock, 0, ctx->stream>>>(n, g->eu, g->ev, comp, best, parent, mask, flag); ++ctx->launches;
+        sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_mst_round");
-        int hflag = 0;
-        SFG_CUDA(ctx, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        if (!hflag) {
+        // The round's "any hook" flag travels with the pointer-jumping readback: a round in
+        // which nothing hooks leaves every label its own parent, so break, jumping and relabel
+        // change nothing and the check can wait for the next synchronisation.
+        SFG_CUDA(ctx, cudaMemcpyAsync(hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        sfg_tic(ctx, "mst_break");
+        k_mst_break<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent); ++ctx->launches;
+        sfg_toc(ctx);
+        SFG_TRY(sfg_pointer_jump(ctx, n, comp, parent));
+        if (!*hflag) {
             if (n_tree) SFG_TRY(sfg_count_mask(ctx, mask, m, n_tree));
             if (comp_out)
                 SFG_CUDA(ctx, cudaMemcpyAsync(comp_out, comp, sizeof(int32_t) * n,
                                               cudaMemcpyDeviceToDevice, ctx->stream));
             return SFG_OK;
         }
-        k_mst_break<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent); ++ctx->launches;
-        SFG_TRY(sfg_pointer_jump(ctx, n, comp, parent));
+        sfg_tic(ctx, "mst_relabel");
         k_mst_relabel<<<gn, kBlock, 0, ctx->stream>>>(n, comp, parent); ++ctx->launches;
+        sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_mst_relabel");
     }
     return sfg_fail(ctx, SFG_ETIMEOUT, "spanning forest did not converge in 64 rounds");

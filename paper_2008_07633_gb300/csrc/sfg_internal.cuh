@@ -25,6 +25,7 @@ struct sfg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaMemPool_t pool = nullptr;          // the device's stream-ordered pool of the library
+    int* host_word = nullptr;              // pinned host ints for flags read after a sync
     int num_sms = 0;
     std::string last_error;
     bool timing = false;
@@ -113,6 +114,12 @@ struct Scratch {
             if (q == p) q = nullptr;
     }
 };
+
+// The context's pinned host ints (allocated on first use): a stream-ordered copy into one costs no
+// synchronisation, and the host reads it after the next one. Slots: 0 spanning-forest round
+// flag, 1 pointer-jumping flag.
+constexpr int kSfgHostWords = 4;
+sfg_status sfg_host_word(sfg_ctx* ctx, int slot, int** out);
 
 // Kernel timing (no-ops unless ctx->timing).
 void sfg_tic(sfg_ctx* ctx, const char* name);
