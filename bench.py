@@ -16,6 +16,11 @@ The timed region uses inputs larger than L2 (each vector block is 268 MB), so no
 Multi-GPU: the workload is one graph; N > 1 runs N independent replicas (weak scaling, no
 collective on the data path), one per rank, and the value is the sum over ranks.
 
+Also in the line, measured outside the timed region: `sparsify_forms` (sparsify time and kappa of
+each form against the plain two-level FP32 method), `mlp_forward` (learned-scorer inference on
+the tensor cores over 28M feature rows) and `small_graph_latency` (the 64 x 64 oracle-size grid,
+where launch and synchronisation costs dominate).
+
 --impl reference times the CPU oracle (single thread, FP64) on a bounded sample of the same
 workload: the first 32 of the 128 planes (524,288 nodes), same K, sweeps and budget fraction.
 """
@@ -151,6 +156,44 @@ def mlp_report(S, ctx, dev, rows, iters):
                          "frac": gbs / peak, "peak_kind": peak_kind,
                          "traffic": per_row * rows if per_row else None,
                          "bytes_per_row": MLP_BYTES_PER_ROW, "flop_per_row": MLP_FLOP_PER_ROW}}
+
+
+def small_graph_latency(S, ctx, dev, reps=20):
+    """Latency of the oracle-size configuration (64 x 64 grid, weights U[1,10), K = 8, 10 sweeps,
+    10% of the off-tree edges), which launch and synchronisation costs dominate: one flat
+    sfg_sparsify call and one filter+score step, wall clock per call after warm-up."""
+    import torch
+
+    from paper_2008_07633_gb300 import inputs as gen
+
+    n, u, v, w = gen.grid2d(64, 64, seed=1)
+    g = S.sfg_laplacian(ctx, n, *(torch.from_numpy(a).to(dev) for a in (u, v, w)))
+    tree, _ = S.sfg_spanning_tree(ctx, g)
+    p = S.sfg_graph_subgraph(ctx, g, tree)
+    off = torch.nonzero(tree == 0).flatten().to(torch.int32)
+    k = int(np.floor(0.1 * off.numel() + 0.5))
+
+    def wall(f):
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            f()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    def fs():
+        sc = S.sfg_filter_score(ctx, g, p, off, 8, 10, 0.7, 1001)
+        S.sfg_select_topk(ctx, sc, off, k)
+
+    out = {"workload": "grid2d-64x64, w=U[1,10), K=8, T=10, omega=0.7, fp32, 10% of off-tree edges",
+           "sparsify_flat_ms": wall(lambda: S.sfg_sparsify(ctx, g, K=8, steps=10, levels=0, omega=0.7,
+                                                           seed=1001, budget_frac=0.1, budget_unit=1)),
+           "filter_score_topk_ms": wall(fs)}
+    g.close()
+    p.close()
+    return out
 
 
 class ClockSampler:
@@ -443,6 +486,7 @@ def run_ours(args):
                 forms[name]["kappa_vs_reference"] = forms[name]["kappa"] / ref["kappa"]
                 forms[name]["speedup_vs_reference"] = ref["sparsify_ms"] / forms[name]["sparsify_ms"]
 
+    small = small_graph_latency(S, ctx, dev) if rank == 0 else None
     if rank != 0:
         return 0
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -466,6 +510,8 @@ def run_ours(args):
         out["sparsify_forms"] = forms
     if mlp:
         out["mlp_forward"] = mlp
+    if small:
+        out["small_graph_latency"] = small
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

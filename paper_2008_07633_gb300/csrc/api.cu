@@ -75,11 +75,19 @@ sfg_status sfg_check_dev(sfg_ctx* ctx, const void* p, const char* what) {
 }
 
 int sfg_grid(sfg_ctx* ctx, const void* kernel, int block, size_t smem, int64_t work_items) {
+    // resident CTAs per SM, asked once per (kernel, block, shared memory) and context
+    const auto key = std::make_tuple(kernel, block, smem);
+    auto it = ctx->occupancy.find(key);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
+    if (it != ctx->occupancy.end()) {
+        per_sm = it->second;
+    } else {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        ctx->occupancy.emplace(key, per_sm);
     }
     int64_t full = (int64_t)per_sm * ctx->num_sms;
     int64_t need = (work_items + block - 1) / block;

@@ -9,6 +9,7 @@
 #include <map>
 #include <cstdio>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/sfg.h"
@@ -33,6 +34,7 @@ struct sfg_ctx {
     std::vector<cudaEvent_t> event_pool;   // free events
     int64_t launches = 0;                  // kernels launched through this context
     std::map<uint32_t, int> tune;          // (K, dtype, degree bucket) -> sweep variant
+    std::map<std::tuple<const void*, int, size_t>, int> occupancy;  // resident CTAs per SM
     int64_t alloc_count = 0;               // for the allocation-failure injection hook
     int64_t fail_alloc_at = -1;            // SFG_FAULT_ALLOC=<n>: the n-th allocation fails
 };
