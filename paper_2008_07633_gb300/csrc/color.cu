@@ -98,19 +98,69 @@ __global__ void k_color_bounds(int32_t n, int32_t ncolors, const uint64_t* __res
 // (2 - omega) * total weight > 0 for omega < 2. Constants are the fixed points, and the iteration
 // converges to the constant (y . x0) / (y . 1); removing that y-weighted mean first keeps the
 // block free of a constant the final projection would otherwise cancel in FP32.
+// Eight lanes per row, striding over its entries, folded in a fixed order; rows longer than
+// SFG_HEAVY_ROW are left to k_gs_weights_heavy.
 __global__ void k_gs_weights(int32_t n, const int32_t* __restrict__ row_ptr,
                              const int2* __restrict__ colval, const int32_t* __restrict__ color,
                              double omega, double* __restrict__ y) {
-    for (int64_t p = blockIdx.x * (int64_t)256 + threadIdx.x; p < n; p += (int64_t)gridDim.x * 256) {
-        const int32_t cp = color[p];
-        double d = 0.0, later = 0.0;
-        for (int32_t j = row_ptr[p]; j < row_ptr[p + 1]; ++j) {
-            const int32_t q = colval[j].x;
-            const double w = (double)__int_as_float(colval[j].y);
-            d += w;
-            if (color[q] > cp || (color[q] == cp && q > (int32_t)p)) later += w;
+    constexpr int L = 8;
+    const int sub = threadIdx.x % L;
+    const int64_t g0 = ((int64_t)blockIdx.x * 256 + threadIdx.x) / L;
+    const int64_t ng = (int64_t)gridDim.x * 256 / L;
+    for (int64_t p0 = g0 - g0 % (32 / L); p0 < n; p0 += ng) {  // whole warps iterate together
+        const int64_t p = p0 + g0 % (32 / L);
+        int32_t a = 0, b = 0, cp = 0;
+        if (p < n) {
+            a = row_ptr[p], b = row_ptr[p + 1], cp = color[p];
+            if (b - a > SFG_HEAVY_ROW) b = a;
         }
-        y[p] = d - omega * later;
+        double d = 0.0, later = 0.0;
+        for (int32_t j = a + sub; j < b; j += L) {
+            const int2 cv = colval[j];
+            const double w = (double)__int_as_float(cv.y);
+            const int32_t cq = color[cv.x];
+            d += w;
+            if (cq > cp || (cq == cp && cv.x > (int32_t)p)) later += w;
+        }
+#pragma unroll
+        for (int o = 1; o < L; o <<= 1) {
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+            later += __shfl_xor_sync(0xffffffffu, later, o);
+        }
+        if (p < n && sub == 0 && row_ptr[p + 1] - a <= SFG_HEAVY_ROW) y[p] = d - omega * later;
+    }
+}
+
+// The same weights for the rows over SFG_HEAVY_ROW entries: one CTA of 256 threads per row, a
+// fixed-order tree over the threads' partial sums.
+__global__ void __launch_bounds__(256) k_gs_weights_heavy(int32_t nh, const int32_t* __restrict__ hrow,
+                                                          const int32_t* __restrict__ row_ptr,
+                                                          const int2* __restrict__ colval,
+                                                          const int32_t* __restrict__ color,
+                                                          double omega, double* __restrict__ y) {
+    __shared__ double sd[256], sl[256];
+    for (int32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int32_t p = hrow[h], cp = color[p];
+        double d = 0.0, later = 0.0;
+        for (int32_t j = row_ptr[p] + threadIdx.x; j < row_ptr[p + 1]; j += 256) {
+            const int2 cv = colval[j];
+            const double w = (double)__int_as_float(cv.y);
+            const int32_t cq = color[cv.x];
+            d += w;
+            if (cq > cp || (cq == cp && cv.x > p)) later += w;
+        }
+        sd[threadIdx.x] = d;
+        sl[threadIdx.x] = later;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) {
+                sd[threadIdx.x] += sd[threadIdx.x + o];
+                sl[threadIdx.x] += sl[threadIdx.x + o];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) y[p] = sd[0] - omega * sl[0];
+        __syncthreads();
     }
 }
 

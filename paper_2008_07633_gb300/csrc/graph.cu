@@ -203,7 +203,7 @@ void sfg_graph_free(sfg_graph* g) {
     if (!g) return;
     cudaStream_t s = g->stream;
     void* ptrs[] = {g->eu, g->ev, g->ew, g->row_ptr, g->colval, g->eid, g->deg, g->invdeg,
-                    g->gs_color, g->gs_order, g->hv_rows, g->hv_soff, g->hv_seg};
+                    g->gs_color, g->gs_order, g->hv_rows, g->hv_soff, g->hv_seg, g->gh_rows, g->gh_soff, g->gh_seg};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
     delete g;

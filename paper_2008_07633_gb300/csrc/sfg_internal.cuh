@@ -63,6 +63,15 @@ struct sfg_graph {
     int32_t* hv_rows = nullptr;
     int32_t* hv_soff = nullptr;
     int4* hv_seg = nullptr;
+    // The same rows grouped by Gauss-Seidel colour class (built on the first Gauss-Seidel
+    // smoothing): gh_rows sorted by (colour, id), row k's segments at gh_seg[gh_soff[k],
+    // gh_soff[k + 1]); colour c's rows at [gh_coff[c], gh_coff[c + 1]) and its segments at
+    // [gh_scoff[c], gh_scoff[c + 1]).
+    bool gh_ready = false;
+    int32_t* gh_rows = nullptr;
+    int32_t* gh_soff = nullptr;
+    int4* gh_seg = nullptr;
+    std::vector<int64_t> gh_coff, gh_scoff;
     cudaStream_t stream = nullptr;
 };
 
@@ -233,6 +242,9 @@ sfg_status sfg_gs_inherit(sfg_ctx* ctx, const sfg_graph* P, const sfg_graph* G);
 __global__ void k_gs_weights(int32_t n, const int32_t* __restrict__ row_ptr,
                              const int2* __restrict__ colval, const int32_t* __restrict__ color,
                              double omega, double* __restrict__ y);
+__global__ void k_gs_weights_heavy(int32_t nh, const int32_t* __restrict__ hrow,
+                                   const int32_t* __restrict__ row_ptr, const int2* __restrict__ colval,
+                                   const int32_t* __restrict__ color, double omega, double* __restrict__ y);
 sfg_status sfg_smooth_gs_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                               uint64_t seed, sfg_dtype storage, void* X_out);
 sfg_status sfg_pointer_jump(sfg_ctx* ctx, int32_t n, const int32_t* comp, int32_t* parent);

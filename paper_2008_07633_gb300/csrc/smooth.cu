@@ -448,7 +448,19 @@ __global__ void k_heavy_fill(int32_t n, const int32_t* __restrict__ row_ptr, con
     }
 }
 
-// Heavy-row lists of L (a cache of the graph, built on its first sweep).
+// For each heavy row h: (row, colour, first entry, end entry).
+__global__ void k_heavy_gather(int32_t nh, const int32_t* __restrict__ hrow, const int32_t* __restrict__ color,
+                               const int32_t* __restrict__ row_ptr, int32_t* __restrict__ out) {
+    const int32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= nh) return;
+    const int32_t r = hrow[h];
+    out[4 * h] = r;
+    out[4 * h + 1] = color[r];
+    out[4 * h + 2] = row_ptr[r];
+    out[4 * h + 3] = row_ptr[r + 1];
+}
+
+// Heavy-row lists of L (a cache of the graph, built with it).
 sfg_status heavy_prepare(sfg_ctx* ctx, const sfg_graph* Lc) {
     sfg_graph* L = const_cast<sfg_graph*>(Lc);
     if (L->hv_n >= 0) return SFG_OK;
@@ -516,7 +528,8 @@ sfg_status heavy_prepare(sfg_ctx* ctx, const sfg_graph* Lc) {
 template <typename T, int LPR>
 __global__ void __launch_bounds__(kBlock, 4)
     k_gs(int32_t cnt, const int32_t* __restrict__ rows, const int32_t* __restrict__ row_ptr,
-         const int2* __restrict__ colval, const float* __restrict__ coef, float a_self, T* X) {
+         const int2* __restrict__ colval, const float* __restrict__ coef, float a_self, T* X,
+         int32_t hmax) {
     constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR, C = Chunk<LPR>::C;
     const int lane = threadIdx.x & 31, grp = lane / LPR, sub = lane % LPR;
     const unsigned gm = group_mask<LPR>(lane);
@@ -533,6 +546,7 @@ __global__ void __launch_bounds__(kBlock, 4)
             lo = row_ptr[r];
             hi = row_ptr[r + 1];
             cf = coef[r];
+            if (hi - lo > hmax) hi = lo - 1;  // updated by the heavy-row kernels of this class
         }
         const int32_t row = __shfl_sync(0xffffffffu, r, grp);
         const int32_t a = __shfl_sync(0xffffffffu, lo, grp);
@@ -563,6 +577,117 @@ __global__ void __launch_bounds__(kBlock, 4)
             Vec<T>::store(xp, y);
         }
     }
+}
+
+// The heavy rows of one colour class, in place: row h adds its segments' partials (segment ids
+// soff[h] - base ... soff[h + 1] - base of this class's partial array) and applies the update of
+// k_gs. Rows of one class are not adjacent, so the partials read only rows of other classes.
+template <typename T, int LPR>
+__global__ void __launch_bounds__(kBlock) k_heavy_final_gs(int32_t nh, const int32_t* __restrict__ hrow,
+                                                           const int32_t* __restrict__ hsoff, int64_t base,
+                                                           const float* __restrict__ partial,
+                                                           const float* __restrict__ coef, float a_self,
+                                                           T* X) {
+    constexpr int E = Vec<T>::E, K = LPR * E;
+    const int sub = (threadIdx.x & 31) % LPR;
+    const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
+    const int64_t ng = (int64_t)gridDim.x * kBlock / LPR;
+    for (int64_t h = g0; h < nh; h += ng) {
+        const int32_t r = hrow[h];
+        float acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        for (int64_t sid = hsoff[h] - base; sid < hsoff[h + 1] - base; ++sid) {
+            const float* pr = partial + sid * K + sub * E;
+#pragma unroll
+            for (int e = 0; e < E; e += 4) {
+                const float4 q = *reinterpret_cast<const float4*>(pr + e);
+                acc[e] += q.x;
+                acc[e + 1] += q.y;
+                acc[e + 2] += q.z;
+                acc[e + 3] += q.w;
+            }
+        }
+        T* xp = X + (int64_t)r * K + sub * E;
+        float xs[E], y[E];
+        Vec<T>::load(xp, xs);
+        const float cp = coef[r];
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] = fmaf(cp, acc[e], a_self * xs[e]);
+        Vec<T>::store(xp, y);
+    }
+}
+
+// Heavy rows of L grouped by colour class (a cache of the graph, built on the first
+// Gauss-Seidel smoothing): rows sorted by (colour, id), their segments in that order, and the
+// per-colour offsets of both on the host.
+sfg_status gs_heavy_prepare(sfg_ctx* ctx, const sfg_graph* Lc) {
+    sfg_graph* L = const_cast<sfg_graph*>(Lc);
+    if (L->gh_ready) return SFG_OK;
+    const int ncol = (int)L->gs_off.size() - 1;
+    L->gh_coff.assign((size_t)std::max(ncol, 0) + 1, 0);
+    L->gh_scoff.assign((size_t)std::max(ncol, 0) + 1, 0);
+    const int32_t nh = std::max(L->hv_n, 0);
+    if (nh == 0 || ncol <= 0) {
+        L->gh_ready = true;
+        return SFG_OK;
+    }
+    std::vector<int32_t> h4((size_t)4 * nh);
+    {
+        Scratch s(ctx);
+        int32_t* dev4;
+        SFG_TRY(s.get(&dev4, (size_t)4 * nh));
+        k_heavy_gather<<<ceil_div_u(nh, kBlock), kBlock, 0, ctx->stream>>>(nh, L->hv_rows, L->gs_color,
+                                                                            L->row_ptr, dev4);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_heavy_gather");
+        SFG_CUDA(ctx, cudaMemcpyAsync(h4.data(), dev4, sizeof(int32_t) * 4 * nh, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    // stable by colour: hv_rows are in id order, so each class keeps increasing ids
+    std::vector<int32_t> ord(nh);
+    for (int32_t h = 0; h < nh; ++h) ord[h] = h;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int32_t a, int32_t b) { return h4[4 * a + 1] < h4[4 * b + 1]; });
+    std::vector<int32_t> grows(nh), gsoff((size_t)nh + 1);
+    std::vector<int64_t> ccount((size_t)ncol, 0), scount((size_t)ncol, 0);
+    std::vector<int4> gseg;
+    for (int32_t k = 0; k < nh; ++k) {
+        const int32_t h = ord[k], r = h4[4 * h], c = h4[4 * h + 1], lo = h4[4 * h + 2], hi = h4[4 * h + 3];
+        grows[k] = r;
+        gsoff[k] = (int32_t)gseg.size();
+        for (int32_t j = lo; j < hi; j += kSeg) gseg.push_back(make_int4(r, j, std::min(j + kSeg, hi), 0));
+        ccount[c] += 1;
+        scount[c] += (hi - lo + kSeg - 1) / kSeg;
+    }
+    gsoff[nh] = (int32_t)gseg.size();
+    for (int c = 0; c < ncol; ++c) {
+        L->gh_coff[c + 1] = L->gh_coff[c] + ccount[c];
+        L->gh_scoff[c + 1] = L->gh_scoff[c] + scount[c];
+    }
+    int32_t *drows = nullptr, *dsoff = nullptr;
+    int4* dseg = nullptr;
+    sfg_status st = sfg_alloc(ctx, (void**)&drows, sizeof(int32_t) * nh);
+    if (st == SFG_OK) st = sfg_alloc(ctx, (void**)&dsoff, sizeof(int32_t) * (nh + 1));
+    if (st == SFG_OK) st = sfg_alloc(ctx, (void**)&dseg, sizeof(int4) * gseg.size());
+    if (st != SFG_OK) {
+        for (void* q : {(void*)drows, (void*)dsoff, (void*)dseg})
+            if (q) sfg_free(ctx, q);
+        return st;
+    }
+    L->gh_rows = drows;
+    L->gh_soff = dsoff;
+    L->gh_seg = dseg;
+    SFG_CUDA(ctx, cudaMemcpyAsync(drows, grows.data(), sizeof(int32_t) * nh, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(dsoff, gsoff.data(), sizeof(int32_t) * (nh + 1), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(dseg, gseg.data(), sizeof(int4) * gseg.size(), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host arrays go out of scope
+    L->gh_ready = true;
+    return SFG_OK;
 }
 
 __global__ void k_fill(int k, float v, float* __restrict__ p) {
@@ -951,8 +1076,13 @@ struct Smoother {
         SFG_TRY(s.get(&yw, (size_t)n));
         k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
             n, L->invdeg, omega, coef);
-        k_gs_weights<<<sfg_grid(ctx, (const void*)k_gs_weights, kBlock, 0, n), kBlock, 0,
+        k_gs_weights<<<sfg_grid(ctx, (const void*)k_gs_weights, kBlock, 0, (int64_t)n * 8), kBlock, 0,
                        ctx->stream>>>(n, L->row_ptr, L->colval, L->gs_color, omega, yw);
+        if (L->hv_n > 0) {
+            k_gs_weights_heavy<<<std::min(L->hv_n, 4 * ctx->num_sms), 256, 0, ctx->stream>>>(
+                L->hv_n, L->hv_rows, L->row_ptr, L->colval, L->gs_color, omega, yw);
+            ++ctx->launches;
+        }
         k_init<T, LPR, true><<<grid, kBlock, 0, ctx->stream>>>(n, seed, yw, X_out, part);
         k_finalize<<<K, kBlock, 0, ctx->stream>>>(part, grid, K, n, 2, mu, scale);
         k_fill<<<1, 64, 0, ctx->stream>>>(K, 1.0f, scale);
@@ -962,14 +1092,34 @@ struct Smoother {
         SFG_LAUNCH_CHECK(ctx, "gs init");
         const float a_self = (float)(1.0 - omega);
         const int ncol = (int)L->gs_off.size() - 1;
+        SFG_TRY(gs_heavy_prepare(ctx, L));
+        const int32_t hmax = L->hv_n > 0 ? kHeavy : INT32_MAX;
+        int64_t max_seg = 0;
+        for (int c = 0; c < ncol; ++c) max_seg = std::max(max_seg, L->gh_scoff[c + 1] - L->gh_scoff[c]);
+        float* partial = nullptr;
+        if (max_seg > 0) SFG_TRY(s.get(&partial, (size_t)max_seg * K));
         for (int t = 0; t < steps; ++t)
             for (int c = 0; c < ncol; ++c) {
                 const int64_t c0 = L->gs_off[c], cnt = L->gs_off[c + 1] - c0;
                 if (cnt == 0) continue;
                 const int g = sfg_grid(ctx, (const void*)k_gs<T, LPR>, kBlock, 0, cnt * LPR);
                 k_gs<T, LPR><<<g, kBlock, 0, ctx->stream>>>((int32_t)cnt, L->gs_order + c0,
-                                                            L->row_ptr, L->colval, coef, a_self, buf);
+                                                            L->row_ptr, L->colval, coef, a_self, buf,
+                                                            hmax);
                 ++ctx->launches;
+                const int64_t nhc = L->gh_coff[c + 1] - L->gh_coff[c];
+                if (nhc > 0) {  // this class's rows over the tile limit
+                    const int64_t s0 = L->gh_scoff[c], nsc = L->gh_scoff[c + 1] - s0;
+                    const int gp = sfg_grid(ctx, (const void*)k_heavy_part<T, LPR>, kBlock, 0, nsc * LPR);
+                    k_heavy_part<T, LPR><<<gp, kBlock, 0, ctx->stream>>>(nsc, L->gh_seg + s0, L->colval,
+                                                                         buf, partial);
+                    const int gf = sfg_grid(ctx, (const void*)k_heavy_final_gs<T, LPR>, kBlock, 0,
+                                            nhc * LPR);
+                    k_heavy_final_gs<T, LPR><<<gf, kBlock, 0, ctx->stream>>>(
+                        (int32_t)nhc, L->gh_rows + L->gh_coff[c], L->gh_soff + L->gh_coff[c], s0, partial,
+                        coef, a_self, buf);
+                    ctx->launches += 2;
+                }
             }
         SFG_LAUNCH_CHECK(ctx, "k_gs");
         k_col_stats<T, LPR><<<gstat, kBlock, 0, ctx->stream>>>(n, buf, part);

@@ -171,6 +171,28 @@ def chung_lu(n, avg_deg=16.0, gamma=2.3, seed=5, i0=1.0, lcc=True):
     return n, a.astype(np.int32), b.astype(np.int32), w
 
 
+def hub_graph(n=6000, m=15000, seed=31, hubs=None):
+    """A sparse random graph (m endpoint pairs drawn uniformly, self-loops and repeats left to the
+    Laplacian) plus star hubs whose degrees are exact: by default about 2000, 700, 384 (three whole
+    128-entry segments), 257 and 256, one of them the last node. The random pairs avoid the hubs
+    and the star leaves are drawn from the other nodes without repetition. Weights U[1, 10)."""
+    rng = _rng(seed)
+    if hubs is None:
+        hubs = ((7, 2000), (n * 2 // 3, 700), (n - 1, 384), (100, 257), (200, 256))
+    hub_ids = [h for h, _ in hubs]
+    u0, v0 = rng.integers(0, n, m), rng.integers(0, n, m)
+    keep = ~(np.isin(u0, hub_ids) | np.isin(v0, hub_ids))
+    u, v = [u0[keep]], [v0[keep]]
+    others = np.setdiff1d(np.arange(n), hub_ids)
+    for hub, d in hubs:
+        u.append(np.full(d, hub))
+        v.append(rng.choice(others, d, replace=False))
+    u = np.concatenate(u).astype(np.int32)
+    v = np.concatenate(v).astype(np.int32)
+    w = rng.uniform(1.0, 10.0, u.size).astype(np.float32)
+    return n, u, v, w
+
+
 def path(n, weights="unit", seed=6):
     u = np.arange(n - 1)
     return n, u.astype(np.int32), (u + 1).astype(np.int32), _weights(_rng(seed), n - 1, weights)

@@ -252,6 +252,24 @@ def test_sparsify_batched_matches_per_graph(S, ctx):
             assert (extra_b & extra_s).sum() >= 0.9 * extra_s.sum()
 
 
+def test_sparsify_batched_hub_rows(S, ctx):
+    # rows over the sweep's tile limit inside the disjoint union: the union's heavy-row segments
+    # span several member graphs, and each member must still match its own sparsify call
+    specs = [gen.hub_graph(seed=31), gen.grid2d(30, 30, seed=4),
+             gen.hub_graph(n=4000, m=9000, seed=32, hubs=((0, 1500), (3999, 300), (1234, 600)))]
+    gs = [S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w)) for n, u, v, w in specs]
+    masks, counts = S.sfg_sparsify_batched(ctx, gs, K=32, steps=10, seed=5, budget_frac=0.05)
+    for g, mb, cnt in zip(gs, masks, counts):
+        single, ns = S.sfg_sparsify(ctx, g, K=32, steps=10, levels=0, seed=5, budget_frac=0.05,
+                                    budget_unit=0)
+        mb, single = host(mb), host(single)
+        tree = host(S.sfg_spanning_tree(ctx, g)[0])
+        assert np.all(mb[tree == 1] == 1)
+        assert cnt == ns == int(mb.sum())
+        extra_b, extra_s = (mb == 1) & (tree == 0), (single == 1) & (tree == 0)
+        assert (extra_b & extra_s).sum() >= 0.9 * extra_s.sum()
+
+
 def test_sparsify_batched_kappa_vs_oracle(S, ctx):
     specs = _batch_graphs()[:4]
     gs = [S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w)) for n, u, v, w in specs]

@@ -43,6 +43,9 @@ GRAPHS = {
     "chung_lu": lambda: gen.chung_lu(3000, seed=4),
     "disconnected": lambda: gen.random_graph(900, 1300, seed=5, connected=False),
     "power_grid": lambda: gen.power_grid(40, seed=6),
+    # rows over the sweep's 256-entry tile limit: per-colour segments and the in-place update
+    "hubs": lambda: gen.hub_graph(n=2500, m=6000, seed=33,
+                                  hubs=((3, 900), (2499, 300), (1000, 257), (1500, 256), (7, 520))),
 }
 
 
@@ -81,7 +84,7 @@ def test_gs_bf16_storage(S, ctx):
     assert colnorm_rel(x.astype(np.float64), ref) <= 2e-2
 
 
-@pytest.mark.parametrize("name", ["grid2d", "knn", "power_grid"])
+@pytest.mark.parametrize("name", ["grid2d", "knn", "power_grid", "hubs"])
 def test_flat_sparsify_with_gs_kappa(S, ctx, name):
     n, u, v, w = GRAPHS[name]()
     og = O.canonicalize(n, u, v, w)

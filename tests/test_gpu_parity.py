@@ -57,34 +57,13 @@ def score_err(s, ref):
     return (np.abs(s - ref) / np.maximum(np.abs(ref), max(floor, 1e-300))).max() if ref.size else 0.0
 
 
-def hub_graph(n=6000, m=15000, seed=31):
-    """A sparse random graph plus hub rows longer than the sweep's 256-entry tile limit: degrees
-    about 2000, 700, 384 (three whole 128-entry segments), 257 and 256 (just over and at the
-    limit), one of them the last node (ragged tail)."""
-    rng = np.random.default_rng(seed)
-    hubs = ((7, 2000), (4000, 700), (n - 1, 384), (100, 257), (200, 256))
-    hub_ids = [h for h, _ in hubs]
-    u0, v0 = rng.integers(0, n, m), rng.integers(0, n, m)
-    keep = ~(np.isin(u0, hub_ids) | np.isin(v0, hub_ids))   # hub degrees are exactly d
-    u, v = [u0[keep]], [v0[keep]]
-    others = np.setdiff1d(np.arange(n), hub_ids)
-    for hub, d in hubs:
-        nb = rng.choice(others, d, replace=False)
-        u.append(np.full(d, hub))
-        v.append(nb)
-    u = np.concatenate(u).astype(np.int32)
-    v = np.concatenate(v).astype(np.int32)
-    w = rng.uniform(1.0, 10.0, u.size).astype(np.float32)
-    return n, u, v, w
-
-
 GRAPHS = {
     "grid64": lambda: gen.grid2d(64, 64, seed=1),
     "multigraph": lambda: gen.random_graph(3001, 12000, seed=3, dup_frac=0.1, self_loops=17),
     "disconnected": lambda: gen.random_graph(2500, 3000, seed=4, connected=False),
     "intweights": lambda: gen.random_graph(1500, 6000, seed=5, lo=1, hi=4),
     "grid3d": lambda: gen.grid3d(17, seed=2),
-    "hubs": hub_graph,
+    "hubs": gen.hub_graph,
 }
 
 
@@ -191,7 +170,7 @@ def test_jacobi_same_input(S, ctx, K):
 @pytest.mark.parametrize("K", [4, 16, 32, 64])
 def test_jacobi_hub_rows(S, ctx, K):
     # rows over the tile limit go through the segment kernels; every lane-group width
-    n, u, v, w = hub_graph()
+    n, u, v, w = gen.hub_graph()
     g, og = make(S, ctx, n, u, v, w)
     x0 = gen.gaussian_block(n, K, seed=13)
     x = host(S.sfg_jacobi(ctx, g, dev(x0), 6, 0.7))
@@ -204,7 +183,7 @@ def test_jacobi_hub_rows(S, ctx, K):
 @pytest.mark.parametrize("K,dt", [(32, torch.float32), (64, torch.float32), (32, torch.bfloat16)])
 def test_smooth_hub_rows(S, ctx, K, dt):
     # first sweep (mean removal) and last sweep (projection statistics) through the heavy rows
-    g, og = make(S, ctx, *hub_graph())
+    g, og = make(S, ctx, *gen.hub_graph())
     x = host(S.sfg_smooth(ctx, g, K, 12, 0.7, seed=5, storage=dt).float())
     ref = O.smooth(og, K, 12, 0.7, seed=5)
     err = colwise_err(x.astype(np.float64), ref)
@@ -212,7 +191,7 @@ def test_smooth_hub_rows(S, ctx, K, dt):
 
 
 def test_filter_score_hub_rows(S, ctx):
-    n, u, v, w = hub_graph()
+    n, u, v, w = gen.hub_graph()
     g, og = make(S, ctx, n, u, v, w)
     tree, _ = S.sfg_spanning_tree(ctx, g)
     p = S.sfg_graph_subgraph(ctx, g, tree)
