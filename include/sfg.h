@@ -362,7 +362,7 @@ SFG_API sfg_status sfg_solve_pcg(sfg_ctx* ctx, const sfg_graph* G, const uint8_t
  * Learned edge proposals (an addition to the paper's method; the paper has no learned part).
  * A small network predicts each candidate edge's score after `steps` sweeps from features of a
  * much shorter embedding; its best guesses are rescored by the plain method, which therefore
- * stays both the fallback and the judge.
+ * stays both the fallback and the final arbiter of selection.
  * Features (16 per edge, FP32, row-major), for e = (p, q) with weighted degree d, neighbour count
  * deg and the projected-embedding distances s_G, s_P of sfg_score_edges (modes G and P) after
  * `steps` sweeps from `seed`: ln w, ln d_p + ln d_q, |ln d_p - ln d_q|, ln(s_G + 1e-30),

@@ -10,6 +10,10 @@
 // 16-byte gathers in flight. Every byte of the block is read and written once per sweep; the
 // neighbour gathers are served by L2 on meshes (the band of rows between p - D and p + D fits).
 //
+// Rows with more than 256 entries (the hubs of power-law graphs) would hold one lane group, and
+// with it its warp, for the whole sweep; they are swept apart in fixed 128-entry segments whose
+// partial sums are added in order (k_heavy_part, k_heavy_final), so results stay deterministic.
+//
 // The first sweep also removes the initial column means (A-form sweeps map a constant column to
 // itself, so J(X - 1 mu^T) = J(X) - 1 mu^T), and the last sweep accumulates the column sums and
 // sums of squares the projection needs, so neither costs an extra pass over the block.

@@ -14,6 +14,7 @@ import torch
 
 import oracle as O
 from paper_2008_07633_gb300 import inputs as gen
+from conftest import write_report
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -217,11 +218,9 @@ def test_precision_powergrid_bf16_vs_fp32(S, ctx):
         kap[name] = S.sfg_kappa(ctx, g, mask, steps=100)[0]
     print(f"C3 kappa: fp32 {kap['fp32']:.1f}, bf16 {kap['bf16']:.1f} "
           f"(ratio {kap['bf16'] / kap['fp32']:.4f})")
-    import os
-    if os.path.isdir("gpurun_out"):
-        open("gpurun_out/precision_report.txt", "w").write(
-            f"C3 2048^2 power grid, K=64, T=20: rows rel err fp32 {e32:.2e}, bf16 {e16:.2e}; "
-            f"kappa fp32 {kap['fp32']:.1f}, bf16 {kap['bf16']:.1f}\n")
+    write_report("precision_report.txt",
+                 f"C3 2048^2 power grid, K=64, T=20: rows rel err fp32 {e32:.2e}, bf16 {e16:.2e}; "
+                 f"kappa fp32 {kap['fp32']:.1f}, bf16 {kap['bf16']:.1f}")
     assert abs(kap["bf16"] - kap["fp32"]) <= 0.25 * kap["fp32"]
 
 

@@ -7,6 +7,7 @@ import torch
 
 import oracle as O
 from paper_2008_07633_gb300 import inputs as gen
+from conftest import write_report
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -137,5 +138,4 @@ def test_gs_versus_jacobi_report(S, ctx):
     report = "GS_REPORT 48^3 grid, K=32, 5% budget: " + "; ".join(rows)
     print("\n" + report)
     import os
-    if os.path.isdir("gpurun_out"):
-        open("gpurun_out/gs_report.txt", "w").write(report + "\n")
+    write_report("gs_report.txt", report)

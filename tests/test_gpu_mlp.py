@@ -13,6 +13,7 @@ import torch
 import oracle as O
 import oracle.mlp as M
 from paper_2008_07633_gb300 import inputs as gen
+from conftest import write_report
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -153,8 +154,8 @@ def test_learned_proposals_against_plain_method(S, ctx):
     """Train on method-generated data (8 seeded graphs), then on a held-out graph compare the
     learned form (2-step features -> network -> top proposals -> 20-step rescoring) with the plain
     method at several proposal fractions, and the network's ranking with ranking by the 2-step
-    score itself (the method without the network). The plain method judges: the learned form must
-    match its kappa within 5% at some proposal fraction <= 0.5; the curve is reported."""
+    score itself (the method without the network). The plain method is the yardstick: the learned
+    form must match its kappa within 5% at some proposal fraction <= 0.5; the curve is reported."""
     X, y = _train_set(S, ctx, range(201, 209))
     net = S.sfg_mlp_create(ctx, seed=11)
     loss = S.sfg_mlp_train(ctx, net, X, y, batch=8192, epochs=30, lr=2e-3)
@@ -187,7 +188,6 @@ def test_learned_proposals_against_plain_method(S, ctx):
               f"score: network {r_net:.3f}, 2-step score {r_two:.3f}; top-k recall in the "
               f"proposals (network, 2-step): {dict((f, (round(a, 3), round(b, 3))) for f, (a, b) in rec.items())}")
     print("\n" + report)
-    with open("gpurun_out/learned_report.txt" if __import__("os").path.isdir("gpurun_out") else "/dev/null", "w") as fh:
-        fh.write(report + "\n")
+    write_report("learned_report.txt", report)
     assert r_net > 0.5
     assert min(abs(c - kp) / kp for c in curve.values()) <= 0.05, report

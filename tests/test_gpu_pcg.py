@@ -7,6 +7,7 @@ import torch
 
 import oracle as O
 from paper_2008_07633_gb300 import inputs as gen
+from conftest import write_report
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -93,5 +94,4 @@ def test_pcg_report(S, ctx):
         rows.append(f"{label}: {it} iterations, {time.perf_counter() - t0:.2f} s, relres {rel:.1e}")
     report = f"PCG_REPORT 64^3 grid (n={n}, m={g.m}): " + "; ".join(rows)
     print("\n" + report)
-    if os.path.isdir("gpurun_out"):
-        open("gpurun_out/pcg_report.txt", "w").write(report + "\n")
+    write_report("pcg_report.txt", report)

@@ -12,6 +12,7 @@ import torch
 
 import oracle as O
 from paper_2008_07633_gb300 import inputs as gen
+from conftest import write_report
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -68,8 +69,7 @@ def test_kappa_versus_budget_thermal(S, ctx):
                 flat.append((k, info["lambda_min_exact"]))
     report = f"KAPPA_BUDGET thermal3d 48x48x24 (n={n}, m={g.m}), K=32, T=20: " + "; ".join(rows)
     print("\n" + report)
-    if os.path.isdir("gpurun_out"):
-        open("gpurun_out/kappa_budget_report.txt", "w").write(report + "\n")
+    write_report("kappa_budget_report.txt", report)
     for (k0, e0), (k1, e1) in zip(flat, flat[1:]):
         if e0 and e1:
             assert k1 <= k0 * (1 + 1e-6)
@@ -119,8 +119,7 @@ def test_batch_of_512_knn_graphs(S, ctx):
               f"{t_loop * 1e3:.1f} ms = {512 / t_loop:.0f} graphs/s ({t_loop / t_batch:.1f}x); "
               f"kappa over a 32-graph sample: median {np.median(ks):.1f}, max {ks.max():.1f}")
     print("\n" + report)
-    if os.path.isdir("gpurun_out"):
-        open("gpurun_out/batch_report.txt", "w").write(report + "\n")
+    write_report("batch_report.txt", report)
     assert sum(counts) == sum(int(m.sum().item()) for m in masks)
 
 
@@ -169,7 +168,6 @@ def test_learned_proposals_chung_lu_4m(S, ctx):
               f"{times['learned']:.1f} ms, kappa {kap['learned']:.1f} "
               f"(gap {kap['learned'] / kap['plain'] - 1:+.1%}, {times['plain'] / times['learned']:.2f}x)")
     print("\n" + report)
-    if os.path.isdir("gpurun_out"):
-        open("gpurun_out/learned_c5_report.txt", "w").write(report + "\n")
+    write_report("learned_c5_report.txt", report)
     assert int(masks["plain"].sum().item()) == int(masks["learned"].sum().item())
     assert np.isfinite(kap["learned"]) and np.isfinite(kap["plain"])
