@@ -98,36 +98,23 @@ __global__ void k_color_bounds(int32_t n, int32_t ncolors, const uint64_t* __res
 // (2 - omega) * total weight > 0 for omega < 2. Constants are the fixed points, and the iteration
 // converges to the constant (y . x0) / (y . 1); removing that y-weighted mean first keeps the
 // block free of a constant the final projection would otherwise cancel in FP32.
-// Eight lanes per row, striding over its entries, folded in a fixed order; rows longer than
-// SFG_HEAVY_ROW are left to k_gs_weights_heavy.
+// One thread per row (rows of meshes and k-NN graphs are short, and eight-lane groups measured
+// slower there); rows longer than SFG_HEAVY_ROW are left to k_gs_weights_heavy.
 __global__ void k_gs_weights(int32_t n, const int32_t* __restrict__ row_ptr,
                              const int2* __restrict__ colval, const int32_t* __restrict__ color,
                              double omega, double* __restrict__ y) {
-    constexpr int L = 8;
-    const int sub = threadIdx.x % L;
-    const int64_t g0 = ((int64_t)blockIdx.x * 256 + threadIdx.x) / L;
-    const int64_t ng = (int64_t)gridDim.x * 256 / L;
-    for (int64_t p0 = g0 - g0 % (32 / L); p0 < n; p0 += ng) {  // whole warps iterate together
-        const int64_t p = p0 + g0 % (32 / L);
-        int32_t a = 0, b = 0, cp = 0;
-        if (p < n) {
-            a = row_ptr[p], b = row_ptr[p + 1], cp = color[p];
-            if (b - a > SFG_HEAVY_ROW) b = a;
-        }
+    for (int64_t p = blockIdx.x * (int64_t)256 + threadIdx.x; p < n; p += (int64_t)gridDim.x * 256) {
+        const int32_t a = row_ptr[p], b = row_ptr[p + 1];
+        if (b - a > SFG_HEAVY_ROW) continue;
+        const int32_t cp = color[p];
         double d = 0.0, later = 0.0;
-        for (int32_t j = a + sub; j < b; j += L) {
-            const int2 cv = colval[j];
-            const double w = (double)__int_as_float(cv.y);
-            const int32_t cq = color[cv.x];
+        for (int32_t j = a; j < b; ++j) {
+            const int32_t q = colval[j].x;
+            const double w = (double)__int_as_float(colval[j].y);
             d += w;
-            if (cq > cp || (cq == cp && cv.x > (int32_t)p)) later += w;
+            if (color[q] > cp || (color[q] == cp && q > (int32_t)p)) later += w;
         }
-#pragma unroll
-        for (int o = 1; o < L; o <<= 1) {
-            d += __shfl_xor_sync(0xffffffffu, d, o);
-            later += __shfl_xor_sync(0xffffffffu, later, o);
-        }
-        if (p < n && sub == 0 && row_ptr[p + 1] - a <= SFG_HEAVY_ROW) y[p] = d - omega * later;
+        y[p] = d - omega * later;
     }
 }
 

@@ -1080,7 +1080,7 @@ struct Smoother {
         SFG_TRY(s.get(&yw, (size_t)n));
         k_coef<<<sfg_grid(ctx, (const void*)k_coef, kBlock, 0, n), kBlock, 0, ctx->stream>>>(
             n, L->invdeg, omega, coef);
-        k_gs_weights<<<sfg_grid(ctx, (const void*)k_gs_weights, kBlock, 0, (int64_t)n * 8), kBlock, 0,
+        k_gs_weights<<<sfg_grid(ctx, (const void*)k_gs_weights, kBlock, 0, n), kBlock, 0,
                        ctx->stream>>>(n, L->row_ptr, L->colval, L->gs_color, omega, yw);
         if (L->hv_n > 0) {
             k_gs_weights_heavy<<<std::min(L->hv_n, 4 * ctx->num_sms), 256, 0, ctx->stream>>>(
