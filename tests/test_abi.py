@@ -62,6 +62,8 @@ def test_host_side_status_without_gpu(lib):
         assert st != 0 and not h.value
     assert lib.sfg_ctx_create(None, 0, None) == 1
     assert lib.sfg_graph_info(None, None, None) == 1
+    assert lib.sfg_ctx_trim(None) == 1
+    lib.sfg_ctx_destroy(None)  # a no-op, not a crash
 
 
 def test_params_struct_layout():
