@@ -50,7 +50,7 @@ typedef enum {
 typedef enum { SFG_F32 = 0, SFG_BF16 = 1 } sfg_dtype;
 
 /* Edge score (Sec. 3.5, Eqs. formula_eig_perturb1_conclusion and ..._conclusion2, with the
- * eigenvector block U replaced by the smoothed block X; Algorithm 1 lines 13-14).
+ * eigenvector block U replaced by the smoothed block X; the scoring and selection steps of Algorithm 1).
  * s_G = w(p,q) * ||X_G^T e_pq||^2 and s_P = w(p,q) * ||X_P^T e_pq||^2, where X_G is the block
  * smoothed on L_G and X_P the block smoothed on L_P from the same seed.
  * RATIO: s_P / (s_G + eta); G: s_G (Algorithm 1 embeds G); P: s_P (Sec. 3.5 perturbs L_P). */
@@ -179,7 +179,7 @@ SFG_API sfg_status sfg_tune_set(sfg_ctx* ctx, int K, sfg_dtype storage, int degr
 SFG_API sfg_status sfg_tune_table(const sfg_ctx* ctx, char* buf, int64_t cap, int64_t* len_host);
 
 /* ---------------------------------------------------------------------------------------------
- * Spectrally critical edges (Sec. 3.5; Algorithm 1 lines 13-14)
+ * Spectrally critical edges (Sec. 3.5; scoring and selection steps of Algorithm 1)
  * ------------------------------------------------------------------------------------------- */
 
 /* scores_out[i] = score of canonical edge edge_ids[i] of LG (0 <= id < m), from the two n x K
@@ -189,8 +189,8 @@ SFG_API sfg_status sfg_score_edges(sfg_ctx* ctx, const sfg_graph* LG, const void
                            int K, sfg_dtype storage, const int32_t* edge_ids, int64_t ne,
                            sfg_score_mode mode, float* scores_out);
 
-/* The filter + score step of edge recovery (Sec. 3.5 with Sec. 3.2's embedding; Algorithm 1
- * lines 12-13) in one call: one seeded block (sfg_smooth step 1) is swept `steps` times on L_G
+/* The filter + score step of edge recovery (Sec. 3.5 with Sec. 3.2's embedding; the embedding and
+ * scoring steps of Algorithm 1) in one call: one seeded block (sfg_smooth step 1) is swept `steps` times on L_G
  * and on L_P (same node count), and the listed edges of LG are scored as sfg_score_edges would
  * score the two projected blocks. The projected blocks are not materialised: the projection's
  * mean removal cancels in X_p - X_q and its per-column scaling is applied inside the scorer, so
@@ -231,11 +231,12 @@ SFG_API sfg_status sfg_affinity(sfg_ctx* ctx, const sfg_graph* L, const float* X
  * their own pool, runtimes that must keep the device footprint fixed after start-up, code running
  * where cudaMalloc / cudaMallocAsync are not permitted). Same arguments and the same bit-exact
  * result as sfg_affinity, but its scratch (one FP64 row norm per node) is a fixed file-scope
- * device array of SFG_AFFINITY_NOALLOC_MAX_N entries (8 MiB) that every GPU loading the library
- * keeps until the process exits; the call itself allocates nothing.
+ * device array of SFG_AFFINITY_NOALLOC_MAX_N entries (8 MiB); the call itself allocates nothing.
+ *  - The array is taken once per device, when the first context on that device is created:
+ *    sfg_ctx_create looks up its device address (cudaGetSymbolAddress, with that device current),
+ *    which loads the module that holds it. From then on the device keeps the 8 MiB until the
+ *    process exits, and no sfg_affinity_noalloc call takes any memory.
  *  - n > SFG_AFFINITY_NOALLOC_MAX_N gives SFG_ECAPACITY (use sfg_affinity).
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *    that device current; make that first call before any stream capture.
  *  - Every call on a device shares the one array: calls whose work overlaps on the GPU (several
  *    streams or contexts at once) race on it. Serialise them, e.g. on one stream. */
 #define SFG_AFFINITY_NOALLOC_MAX_N (1 << 20)
@@ -252,7 +253,7 @@ SFG_API sfg_status sfg_affinity_noalloc(sfg_ctx* ctx, const sfg_graph* L, const 
 SFG_API sfg_status sfg_coarsen(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K, int32_t* agg_out,
                        int32_t* fine2coarse_out, int32_t* n_coarse_host, sfg_graph** coarse_out);
 
-/* Backward mapping of Sec. 3.4 / Algorithm 1 lines 5-11: pmask_f[e] over the fine graph's edges =
+/* Backward mapping of Sec. 3.4 (the backward-mapping step of Algorithm 1): pmask_f[e] over the fine graph's edges =
  * union of a maximum spanning tree of each aggregation set's induced subgraph, and, for every
  * coarse edge (I, J) with pmask_c set, the heaviest fine edge between S_I and S_J (ties: smallest
  * id). agg and fine2coarse as produced by sfg_coarsen. Synchronises. */

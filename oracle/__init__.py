@@ -89,6 +89,8 @@ def _declare(L):
                                     _i32p, _i32p, _f32p, _u8p, _u8p]),
         "orc_sparsify": (_int, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _int, _f64, _u64, _int,
                                 _f64, _int, _f64, _u8p]),
+        "orc_sparsify_levels": (_int, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _int, _f64, _u64,
+                                       _int, _f64, _int, _f64, _u8p, _i64p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -291,6 +293,17 @@ def sparsify(g: Graph, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=RATIO, b
     return mask, int(lf)
 
 
+def sparsify_levels(g: Graph, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=RATIO,
+                    budget_frac=0.1, budget_unit=1, eta=ETA):
+    """Algorithm 1 as `sparsify`, also returning per level l = 0..lf the row (N_l, M_l, c_l,
+    edges of P_l before the level's edge recovery, edges after it)."""
+    mask = np.empty(g.m, np.uint8)
+    stats = np.zeros((levels + 1, 5), np.int64)
+    lf = lib().orc_sparsify_levels(*g.args(), K, steps, levels, omega, seed, mode, budget_frac,
+                                   budget_unit, eta, _p(mask, _u8p), _p(stats, _i64p))
+    return mask, int(lf), stats[:lf + 1]
+
+
 # ------------------------------------------------------------------------------------------------
 # Sec. 2.2 relative condition number (measurement, FP64 dense; tiny and small graphs only)
 # ------------------------------------------------------------------------------------------------
@@ -410,7 +423,7 @@ def sparsify_to_kappa(g: Graph, kappa_target, batch_frac, max_rounds, K=8, steps
 
 def sparsify_flat(g: Graph, K=8, steps=10, omega=0.7, seed=0, mode=RATIO, budget_frac=0.1,
                   budget_unit=1, smoother="jacobi"):
-    """Flat Algorithm 1 (lines 13-14 on the spanning forest) with either smoother: P = maximum
+    """Flat Algorithm 1 (its scoring and selection steps on the spanning forest) with either smoother: P = maximum
     spanning forest; embed G and P from the same seed with weighted Jacobi or Gauss-Seidel (both in
     the order of G's colouring, which is proper for P), score the edges outside P, add the top
     round_half_up(beta * base) of them."""

@@ -277,7 +277,7 @@ void score_edges(const Graph& g, const std::vector<double>& xg, const std::vecto
     }
 }
 
-// Algorithm 1 "include top few edges with large distortion": the k largest by (score descending,
+// Algorithm 1, selection step (keep the candidates of largest distortion): the k largest by (score descending,
 // id ascending); returned ids ascending.
 void topk(const double* scores, const int32_t* ids, int64_t ne, int64_t k, int32_t* out) {
     std::vector<int64_t> order((size_t)ne);
@@ -390,7 +390,7 @@ struct Params {
 };
 
 // Add spectrally critical off-subgraph edges to the sparsifier mask of one level (Sec. 3.5,
-// Algorithm 1 "for each subgraph edge ... include top few edges with large distortion").
+// Algorithm 1, scoring and selection steps: score every edge outside the subgraph, add the top ones).
 // Budget (reading): the level's sparsifier ends with round(beta * base) edges beyond a spanning
 // forest (N_l - c_l edges); edges already present count; nothing is added if already over.
 int64_t recover_edges(const Graph& g, const std::vector<double>& xg,
@@ -671,15 +671,31 @@ void orc_backward_map(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv
 // multilevel method (coarsen levels times, sparsify the coarsest graph flat, map back and recover
 // edges at each finer level). Writes the sparsifier mask over G's canonical edges; returns the
 // number of levels actually built (coarsening stops early when a level has no edges left).
+// stats (may be NULL; 5 entries per level l = 0..levels): N_l, M_l, c_l (components of G_l), the
+// edges of P_l before edge recovery at that level (the mapped backbone; the spanning forest at the
+// coarsest level) and after it.
+int orc_sparsify_levels(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
+                        int K, int steps, int levels, double omega, uint64_t seed, int mode,
+                        double budget_frac, int budget_unit, double eta, uint8_t* mask_out,
+                        int64_t* stats);
+
 int orc_sparsify(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
                  int K, int steps, int levels, double omega, uint64_t seed, int mode,
                  double budget_frac, int budget_unit, double eta, uint8_t* mask_out) {
+    return orc_sparsify_levels(n, m, cu, cv, cw, K, steps, levels, omega, seed, mode, budget_frac,
+                               budget_unit, eta, mask_out, nullptr);
+}
+
+int orc_sparsify_levels(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
+                        int K, int steps, int levels, double omega, uint64_t seed, int mode,
+                        double budget_frac, int budget_unit, double eta, uint8_t* mask_out,
+                        int64_t* stats) {
     Params P{K, steps, levels, omega, seed, mode, budget_frac, budget_unit, eta};
     std::vector<Graph> G(1, make_graph(n, m, cu, cv, cw));
     std::vector<std::vector<int32_t>> AGG(1), F2C(1);
     std::vector<std::vector<double>> XG;
     int lf = 0;
-    for (int l = 1; l <= levels; ++l) {  // Algorithm 1 line 2: multilevel spectral reduction
+    for (int l = 1; l <= levels; ++l) {  // Algorithm 1, coarsening phase: multilevel spectral reduction
         const Graph& f = G.back();
         if (f.m() == 0) break;
         Laplacian L = build_laplacian(f);
@@ -698,13 +714,31 @@ int orc_sparsify(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, con
         G.push_back(std::move(c));
         lf = l;
     }
+    auto count = [](const std::vector<uint8_t>& mk) {
+        int64_t c = 0;
+        for (uint8_t b : mk) c += b;
+        return c;
+    };
+    auto record = [&](int l, int64_t before, int64_t after) {
+        if (!stats) return;
+        const Graph& gl = G[(size_t)l];
+        int64_t* s = stats + 5 * l;
+        s[0] = gl.n; s[1] = gl.m(); s[2] = count_components(gl); s[3] = before; s[4] = after;
+    };
     std::vector<uint8_t> pm((size_t)G[(size_t)lf].m());
-    sparsify_flat(G[(size_t)lf], P, level_seed(seed, lf), pm.data());
-    for (int l = lf; l >= 1; --l) {  // Algorithm 1 lines 4-17
+    {
+        kruskal_max(G[(size_t)lf], nullptr, pm.data());
+        const int64_t before = count(pm);
+        sparsify_flat(G[(size_t)lf], P, level_seed(seed, lf), pm.data());
+        record(lf, before, count(pm));
+    }
+    for (int l = lf; l >= 1; --l) {  // Algorithm 1, level loop
         const Graph& f = G[(size_t)l - 1];
         std::vector<uint8_t> pf((size_t)f.m());
         backward_map(f, AGG[(size_t)l].data(), F2C[(size_t)l].data(), G[(size_t)l], pm.data(), pf.data());
+        const int64_t before = count(pf);
         recover_edges(f, XG[(size_t)l - 1], P, level_seed(seed, l - 1), pf.data());
+        record(l - 1, before, count(pf));
         pm.swap(pf);
     }
     std::copy(pm.begin(), pm.end(), mask_out);

@@ -177,7 +177,7 @@ sfg_status sfg_ctx_create(sfg_ctx** out, int device, void* cuda_stream) {
         cudaGetLastError();
         return SFG_EINVAL;
     }
-    if (cudaSetDevice(device) != cudaSuccess) return SFG_ECUDA;
+    SfgDeviceGuard guard(device);
     sfg_ctx* c = new sfg_ctx();
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
@@ -189,12 +189,20 @@ sfg_status sfg_ctx_create(sfg_ctx** out, int device, void* cuda_stream) {
         delete c;
         return SFG_ECUDA;
     }
+    // The allocation-free entry points' file-scope scratch is resolved here, so that the module
+    // that holds it is loaded (and its memory taken) when a context is created, never inside
+    // one of those calls.
+    if (sfg_noalloc_prepare(c) != SFG_OK) {
+        delete c;
+        return SFG_ECUDA;
+    }
     *out = c;
     return SFG_OK;
 }
 
 sfg_status sfg_ctx_trim(sfg_ctx* ctx) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     SFG_CUDA(ctx, cudaMemPoolTrimTo(ctx->pool, 0));
     return SFG_OK;
@@ -202,6 +210,7 @@ sfg_status sfg_ctx_trim(sfg_ctx* ctx) {
 
 void sfg_ctx_destroy(sfg_ctx* ctx) {
     if (!ctx) return;
+    SFG_DEVICE(ctx);
     for (auto& r : ctx->timers) {
         cudaEventDestroy(r.start);
         cudaEventDestroy(r.stop);
@@ -221,6 +230,7 @@ void sfg_ctx_destroy(sfg_ctx* ctx) {
 
 sfg_status sfg_ctx_set_stream(sfg_ctx* ctx, void* cuda_stream) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     ctx->stream = (cudaStream_t)cuda_stream;
     return SFG_OK;
 }
@@ -229,6 +239,7 @@ const char* sfg_last_error(const sfg_ctx* ctx) { return ctx ? ctx->last_error.c_
 
 sfg_status sfg_ctx_timing(sfg_ctx* ctx, int on) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     for (auto& r : ctx->timers) {
         ctx->event_pool.push_back(r.start);
@@ -242,6 +253,7 @@ sfg_status sfg_ctx_timing(sfg_ctx* ctx, int on) {
 sfg_status sfg_ctx_kernel_time(sfg_ctx* ctx, const char* prefix, int64_t* launches_host,
                                double* ms_host) {
     if (!ctx || !prefix || !launches_host || !ms_host) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     int64_t n = 0;
     double total = 0.0;
@@ -260,6 +272,7 @@ sfg_status sfg_ctx_kernel_time(sfg_ctx* ctx, const char* prefix, int64_t* launch
 
 sfg_status sfg_ctx_launches(const sfg_ctx* ctx, int64_t* launches_host) {
     if (!ctx || !launches_host) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     *launches_host = ctx->launches;
     return SFG_OK;
 }
@@ -267,6 +280,7 @@ sfg_status sfg_ctx_launches(const sfg_ctx* ctx, int64_t* launches_host) {
 sfg_status sfg_autotune(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype storage,
                         int* variant_host, double* us_per_sweep_host) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!L) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
     if (!sfg_k_supported(K, storage))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", K, (int)storage);
@@ -275,6 +289,7 @@ sfg_status sfg_autotune(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype stora
 
 sfg_status sfg_tune_set(sfg_ctx* ctx, int K, sfg_dtype storage, int degree_bucket, int variant) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (degree_bucket < 0 || degree_bucket > 15 || variant < -1 || variant >= SFG_SWEEP_VARIANTS)
         return sfg_fail(ctx, SFG_EINVAL, "bad tuning entry");
     const uint32_t key = tune_key(K, storage, degree_bucket);
@@ -285,6 +300,7 @@ sfg_status sfg_tune_set(sfg_ctx* ctx, int K, sfg_dtype storage, int degree_bucke
 
 sfg_status sfg_tune_table(const sfg_ctx* ctx, char* buf, int64_t cap, int64_t* len_host) {
     if (!ctx || !len_host) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     static const int tpi[SFG_SWEEP_VARIANTS] = {1, 2, 4, 1, 2, 4};
     static const int minb[SFG_SWEEP_VARIANTS] = {4, 4, 4, 3, 3, 3};
     std::string j = "[";

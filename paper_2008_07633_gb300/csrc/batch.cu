@@ -142,6 +142,7 @@ extern "C" sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph
                                            const sfg_params* P, uint8_t* const* masks_out,
                                            int64_t* n_selected_host) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (ng < 1 || !gs || !P || !masks_out) return sfg_fail(ctx, SFG_EINVAL, "bad batch arguments");
     if (P->levels != 0)
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "the batched form is flat (levels = 0)");

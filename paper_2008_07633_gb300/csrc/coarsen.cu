@@ -1,5 +1,5 @@
 // One level of spectral coarsening (Sec. 3.2) and the sparsifier backward mapping (Sec. 3.4,
-// Algorithm 1 lines 5-11).
+// the backward-mapping step of Algorithm 1).
 //
 // Aggregation: every node hooks to the neighbour of smallest algebraic distance (ties: smaller
 // id). Under that strict choice the hook graph has no cycle longer than two, so breaking each
@@ -189,6 +189,7 @@ extern "C" {
 sfg_status sfg_coarsen(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K, int32_t* agg_out,
                        int32_t* fine2coarse_out, int32_t* n_coarse_host, sfg_graph** coarse_out) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!L || !coarse_out || !n_coarse_host) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
     if (K < 1) return sfg_fail(ctx, SFG_EINVAL, "K must be >= 1");
     SFG_TRY(sfg_check_dev(ctx, X, "X"));
@@ -204,6 +205,7 @@ sfg_status sfg_backward_map(sfg_ctx* ctx, const sfg_graph* fine, const int32_t* 
                             const int32_t* fine2coarse, const sfg_graph* coarse,
                             const uint8_t* pmask_c, uint8_t* pmask_f) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!fine || !coarse) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
     SFG_TRY(sfg_check_dev(ctx, agg, "agg"));
     if (fine->m > 0) {

@@ -276,6 +276,7 @@ sfg_status sfg_gs_inherit(sfg_ctx* ctx, const sfg_graph* Pc, const sfg_graph* G)
 extern "C" sfg_status sfg_coloring(sfg_ctx* ctx, const sfg_graph* L, int32_t* color_out,
                                    int32_t* ncolors_host) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!L) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
     if (L->n > 0 && color_out) SFG_TRY(sfg_check_dev(ctx, color_out, "color_out"));
     SFG_TRY(sfg_gs_prepare(ctx, L));

@@ -201,6 +201,7 @@ int grid_of(sfg_ctx* ctx, K kernel, int64_t work) {
 
 void sfg_graph_free(sfg_graph* g) {
     if (!g) return;
+    SfgDeviceGuard guard(g->device);
     cudaStream_t s = g->stream;
     void* ptrs[] = {g->eu, g->ev, g->ew, g->row_ptr, g->colval, g->eid, g->deg, g->invdeg,
                     g->gs_color, g->gs_order, g->hv_rows, g->hv_soff, g->hv_seg, g->gh_rows, g->gh_soff, g->gh_seg};
@@ -212,6 +213,7 @@ void sfg_graph_free(sfg_graph* g) {
 // Allocate the arrays of a graph with n nodes and m canonical edges.
 sfg_status sfg_alloc_graph(sfg_ctx* ctx, int32_t n, int64_t m, sfg_graph** out) {
     sfg_graph* g = new sfg_graph();
+    g->device = ctx->device;
     g->n = n;
     g->m = m;
     g->stream = ctx->stream;
@@ -389,6 +391,7 @@ extern "C" {
 sfg_status sfg_laplacian(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u, const int32_t* v,
                          const float* w, sfg_graph** out) {
     if (!ctx || !out) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     *out = nullptr;
     if (n < 1) return sfg_fail(ctx, SFG_EINVAL, "n must be >= 1 (got %d)", n);
     if (m < 0 || m >= (1ll << 31)) return sfg_fail(ctx, SFG_EINVAL, "m out of range");
@@ -397,7 +400,6 @@ sfg_status sfg_laplacian(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u, c
         SFG_TRY(sfg_check_dev(ctx, v, "v"));
         SFG_TRY(sfg_check_dev(ctx, w, "w"));
     }
-    SFG_CUDA(ctx, cudaSetDevice(ctx->device));
     return sfg_build_graph(ctx, n, m, u, v, w, true, out, nullptr);
 }
 
@@ -412,6 +414,7 @@ sfg_status sfg_graph_info(const sfg_graph* g, int32_t* n_host, int64_t* m_host) 
 
 sfg_status sfg_graph_edges(sfg_ctx* ctx, const sfg_graph* g, int32_t* u, int32_t* v, float* w) {
     if (!ctx || !g) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (g->m == 0) return SFG_OK;
     if (u) SFG_CUDA(ctx, cudaMemcpyAsync(u, g->eu, 4 * g->m, cudaMemcpyDeviceToDevice, ctx->stream));
     if (v) SFG_CUDA(ctx, cudaMemcpyAsync(v, g->ev, 4 * g->m, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -422,6 +425,7 @@ sfg_status sfg_graph_edges(sfg_ctx* ctx, const sfg_graph* g, int32_t* u, int32_t
 sfg_status sfg_graph_csr(sfg_ctx* ctx, const sfg_graph* g, int32_t* row_ptr, int32_t* col,
                          float* val, int32_t* eid, double* deg) {
     if (!ctx || !g) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     const int64_t nnz = 2 * g->m;
     if (row_ptr)
         SFG_CUDA(ctx, cudaMemcpyAsync(row_ptr, g->row_ptr, 4 * ((size_t)g->n + 1),
@@ -443,6 +447,7 @@ sfg_status sfg_graph_csr(sfg_ctx* ctx, const sfg_graph* g, int32_t* row_ptr, int
 sfg_status sfg_graph_subgraph(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* mask,
                               sfg_graph** out) {
     if (!ctx || !g || !out) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     *out = nullptr;
     if (g->m > 0) SFG_TRY(sfg_check_dev(ctx, mask, "mask"));
     return sfg_subgraph_impl(ctx, g, mask, out);

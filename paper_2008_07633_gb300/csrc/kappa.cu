@@ -1280,6 +1280,7 @@ extern "C" SFG_API sfg_status sfg_kappa(sfg_ctx* ctx, const sfg_graph* G, const 
                                         int steps, uint64_t seed, double* kappa_host,
                                         double* info_host) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!G || !kappa_host) return sfg_fail(ctx, SFG_EINVAL, "sfg_kappa: G and kappa_host are required");
     if (steps < 1) return sfg_fail(ctx, SFG_EINVAL, "sfg_kappa: steps must be >= 1");
     if (G->m > 0) SFG_TRY(sfg_check_dev(ctx, mask, "mask"));
@@ -1290,6 +1291,7 @@ extern "C" SFG_API sfg_status sfg_solve_pcg(sfg_ctx* ctx, const sfg_graph* G, co
                                             const double* b, double tol, int maxit, double* x,
                                             int* iters_host, double* relres_host) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!G) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
     if (!(tol > 0.0) || maxit < 0) return sfg_fail(ctx, SFG_EINVAL, "tol must be > 0 and maxit >= 0");
     if (G->n > 0) {

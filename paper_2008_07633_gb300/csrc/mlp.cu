@@ -593,6 +593,7 @@ struct sfg_mlp {
     uint2 *w1f = nullptr, *w2f = nullptr, *w2tf = nullptr;
     int64_t step = 0;
     cudaStream_t stream = nullptr;
+    int device = -1;
 };
 
 static Net net_of(const sfg_mlp* n) { return Net{n->theta, n->w1f, n->w2f, n->w2tf}; }
@@ -606,6 +607,7 @@ static sfg_status refresh_frags(sfg_ctx* ctx, sfg_mlp* n) {
 
 static void mlp_free(sfg_mlp* n) {
     if (!n) return;
+    SfgDeviceGuard guard(n->device);
     void* ptrs[] = {n->theta, n->m, n->v, n->grad, n->w1f, n->w2f, n->w2tf};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, n->stream);
@@ -639,9 +641,13 @@ sfg_status sfg_mlp_forward_impl(sfg_ctx* ctx, const sfg_mlp* net, const float* f
     SFG_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
     const int64_t ntiles = (ne + 127) / 128;
     // One wave of resident CTAs, counted from the kernel's registers and static shared memory
-    // (each CTA also holds 64 of the SM's 512 TMEM columns, so at most 8 fit).
-    static int per_sm = 0;
-    if (per_sm == 0) {
+    // (each CTA also holds 64 of the SM's 512 TMEM columns, so at most 8 fit); kept per context,
+    // i.e. per device.
+    const auto key = std::make_tuple((const void*)k_mlp_forward_tc, 128, (size_t)0);
+    int per_sm = 0;
+    if (auto it = ctx->occupancy.find(key); it != ctx->occupancy.end()) {
+        per_sm = it->second;
+    } else {
         SFG_CUDA(ctx, cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
                                            (int)cudaSharedmemCarveoutMaxShared));
         cudaFuncAttributes fa;
@@ -654,6 +660,7 @@ sfg_status sfg_mlp_forward_impl(sfg_ctx* ctx, const sfg_mlp* net, const float* f
         const int by_regs = regs_sm / (warp_regs * 4);
         const int by_smem = smem_sm / ((int)fa.sharedSizeBytes + smem_rsv);
         per_sm = std::max(1, std::min({by_regs, by_smem, 512 / 64}));
+        ctx->occupancy.emplace(key, per_sm);
     }
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * per_sm);
     sfg_tic(ctx, "mlp_forward");
@@ -689,9 +696,11 @@ extern "C" {
 
 sfg_status sfg_mlp_create(sfg_ctx* ctx, uint64_t seed, sfg_mlp** out) {
     if (!ctx || !out) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     *out = nullptr;
     sfg_mlp* n = new sfg_mlp();
     n->stream = ctx->stream;
+    n->device = ctx->device;
     sfg_status st = SFG_OK;
     auto A = [&](void** p, size_t bytes) {
         if (st == SFG_OK) st = sfg_alloc(ctx, p, bytes);
@@ -721,6 +730,7 @@ void sfg_mlp_destroy(sfg_mlp* net) { mlp_free(net); }
 
 sfg_status sfg_mlp_params(sfg_ctx* ctx, const sfg_mlp* net, float* theta_out) {
     if (!ctx || !net) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     SFG_TRY(sfg_check_dev(ctx, theta_out, "theta_out"));
     SFG_CUDA(ctx, cudaMemcpyAsync(theta_out, net->theta, 4 * NP, cudaMemcpyDeviceToDevice, ctx->stream));
     return SFG_OK;
@@ -728,6 +738,7 @@ sfg_status sfg_mlp_params(sfg_ctx* ctx, const sfg_mlp* net, float* theta_out) {
 
 sfg_status sfg_mlp_set_params(sfg_ctx* ctx, sfg_mlp* net, const float* theta) {
     if (!ctx || !net) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     SFG_TRY(sfg_check_dev(ctx, theta, "theta"));
     SFG_CUDA(ctx, cudaMemcpyAsync(net->theta, theta, 4 * NP, cudaMemcpyDeviceToDevice, ctx->stream));
     SFG_CUDA(ctx, cudaMemsetAsync(net->m, 0, 4 * NP, ctx->stream));
@@ -739,6 +750,7 @@ sfg_status sfg_mlp_set_params(sfg_ctx* ctx, sfg_mlp* net, const float* theta) {
 sfg_status sfg_mlp_forward(sfg_ctx* ctx, const sfg_mlp* net, const float* feats, int64_t ne,
                            float* out) {
     if (!ctx || !net) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (ne < 0) return sfg_fail(ctx, SFG_EINVAL, "ne must be >= 0");
     if (ne == 0) return SFG_OK;
     SFG_TRY(sfg_check_dev(ctx, feats, "feats"));
@@ -749,6 +761,7 @@ sfg_status sfg_mlp_forward(sfg_ctx* ctx, const sfg_mlp* net, const float* feats,
 sfg_status sfg_mlp_gradient(sfg_ctx* ctx, sfg_mlp* net, const float* feats, const float* targets,
                             int64_t ne, float* grad_out, double* loss_host) {
     if (!ctx || !net) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (ne < 1) return sfg_fail(ctx, SFG_EINVAL, "ne must be >= 1");
     SFG_TRY(sfg_check_dev(ctx, feats, "feats"));
     SFG_TRY(sfg_check_dev(ctx, targets, "targets"));
@@ -770,6 +783,7 @@ sfg_status sfg_mlp_gradient(sfg_ctx* ctx, sfg_mlp* net, const float* feats, cons
 sfg_status sfg_mlp_train(sfg_ctx* ctx, sfg_mlp* net, const float* feats, const float* targets,
                          int64_t ne, int64_t batch, int epochs, double lr, double* loss_host) {
     if (!ctx || !net) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (ne < 1 || batch < 1 || epochs < 0 || !(lr > 0.0))
         return sfg_fail(ctx, SFG_EINVAL, "bad training arguments");
     SFG_TRY(sfg_check_dev(ctx, feats, "feats"));
@@ -803,6 +817,7 @@ sfg_status sfg_edge_features(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph*
                              int steps, double omega, uint64_t seed, sfg_dtype storage,
                              const int32_t* edge_ids, int64_t ne, float* feats_out) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!LG || !LP || LG->n != LP->n) return sfg_fail(ctx, SFG_EINVAL, "bad graphs");
     if (!sfg_k_supported(K, storage))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", K, (int)storage);

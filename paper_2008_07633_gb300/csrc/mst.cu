@@ -312,6 +312,7 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
 extern "C" sfg_status sfg_spanning_tree(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow,
                                         uint8_t* mask_out, int64_t* n_tree_host) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!g) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
     if (g->m > 0) {
         SFG_TRY(sfg_check_dev(ctx, mask_out, "mask_out"));

@@ -54,21 +54,32 @@ __global__ void k_affinity_static(int64_t m, const int32_t* __restrict__ eu,
     }
 }
 
-// Device address of the scratch array on ctx's device, looked up once per device (with that
-// device current) and cached.
-sfg_status scratch_address(sfg_ctx* ctx, double** out) {
+}  // namespace
+
+// Device address of the scratch array on ctx's device, looked up once per device and cached.
+// sfg_ctx_create calls this with the context's device current. The lookup loads this file's
+// module on that device (modules load lazily), and with it the array: doing it at context
+// creation keeps every sfg_affinity_noalloc call free of that one-time allocation.
+sfg_status sfg_noalloc_prepare(sfg_ctx* ctx) {
     const int dev = ctx->device;
     if (dev < 0 || dev >= kMaxDevices)
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "device %d beyond the supported %d", dev, kMaxDevices);
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_dev[dev]) {
-        SFG_CUDA(ctx, cudaSetDevice(dev));
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_rownorm_scratch);
         if (e != cudaSuccess) return sfg_cuda_fail(ctx, e, "cudaGetSymbolAddress(scratch)");
         g_scratch_dev[dev] = static_cast<double*>(p);
     }
-    *out = g_scratch_dev[dev];
+    return SFG_OK;
+}
+
+namespace {
+
+sfg_status scratch_address(sfg_ctx* ctx, double** out) {
+    SFG_TRY(sfg_noalloc_prepare(ctx));
+    std::lock_guard<std::mutex> lock(g_mu);
+    *out = g_scratch_dev[ctx->device];
     return SFG_OK;
 }
 
@@ -77,6 +88,7 @@ sfg_status scratch_address(sfg_ctx* ctx, double** out) {
 extern "C" sfg_status sfg_affinity_noalloc(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
                                            double* delta_out) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!L) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
     if (K < 1) return sfg_fail(ctx, SFG_EINVAL, "K must be >= 1");
     if (L->n > SFG_AFFINITY_NOALLOC_MAX_N)

@@ -1,6 +1,6 @@
 // Edge scores. (1) Spectral-perturbation score of candidate edges (Sec. 3.5, Eqs.
 // formula_eig_perturb1_conclusion / formula_eig_perturb1_conclusion2 with U replaced by the
-// smoothed blocks; Algorithm 1 lines 13-14). (2) Algebraic-distance affinity that drives node
+// smoothed blocks; the scoring and selection steps of Algorithm 1). (2) Algebraic-distance affinity that drives node
 // aggregation in coarsening (Sec. 3.2).
 //
 // Scorer schedule: the same LPR-lane group per item as the smoother. For each listed edge the
@@ -14,6 +14,9 @@ namespace {
 constexpr int kBlock = 256;
 #ifndef SFG_SCORE_U
 #define SFG_SCORE_U 2
+#endif
+#ifndef SFG_SCORE_IMPL
+#define SFG_SCORE_IMPL 2
 #endif
 
 template <int LPR>
@@ -141,6 +144,127 @@ __global__ void __launch_bounds__(kBlock, U > 1 ? 4 : 1)
     }
 }
 
+// Scorer with fewer shuffles (same tiles and pipeline as k_score): every lane of a group loads
+// its edge's id, endpoints and weight itself (group-uniform addresses are served as one
+// broadcast), and the two squared distances are folded together: at the first step the even lane
+// of each pair keeps the G partial and the odd lane the P partial, so one shuffle per level moves
+// both, and one more hands the P sum to the group's first lane (LPR = 8: 4 shuffles per edge
+// instead of 9). The score formula is fixed at compile time (MODE).
+template <typename T, int LPR, int SCALED, int U, int MODE>
+__global__ void __launch_bounds__(kBlock, U > 1 ? 4 : 1)
+    k_score2(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
+             const int32_t* __restrict__ ev, const float* __restrict__ ew,
+             const T* __restrict__ XG, const T* __restrict__ XP, float eta,
+             const float* __restrict__ sg, const float* __restrict__ sp,
+             const int32_t* __restrict__ node_off, int ngraphs, float* __restrict__ out) {
+    constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR;
+    const int lane = threadIdx.x & 31, grp = lane / LPR, sub = lane % LPR;
+    const unsigned gm = group_mask<LPR>(lane);
+    const int64_t wid = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
+    const int64_t ntiles = (ne + GPW - 1) / GPW;
+    const int64_t ngroups = (ntiles + U - 1) / U;
+    const T* __restrict__ Xg = XG + sub * E;
+    const T* __restrict__ Xp = XP + sub * E;
+    __shared__ float s_scale[2][SCALED == 1 ? K : 1];
+    if (SCALED == 1) {
+        for (int k = threadIdx.x; k < K; k += kBlock) {
+            s_scale[0][k] = sg[k];
+            s_scale[1][k] = sp[k];
+        }
+        __syncthreads();
+    }
+    // this group's list entry in tile t (-1 past the end)
+    auto load_id = [&](int64_t t) -> int32_t {
+        const int64_t i = t * GPW + grp;
+        return i < ne ? ids[i] : -1;
+    };
+    struct Edge { int32_t p, q; float w; };
+    auto load_edge = [&](int32_t e) {
+        Edge d{0, 0, 0.f};
+        if (e >= 0) { d.p = eu[e]; d.q = ev[e]; d.w = ew[e]; }
+        return d;
+    };
+    int64_t g = wid;
+    Edge cur[U];
+    int32_t idn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        cur[u] = load_edge(load_id(g * U + u));
+        idn[u] = load_id((g + nw) * U + u);
+    }
+    for (; g < ngroups; g += nw) {
+        Edge nxt[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            nxt[u] = load_edge(idn[u]);
+            idn[u] = load_id((g + 2 * nw) * U + u);
+        }
+        uint4 rgp[U], rgq[U], rpp[U], rpq[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t p = cur[u].p, q = cur[u].q;
+            rgp[u] = Vec<T>::load_raw(Xg + p * K);
+            rgq[u] = Vec<T>::load_raw(Xg + q * K);
+            rpp[u] = Vec<T>::load_raw(Xp + p * K);
+            rpq[u] = Vec<T>::load_raw(Xp + q * K);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = (g * U + u) * GPW + grp;
+            const float* sc_g = nullptr;
+            const float* sc_p = nullptr;
+            if (SCALED == 1) {
+                sc_g = s_scale[0] + sub * E;
+                sc_p = s_scale[1] + sub * E;
+            } else if (SCALED == 2) {
+                const int32_t p = cur[u].p;
+                int lo = 0, hi = ngraphs;  // graph of row p
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (node_off[mid] <= p) lo = mid; else hi = mid;
+                }
+                sc_g = sg + (size_t)lo * K + sub * E;
+                sc_p = sp + (size_t)lo * K + sub * E;
+            }
+            float gp[E], gq[E], pp[E], pq[E];
+            Vec<T>::unpack(rgp[u], gp);
+            Vec<T>::unpack(rgq[u], gq);
+            Vec<T>::unpack(rpp[u], pp);
+            Vec<T>::unpack(rpq[u], pq);
+            float dg = 0.f, dp = 0.f;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                float a = gp[k] - gq[k], b = pp[k] - pq[k];
+                if (SCALED) {
+                    a *= sc_g[k];
+                    b *= sc_p[k];
+                }
+                dg = fmaf(a, a, dg);
+                dp = fmaf(b, b, dp);
+            }
+            if (LPR > 1) {
+                // even lanes: G partial sums, odd lanes: P partial sums
+                const bool odd = sub & 1;
+                const float give = odd ? dg : dp;
+                const float got = __shfl_xor_sync(gm, give, 1, LPR);
+                float v = (odd ? dp : dg) + got;
+#pragma unroll
+                for (int o = 2; o < LPR; o <<= 1) v += __shfl_xor_sync(gm, v, o, LPR);
+                const float other = __shfl_xor_sync(gm, v, 1, LPR);
+                dg = v;
+                dp = other;
+            }
+            if (sub == 0 && i < ne) {
+                const float w = cur[u].w;
+                const float sgv = w * dg, spv = w * dp;
+                out[i] = MODE == SFG_SCORE_G ? sgv : (MODE == SFG_SCORE_P ? spv : spv / (sgv + eta));
+            }
+            cur[u] = nxt[u];
+        }
+    }
+}
+
 // ||X_p||^2 in FP64, increasing k, no fused multiply-add.
 __global__ void k_rownorm(int32_t n, const float* __restrict__ X, int K, double* __restrict__ nn) {
     for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
@@ -177,15 +301,27 @@ sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const
     if (ne == 0) return SFG_OK;
     // the grid fills the SMs at the occupancy of the variant that is launched
     constexpr int U = SFG_SCORE_U;
-    const void* k = node_off ? (const void*)k_score<T, LPR, 2, U>
-                             : (sg ? (const void*)k_score<T, LPR, 1, U> : (const void*)k_score<T, LPR, 0, U>);
-    const int grid = sfg_grid(ctx, k, kBlock, 0, (ne + U - 1) / U * LPR);
-    sfg_tic(ctx, "score");
     const T *xg = (const T*)XG, *xp = (const T*)XP;
     float eta = 1e-30f;
+#if SFG_SCORE_IMPL == 2
+    const int sc = node_off ? 2 : (sg ? 1 : 0);
+    static void* const tab[3][3] = {
+        {(void*)k_score2<T, LPR, 0, U, 0>, (void*)k_score2<T, LPR, 0, U, 1>, (void*)k_score2<T, LPR, 0, U, 2>},
+        {(void*)k_score2<T, LPR, 1, U, 0>, (void*)k_score2<T, LPR, 1, U, 1>, (void*)k_score2<T, LPR, 1, U, 2>},
+        {(void*)k_score2<T, LPR, 2, U, 0>, (void*)k_score2<T, LPR, 2, U, 1>, (void*)k_score2<T, LPR, 2, U, 2>}};
+    const void* k = tab[sc][mode];
+    void* args[] = {(void*)&ne, (void*)&ids, (void*)&LG->eu, (void*)&LG->ev, (void*)&LG->ew,
+                    (void*)&xg, (void*)&xp, (void*)&eta, (void*)&sg, (void*)&sp,
+                    (void*)&node_off, (void*)&ngraphs, (void*)&out};
+#else
+    const void* k = node_off ? (const void*)k_score<T, LPR, 2, U>
+                             : (sg ? (const void*)k_score<T, LPR, 1, U> : (const void*)k_score<T, LPR, 0, U>);
     void* args[] = {(void*)&ne, (void*)&ids, (void*)&LG->eu, (void*)&LG->ev, (void*)&LG->ew,
                     (void*)&xg, (void*)&xp, (void*)&mode, (void*)&eta, (void*)&sg, (void*)&sp,
                     (void*)&node_off, (void*)&ngraphs, (void*)&out};
+#endif
+    const int grid = sfg_grid(ctx, k, kBlock, 0, (ne + U - 1) / U * LPR);
+    sfg_tic(ctx, "score");
     const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kBlock), args, 0, ctx->stream);
     if (e != cudaSuccess) return sfg_cuda_fail(ctx, e, "k_score");
     ++ctx->launches;
@@ -253,6 +389,7 @@ sfg_status sfg_score_edges(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, co
                            int K, sfg_dtype storage, const int32_t* edge_ids, int64_t ne,
                            sfg_score_mode mode, float* scores_out) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!LG) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
     if (ne < 0) return sfg_fail(ctx, SFG_EINVAL, "ne must be >= 0");
     if (mode != SFG_SCORE_RATIO && mode != SFG_SCORE_G && mode != SFG_SCORE_P)
@@ -273,6 +410,7 @@ sfg_status sfg_score_edges(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, co
 sfg_status sfg_affinity(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
                         double* delta_out) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!L) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
     if (K < 1) return sfg_fail(ctx, SFG_EINVAL, "K must be >= 1");
     SFG_TRY(sfg_check_dev(ctx, X, "X"));

@@ -1,4 +1,5 @@
-// Top-k selection (Algorithm 1 line 14: "include top few edges with large distortion").
+// Top-k selection (the selection step of Algorithm 1: the candidate edges of largest distortion
+// are added to the sparsifier).
 //
 // Each candidate becomes a unique 64-bit key: the order-preserving image of its FP32 score in the
 // high word and the complement of its id in the low word, so "larger key" is exactly the strict
@@ -139,6 +140,7 @@ sfg_status sfg_topk_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids, 
 extern "C" sfg_status sfg_select_topk(sfg_ctx* ctx, const float* scores, const int32_t* ids,
                                       int64_t ne, int64_t k, int32_t* ids_out) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (ne < 0 || k < 0 || k > ne)
         return sfg_fail(ctx, SFG_EINVAL, "need 0 <= k <= ne (k=%lld, ne=%lld)", (long long)k,
                         (long long)ne);

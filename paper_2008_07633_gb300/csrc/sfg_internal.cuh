@@ -40,6 +40,7 @@ struct sfg_ctx {
 };
 
 struct sfg_graph {
+    int device = -1;           // device that holds the arrays
     int32_t n = 0;
     int64_t m = 0;             // canonical edges
     int32_t* eu = nullptr;     // [m] canonical edge endpoints, eu < ev, sorted
@@ -74,6 +75,24 @@ struct sfg_graph {
     std::vector<int64_t> gh_coff, gh_scoff;
     cudaStream_t stream = nullptr;
 };
+
+// Every entry point runs with the context's device current and gives the caller's current device
+// back when it returns (cudaSetDevice only when the two differ).
+struct SfgDeviceGuard {
+    int prev = -1;
+    explicit SfgDeviceGuard(int device) {
+        int cur = -1;
+        if (device < 0 || cudaGetDevice(&cur) != cudaSuccess || cur == device) return;
+        if (cudaSetDevice(device) == cudaSuccess) prev = cur;
+        else cudaGetLastError();  // the entry point's own CUDA calls then report the failure
+    }
+    ~SfgDeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    SfgDeviceGuard(const SfgDeviceGuard&) = delete;
+    SfgDeviceGuard& operator=(const SfgDeviceGuard&) = delete;
+};
+#define SFG_DEVICE(ctx) SfgDeviceGuard sfg_device_guard_((ctx)->device)
 
 // ------------------------------------------------------------------------------------------------
 // Status helpers. Every API entry point returns through these so the text lands in ctx.
@@ -251,3 +270,6 @@ sfg_status sfg_pointer_jump(sfg_ctx* ctx, int32_t n, const int32_t* comp, int32_
 sfg_status sfg_count_mask(sfg_ctx* ctx, const uint8_t* mask, int64_t m, int64_t* count_host);
 sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
                              double* delta);
+// Resolve (once per device, with ctx's device current) the device address of the file-scope
+// scratch of the allocation-free entry points (noalloc.cu); called by sfg_ctx_create.
+sfg_status sfg_noalloc_prepare(sfg_ctx* ctx);

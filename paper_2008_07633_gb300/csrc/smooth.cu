@@ -23,6 +23,9 @@
 namespace {
 
 constexpr int kBlock = 256;
+#ifndef SFG_JACOBI_HINT
+#define SFG_JACOBI_HINT 0
+#endif
 // Tile-shape variants of the sweep, chosen per (K, storage, degree bucket) by sfg_autotune:
 // TPI = consecutive row tiles a warp sweeps before its grid-stride jump, MINB = resident CTAs per
 // SM requested from the compiler (4 caps registers at 64, 3 at 80).
@@ -152,12 +155,19 @@ __device__ __forceinline__ void gather_slots(const Chunk<LPR>& ch, int s0, unsig
                                              const T* __restrict__ Xl, float (&acc)[Vec<T>::E]) {
     constexpr int K = LPR * Vec<T>::E, C = Chunk<LPR>::C;
     uint4 xv[NS];
+#if SFG_JACOBI_HINT
+    const uint64_t keep = l2_policy_evict_last();
+#endif
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
         const int slot = s0 + u;
         if (slot < C) {
             const int c = __shfl_sync(gm, ch.cv[slot / LPR].x, slot % LPR, LPR);
+#if SFG_JACOBI_HINT
+            xv[u] = ld_hint(Xl + (int64_t)c * K, keep);
+#else
             xv[u] = Vec<T>::load_raw(Xl + (int64_t)c * K);
+#endif
         }
     }
 #pragma unroll
@@ -265,7 +275,11 @@ __global__ void __launch_bounds__(kBlock, MINB)
 #pragma unroll
                 for (int e = 0; e < E; ++e) y[e] = xs[e] - m[e];
             }
+#if SFG_JACOBI_HINT >= 2
+            st_hint(Y + (int64_t)r * K + sub * E, Vec<T>::pack(y), l2_policy_evict_first());
+#else
             Vec<T>::store(Y + (int64_t)r * K + sub * E, y);
+#endif
             if (STATS)
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
@@ -1445,6 +1459,7 @@ extern "C" {
 sfg_status sfg_smooth(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                       uint64_t seed, sfg_dtype storage, void* X_out) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     SFG_TRY(check_smooth_args(ctx, L, K, steps, omega, storage, X_out));
     return sfg_smooth_impl(ctx, L, K, steps, omega, seed, storage, X_out);
 }
@@ -1452,6 +1467,7 @@ sfg_status sfg_smooth(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double
 sfg_status sfg_smooth_gs(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                          uint64_t seed, sfg_dtype storage, void* X_out) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!(omega > 0.0 && omega < 2.0))
         return sfg_fail(ctx, SFG_EINVAL, "omega must be in (0, 2) for Gauss-Seidel");
     SFG_TRY(check_smooth_args(ctx, L, K, steps, 1.0, storage, X_out));
@@ -1461,6 +1477,7 @@ sfg_status sfg_smooth_gs(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, dou
 sfg_status sfg_jacobi(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                       sfg_dtype storage, void* X_inout) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     SFG_TRY(check_smooth_args(ctx, L, K, steps, omega, storage, X_inout));
     return dispatch(K, storage, [&](auto S) {
         using Sm = decltype(S);
@@ -1473,6 +1490,7 @@ sfg_status sfg_filter_score(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* 
                             const int32_t* edge_ids, int64_t ne, sfg_score_mode mode,
                             float* scores_out) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!LG || !LP) return sfg_fail(ctx, SFG_EINVAL, "graph is NULL");
     if (LG->n != LP->n) return sfg_fail(ctx, SFG_EINVAL, "L_G and L_P differ in node count");
     if (!sfg_k_supported(K, storage))

@@ -58,7 +58,7 @@ int64_t round_half_up(double x) { return (int64_t)std::floor(x + 0.5); }
 
 size_t elem_size(sfg_dtype dt) { return dt == SFG_BF16 ? 2 : 4; }
 
-// Edge recovery at one level (Sec. 3.5, Algorithm 1 lines 12-14). `mask` holds the current
+// Edge recovery at one level (Sec. 3.5; the embedding, scoring and selection steps of Algorithm 1). `mask` holds the current
 // sparsifier of g and receives the added edges. XG_f32: the FP32 embedding of g from this level's
 // seed (may be NULL: computed here in the requested storage).
 sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64_t seed,
@@ -149,6 +149,7 @@ struct Level {
 extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* P,
                                    uint8_t* mask_out, int64_t* n_selected_host) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!G || !P) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
     if (!sfg_k_supported(P->K, P->storage) || !sfg_k_supported(P->K, SFG_F32))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K,
@@ -169,7 +170,7 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
         }
     } cleanup{&lv};
 
-    // Algorithm 1 line 2: multilevel spectral graph reduction
+    // Algorithm 1, coarsening phase: multilevel spectral graph reduction
     for (int l = 1; l <= P->levels; ++l) {
         Level& f = lv.back();
         if (f.g->m == 0) break;
@@ -193,7 +194,7 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
     const int64_t comps = (int64_t)gc->n - n_tree;  // same at every level: aggregates are connected
     SFG_TRY(recover(ctx, gc, P, level_seed(P->seed, lf), n_tree, nullptr, pm));
 
-    // Algorithm 1 lines 4-17: map back and recover edges level by level
+    // Algorithm 1, level loop: map back and recover edges level by level
     for (int l = lf; l >= 1; --l) {
         const sfg_graph* f = lv[l - 1].g;
         uint8_t* pf;
@@ -213,6 +214,7 @@ extern "C" sfg_status sfg_sparsify_learned(sfg_ctx* ctx, const sfg_graph* G, con
                                            const sfg_mlp* net, int feat_steps, double propose_frac,
                                            uint8_t* mask_out, int64_t* n_selected_host) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!G || !P) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
     if (P->levels != 0) return sfg_fail(ctx, SFG_EUNSUPPORTED, "learned proposals are flat (levels = 0)");
     if (P->smoother != SFG_SMOOTH_JACOBI)
@@ -288,6 +290,7 @@ extern "C" sfg_status sfg_sparsify_to_kappa(sfg_ctx* ctx, const sfg_graph* G, co
                                             int64_t* n_selected_host, double* kappa_trace_host,
                                             int* rounds_host) {
     if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
     if (!G || !P) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
     if (!sfg_k_supported(P->K, P->storage))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K,

@@ -6,6 +6,30 @@
 template <typename T>
 struct Vec;
 
+// L2 eviction-priority hints (PTX createpolicy + L2::cache_hint): gathered neighbour rows ask to
+// be kept (evict_last), streamed output rows to go first (evict_first).
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ld_hint(const void* ptr, uint64_t pol) {
+    uint4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(ptr), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ void st_hint(void* ptr, uint4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;"
+                 :: "l"(ptr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol) : "memory");
+}
+
 template <>
 struct Vec<float> {
     static constexpr int E = 4;
@@ -15,6 +39,10 @@ struct Vec<float> {
     }
     __device__ __forceinline__ static void store(float* p, const float (&x)[4]) {
         *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+    __device__ __forceinline__ static uint4 pack(const float (&x)[4]) {
+        return make_uint4(__float_as_uint(x[0]), __float_as_uint(x[1]), __float_as_uint(x[2]),
+                          __float_as_uint(x[3]));
     }
     // value as stored (identity for FP32)
     __device__ __forceinline__ static float round(float x) { return x; }
@@ -47,14 +75,17 @@ struct Vec<__nv_bfloat16> {
             x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
         }
     }
-    __device__ __forceinline__ static void store(__nv_bfloat16* p, const float (&x)[8]) {
+    __device__ __forceinline__ static uint4 pack(const float (&x)[8]) {
         unsigned w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);  // RN-even
             w[i] = *reinterpret_cast<const unsigned*>(&h);
         }
-        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat16* p, const float (&x)[8]) {
+        *reinterpret_cast<uint4*>(p) = pack(x);
     }
     __device__ __forceinline__ static float round(float x) {
         return __bfloat162float(__float2bfloat16_rn(x));

@@ -405,6 +405,95 @@ def test_backward_map_tree_to_tree():
     assert O.kappa_dense(g, pf) < float("inf")          # spans G
 
 
+def _strict_before(g, a, b):
+    """Edge a precedes edge b in the strict order of the spanning-forest reading (weight
+    descending, then edge id ascending)."""
+    return g.w[a] > g.w[b] or (g.w[a] == g.w[b] and a < b)
+
+
+def _connected_by(n, edges, g, s, t):
+    adj = {}
+    for e in edges:
+        adj.setdefault(int(g.u[e]), []).append(int(g.v[e]))
+        adj.setdefault(int(g.v[e]), []).append(int(g.u[e]))
+    seen, stack = {s}, [s]
+    while stack:
+        a = stack.pop()
+        for b in adj.get(a, ()):
+            if b not in seen:
+                seen.add(b)
+                stack.append(b)
+    return t in seen
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_backward_map_choices_by_brute_force(seed):
+    """Sec. 3.4 backward mapping, checked edge by edge on small graphs with many weight ties and
+    arbitrary aggregation sets (not only connected ones):
+    - inter-cluster: for each selected coarse edge (I, J), exactly the fine edge between S_I and S_J
+      of largest weight, ties to the smallest id, found by scanning every fine edge;
+    - inner-cluster: an edge inside an aggregate is kept iff its endpoints are not already joined
+      inside that aggregate by edges that come before it in the strict order (the cycle property,
+      which characterises the unique maximum spanning forest of each induced subgraph)."""
+    rng = np.random.default_rng(seed)
+    n = 40
+    u = rng.integers(0, n, 160).astype(np.int32)
+    v = rng.integers(0, n, 160).astype(np.int32)
+    w = rng.integers(1, 4, 160).astype(np.float32)          # weights 1..3: many ties
+    g = G(n, u, v, w)
+    agg = rng.integers(0, 7, n).astype(np.int32)
+    nc = int(agg.max()) + 1
+    c, f2c = O.galerkin(g, agg, nc)
+    pc = (rng.random(c.m) < 0.6).astype(np.uint8)
+    pf = O.backward_map(g, agg, f2c, c, pc)
+    for ce in range(c.m):
+        I, J = int(c.u[ce]), int(c.v[ce])
+        between = [e for e in range(g.m)
+                   if {int(agg[g.u[e]]), int(agg[g.v[e]])} == {I, J}]
+        best = between[0]
+        for e in between[1:]:
+            if g.w[e] > g.w[best]:
+                best = e
+        chosen = [e for e in between if pf[e]]
+        assert chosen == ([best] if pc[ce] else []), (ce, chosen, best)
+    for e in range(g.m):
+        a = int(agg[g.u[e]])
+        if a != int(agg[g.v[e]]):
+            continue
+        earlier = [f for f in range(g.m) if f != e and int(agg[g.u[f]]) == a
+                   and int(agg[g.v[f]]) == a and _strict_before(g, f, e)]
+        keep = not _connected_by(n, earlier, g, int(g.u[e]), int(g.v[e]))
+        assert bool(pf[e]) == keep, e
+
+
+@pytest.mark.parametrize("levels,unit,beta", [(1, 0, 0.05), (2, 0, 0.05), (2, 1, 0.08),
+                                              (3, 0, 0.12)])
+def test_multilevel_budget_per_level(levels, unit, beta):
+    """Reading c13 of the per-level budget (the paper gives no split; only its figures mention
+    per-level edge counts): at every level l the sparsifier ends with round_half_up(beta * base_l)
+    edges beyond a spanning forest of G_l (N_l - c_l edges), base_l = N_l (unit 0) or the number of
+    off-forest edges of G_l (unit 1); edges mapped back from the coarser level count, and nothing
+    is added once they are already over. Every level's component count equals G's (aggregates are
+    connected), checked against a union-find count of G itself."""
+    g = G(*gen.grid2d(24, 24, seed=3, weights="logu", lo=-2, hi=2))
+    comps = O.components(g)
+    mask, lf, st = O.sparsify_levels(g, K=8, steps=10, levels=levels, seed=11, budget_frac=beta,
+                                     budget_unit=unit)
+    assert lf == levels and st.shape == (levels + 1, 5)
+    assert st[0, 0] == g.n and st[0, 1] == g.m and int(mask.sum()) == st[0, 4]
+    assert np.all(np.diff(st[:, 0]) < 0)                   # every level is coarser
+    for l in range(lf + 1):
+        nl, ml, cl, before, after = (int(x) for x in st[l])
+        assert cl == comps
+        forest = nl - cl
+        base = nl if unit == 0 else ml - forest
+        target = int(np.floor(beta * base + 0.5))
+        assert before >= forest
+        assert after == min(ml, max(before, forest + target)), (l, st[l], target)
+    # the coarsest level starts from its spanning forest alone
+    assert st[lf, 3] == st[lf, 0] - st[lf, 2]
+
+
 # ------------------------------------------------ Algorithm 1 ----------------------------------
 def test_sparsify_flat_properties():
     g = G(*gen.grid2d(32, 32, seed=1))
@@ -414,10 +503,23 @@ def test_sparsify_flat_properties():
     assert np.all(mask[tree == 1] == 1)
     off = g.m - (g.n - 1)
     assert int(mask.sum()) == g.n - 1 + int(np.floor(0.1 * off + 0.5))
-    assert O.kappa_dense(g, mask) < 0.2 * O.kappa_dense(g, tree)
     t = G(*gen.path(20, weights="uniform"))
     tm, _ = O.sparsify(t, K=4, steps=5)
     assert np.all(tm == 1)
+
+
+def test_sparsify_flat_cuts_kappa_against_the_tree():
+    # Sec. 3.5 / Table 2: the recovered off-tree edges bring kappa(L_G, L_P) far below the
+    # spanning tree's. 48 x 48 grid, 10% of the off-tree edges: the tree's kappa is 3,257 and
+    # the sparsifier's 111-172 over three seeds of the random vectors (0.034-0.053 of the tree's),
+    # against the bar of 0.1. (On a 32 x 32 grid the ratio is 0.09-0.12 across seeds: the tree's
+    # kappa grows faster with the graph than the sparsifier's, so the bar sits on the larger grid.)
+    g = G(*gen.grid2d(48, 48, seed=1))
+    tree = O.mst(g)
+    kt = O.kappa_dense(g, tree)
+    for s in (1, 5):
+        mask, _ = O.sparsify(g, K=8, steps=10, levels=0, budget_frac=0.1, budget_unit=1, seed=s)
+        assert O.kappa_dense(g, mask) < 0.1 * kt
 
 
 def test_sparsify_beats_random_choice():

@@ -49,3 +49,34 @@ def test_affinity_noalloc_rejects_graphs_beyond_its_scratch():
     with pytest.raises(S.SfgError) as e:
         S.sfg_affinity_noalloc(ctx, g, X)
     assert e.value.status == 5 and "exceeds" in str(e.value)
+
+
+def test_affinity_noalloc_needs_no_allocation():
+    # A context whose first pool allocation fails (SFG_FAULT_ALLOC=1, read when the context is
+    # created): the allocating entry point reports SFG_ENOMEM, the allocation-free one still
+    # gives the same result, call after call. Graph and block come from another context.
+    import os
+
+    import paper_2008_07633_gb300.sfg as S
+
+    ctx = S.sfg_ctx_create(0)
+    g = _graph(S, ctx, *gen.grid2d(48, 48, seed=2))
+    X = torch.from_numpy(gen.gaussian_block(g.n, 16, seed=8)).to(DEV)
+    ref = S.sfg_affinity(ctx, g, X)
+    old = os.environ.get("SFG_FAULT_ALLOC")
+    os.environ["SFG_FAULT_ALLOC"] = "1"
+    try:
+        starved = S.sfg_ctx_create(0)
+    finally:
+        if old is None:
+            del os.environ["SFG_FAULT_ALLOC"]
+        else:
+            os.environ["SFG_FAULT_ALLOC"] = old
+    with pytest.raises(S.SfgError) as e:
+        S.sfg_affinity(starved, g, X)
+    assert e.value.status == 2
+    for _ in range(2):
+        out = torch.empty(g.m, dtype=torch.float64, device=DEV)
+        got = S.sfg_affinity_noalloc(starved, g, X, out=out)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref)
