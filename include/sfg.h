@@ -58,6 +58,7 @@ typedef enum { SFG_SCORE_RATIO = 0, SFG_SCORE_G = 1, SFG_SCORE_P = 2 } sfg_score
 
 typedef struct sfg_ctx sfg_ctx;     /* device, borrowed stream, last error, optional timers */
 typedef struct sfg_graph sfg_graph; /* canonical edge list + CSR Laplacian, device-resident */
+typedef struct sfg_hierarchy sfg_hierarchy; /* levels of one multilevel run (see sfg_sparsify) */
 
 /* ---------------------------------------------------------------------------------------------
  * Context
@@ -243,15 +244,16 @@ SFG_API sfg_status sfg_affinity(sfg_ctx* ctx, const sfg_graph* L, const float* X
 SFG_API sfg_status sfg_affinity_noalloc(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
                                         double* delta_out);
 
-/* One coarsening level from an FP32 block X (n x K): affinities as sfg_affinity; each node hooks
- * to the neighbour with the smallest delta (ties: smaller id); aggregation sets S_i are the
- * connected components of the hooks, numbered by increasing smallest member (agg_out[p] = i for
- * p in S_i); the coarse Laplacian is the Galerkin product H^-T L H^+ of Sec. 3.2, i.e. the
- * canonical form of the list (agg[u], agg[v], w) taken in fine edge-id order.
- * fine2coarse_out[e] (may be NULL) = coarse edge id of fine edge e, or -1 inside an aggregate.
- * Synchronises. */
-SFG_API sfg_status sfg_coarsen(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K, int32_t* agg_out,
-                       int32_t* fine2coarse_out, int32_t* n_coarse_host, sfg_graph** coarse_out);
+/* One coarsening level from a block X (n x K, row-major, `storage` SFG_F32 or SFG_BF16; entries
+ * widened exactly to FP64): affinities as sfg_affinity; each node hooks to the neighbour with the
+ * smallest delta (ties: smaller id); aggregation sets S_i are the connected components of the
+ * hooks, numbered by increasing smallest member (agg_out[p] = i for p in S_i); the coarse
+ * Laplacian is the Galerkin product H^-T L H^+ of Sec. 3.2, i.e. the canonical form of the list
+ * (agg[u], agg[v], w) taken in fine edge-id order. fine2coarse_out[e] (may be NULL) = coarse edge
+ * id of fine edge e, or -1 inside an aggregate. Synchronises. */
+SFG_API sfg_status sfg_coarsen(sfg_ctx* ctx, const sfg_graph* L, const void* X, int K,
+                               sfg_dtype storage, int32_t* agg_out, int32_t* fine2coarse_out,
+                               int32_t* n_coarse_host, sfg_graph** coarse_out);
 
 /* Backward mapping of Sec. 3.4 (the backward-mapping step of Algorithm 1): pmask_f[e] over the fine graph's edges =
  * union of a maximum spanning tree of each aggregation set's induced subgraph, and, for every
@@ -281,15 +283,37 @@ typedef struct {
 /* Smoothers of sfg_params.smoother. */
 enum { SFG_SMOOTH_JACOBI = 0, SFG_SMOOTH_GAUSS_SEIDEL = 1 };
 
-/* mask_out[e] (m entries) = 1 for the edges of the sparsifier P of G. Flat: maximum spanning
- * forest, then the top-scored off-tree edges. Multilevel: coarsen `levels` times (stopping early
- * if a level has no edges left), sparsify the coarsest graph flat, then at each finer level map
- * the sparsifier back (sfg_backward_map), re-embed, score the edges outside it and add the top
- * ones. Budget at each level: the level's sparsifier gets round-half-up(beta * base) edges beyond
- * N_l - c_l (c_l = number of components), counting edges already mapped; none are added if it is
- * already over. n_selected_host (may be NULL) receives the number of edges in P. Synchronises. */
+/* The method (Algorithm 1 of Sec. 3.6: graph in; sparsifier and coarsening hierarchy out).
+ * mask_out[e] (m entries) = 1 for the edges of the sparsifier P of G. Flat: maximum spanning
+ * forest, then the top-scored off-tree edges. Multilevel: coarsen `levels` times (each level
+ * embedded in params->storage; stopping early if a level has no edges left), sparsify the
+ * coarsest graph flat, then at each finer level map the sparsifier back (sfg_backward_map),
+ * re-embed, score the edges outside it and add the top ones. Budget at each level: the level's
+ * sparsifier gets round-half-up(beta * base) edges beyond N_l - c_l (c_l = number of components),
+ * counting edges already mapped; none are added if it is already over. n_selected_host (may be
+ * NULL) receives the number of edges in P. hier_out (may be NULL) receives the hierarchy: the
+ * graphs G_1 .. G_lf, the maps H_1 .. H_lf and every level's sparsifier P_0 .. P_lf (a flat run
+ * has lf = 0), to be released with sfg_hierarchy_destroy. Synchronises. */
 SFG_API sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* params,
-                        uint8_t* mask_out, int64_t* n_selected_host);
+                                uint8_t* mask_out, int64_t* n_selected_host,
+                                sfg_hierarchy** hier_out);
+
+/* Accessors of a hierarchy (Algorithm 1's [G_1 .. G_lf; H_1 .. H_lf] plus the sparsifier P_l of
+ * every level). Level 0 is the input graph G (borrowed: it must outlive the hierarchy), levels
+ * 1 .. lf are the coarse graphs, owned by the hierarchy (do not destroy them).
+ * sfg_hierarchy_levels: lf. sfg_hierarchy_graph: G_level. sfg_hierarchy_map (level 1 .. lf): the
+ * map H_level from G_{level-1} to G_level as agg_out (N_{level-1} entries, node -> aggregate) and
+ * fine2coarse_out (M_{level-1} entries, edge -> coarse edge or -1), each may be NULL, as
+ * sfg_coarsen writes them. sfg_hierarchy_mask (level 0 .. lf): P_level over G_level's canonical
+ * edges (M_level entries; level 0 equals sfg_sparsify's mask_out). Out-of-range levels give
+ * SFG_EINVAL. The copies are stream-ordered on ctx's stream. */
+SFG_API sfg_status sfg_hierarchy_levels(const sfg_hierarchy* h, int* levels_host);
+SFG_API sfg_status sfg_hierarchy_graph(const sfg_hierarchy* h, int level, const sfg_graph** out);
+SFG_API sfg_status sfg_hierarchy_map(sfg_ctx* ctx, const sfg_hierarchy* h, int level,
+                                     int32_t* agg_out, int32_t* fine2coarse_out);
+SFG_API sfg_status sfg_hierarchy_mask(sfg_ctx* ctx, const sfg_hierarchy* h, int level,
+                                      uint8_t* mask_out);
+SFG_API void sfg_hierarchy_destroy(sfg_hierarchy* h);
 
 /* Batched flat method: sparsify ng independent graphs in one set of launches (their disjoint
  * union is processed as one graph; the seeded blocks, projection statistics, budgets and top-k
@@ -301,6 +325,28 @@ SFG_API sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_para
 SFG_API sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* const* gs,
                                         const sfg_params* params, uint8_t* const* masks_out,
                                         int64_t* n_selected_host);
+
+/* Batch plan: the same batched flat method split into a plan, built once per set of graphs, and
+ * runs of it. sfg_batch_create (synchronises) joins the graphs, computes every graph's spanning
+ * forest, candidate edges and budget (params as sfg_sparsify_batched; params->seed is not used)
+ * and, when autotune != 0, times the sweep's tile shapes on the union of the graphs and on the
+ * union of their forests and records the fastest in ctx's table (sfg_autotune). sfg_batch_run
+ * writes the sparsifiers of all graphs for one seed into mask_out (a device buffer of
+ * edges_host entries: graph g's m_g edges at [edge_offsets_host[g], edge_offsets_host[g + 1]),
+ * in its canonical order); it only queues kernels and stream-ordered allocations on ctx's stream
+ * (no host synchronisation), so it can be captured in a CUDA graph and replayed, and every run
+ * with the same seed gives the same bits. sfg_batch_info gives the number of graphs, the total
+ * edge count, the ng + 1 edge offsets and every graph's sparsifier size (each pointer may be
+ * NULL). The plan holds its own copy of the graphs: they may be destroyed after
+ * sfg_batch_create. */
+typedef struct sfg_batch sfg_batch;
+SFG_API sfg_status sfg_batch_create(sfg_ctx* ctx, int ng, const sfg_graph* const* gs,
+                                    const sfg_params* params, int autotune, sfg_batch** out);
+SFG_API sfg_status sfg_batch_info(const sfg_batch* b, int* ng_host, int64_t* edges_host,
+                                  int64_t* edge_offsets_host, int64_t* n_selected_host);
+SFG_API sfg_status sfg_batch_run(sfg_ctx* ctx, const sfg_batch* b, uint64_t seed,
+                                 uint8_t* mask_out);
+SFG_API void sfg_batch_destroy(sfg_batch* b);
 
 /* Relative condition number kappa(L_G, L_P) of Sec. 2.2 (Eq. eqn:ineq), the paper's measure of
  * sparsifier quality, for P = the edges of G with mask[e] != 0 (m entries, device). kappa =

@@ -90,7 +90,7 @@ def _declare(L):
         "orc_sparsify": (_int, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _int, _f64, _u64, _int,
                                 _f64, _int, _f64, _u8p]),
         "orc_sparsify_levels": (_int, [_i32, _i64, _i32p, _i32p, _f32p, _int, _int, _int, _f64, _u64,
-                                       _int, _f64, _int, _f64, _u8p, _i64p]),
+                                       _int, _f64, _int, _f64, _u8p, _i64p, _i32p, _u8p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -294,14 +294,24 @@ def sparsify(g: Graph, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=RATIO, b
 
 
 def sparsify_levels(g: Graph, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=RATIO,
-                    budget_frac=0.1, budget_unit=1, eta=ETA):
+                    budget_frac=0.1, budget_unit=1, eta=ETA, hierarchy=False):
     """Algorithm 1 as `sparsify`, also returning per level l = 0..lf the row (N_l, M_l, c_l,
-    edges of P_l before the level's edge recovery, edges after it)."""
+    edges of P_l before the level's edge recovery, edges after it). hierarchy=True adds the maps
+    agg[l-1] (G_{l-1} -> G_l, l = 1..lf) and the level sparsifiers pmask[l] (over G_l's edges)."""
     mask = np.empty(g.m, np.uint8)
     stats = np.zeros((levels + 1, 5), np.int64)
+    agg = np.zeros((max(levels, 1), g.n), np.int32)
+    pm = np.zeros((levels + 1, max(g.m, 1)), np.uint8)
     lf = lib().orc_sparsify_levels(*g.args(), K, steps, levels, omega, seed, mode, budget_frac,
-                                   budget_unit, eta, _p(mask, _u8p), _p(stats, _i64p))
-    return mask, int(lf), stats[:lf + 1]
+                                   budget_unit, eta, _p(mask, _u8p), _p(stats, _i64p),
+                                   _p(agg, _i32p) if hierarchy else None,
+                                   _p(pm, _u8p) if hierarchy else None)
+    st = stats[:lf + 1]
+    if not hierarchy:
+        return mask, int(lf), st
+    aggs = [agg[l - 1][:st[l - 1, 0]].copy() for l in range(1, lf + 1)]
+    pms = [pm[l][:st[l, 1]].copy() for l in range(lf + 1)]
+    return mask, int(lf), st, aggs, pms
 
 
 # ------------------------------------------------------------------------------------------------

@@ -116,3 +116,50 @@ def adam_step(theta, m, v, g, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** step)
     vh = v / (1 - b2 ** step)
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ------------------------------------------------------------------------------------------------
+# The learned-proposal form of the flat method (not in the paper; the plain method of Sec. 3.5 is
+# its rescoring step and final arbiter), in the order the library specifies: spanning forest;
+# features of every off-forest edge from a feat_steps embedding; network predictions; the top
+# max(k, round_half_up(propose_frac * candidates)) predictions become proposals; the proposals are
+# rescored by the plain filter (steps sweeps on L_G and L_P from the same seed); the top k
+# rescored proposals join the forest.
+# ------------------------------------------------------------------------------------------------
+def learned_stages(og, theta, K, steps, feat_steps, propose_frac, seed, budget_frac=0.05,
+                   budget_unit=0, omega=0.7, mode=0):
+    """Returns a dict with every intermediate of the learned form: forest mask, candidate ids,
+    budget k, feature rows, predictions, proposal ids (ascending), their rescored scores, the
+    selected ids (ascending) and the final mask."""
+    import oracle as O
+
+    forest = O.mst(og).astype(np.uint8)
+    cand = np.nonzero(forest == 0)[0].astype(np.int32)
+    n_tree = int(forest.sum())
+    base = og.n if budget_unit == 0 else cand.size
+    k = min(max(int(np.floor(budget_frac * base + 0.5)), 0), cand.size)
+    out = {"forest": forest, "cand": cand, "k": k}
+    if k == 0:
+        out["mask"] = forest
+        return out
+    nprop = min(max(int(np.floor(propose_frac * cand.size + 0.5)), k), cand.size)
+    pg = og.subgraph(forest)
+    xg_f = O.smooth(og, K, feat_steps, omega, seed)
+    xp_f = O.smooth(pg, K, feat_steps, omega, seed)
+    sg = O.score_edges(og, xg_f, xp_f, cand, O.G_ONLY)
+    sp = O.score_edges(og, xg_f, xp_f, cand, O.P_ONLY)
+    _, _, _, _, deg = O.laplacian_csr(og)
+    cnt = np.bincount(np.concatenate([og.u, og.v]), minlength=og.n)
+    feats = features(og.w[cand], deg[og.u[cand]], deg[og.v[cand]], cnt[og.u[cand]],
+                     cnt[og.v[cand]], sg, sp)
+    pred, _ = forward(theta, feats)
+    prop = O.topk(pred, cand, nprop)
+    xg = O.smooth(og, K, steps, omega, seed)
+    xp = O.smooth(pg, K, steps, omega, seed)
+    scores = O.score_edges(og, xg, xp, prop, mode)
+    sel = O.topk(scores, prop, k)
+    mask = forest.copy()
+    mask[sel] = 1
+    out.update(nprop=nprop, feats=feats, pred=pred, prop=prop, scores=scores, sel=sel, mask=mask,
+               xg=xg, xp=xp)
+    return out

@@ -673,11 +673,13 @@ void orc_backward_map(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv
 // number of levels actually built (coarsening stops early when a level has no edges left).
 // stats (may be NULL; 5 entries per level l = 0..levels): N_l, M_l, c_l (components of G_l), the
 // edges of P_l before edge recovery at that level (the mapped backbone; the spanning forest at the
-// coarsest level) and after it.
+// coarsest level) and after it. agg_all (may be NULL; levels blocks of n entries): block l - 1
+// holds the map from G_{l-1} to G_l. pmask_all (may be NULL; levels + 1 blocks of m entries):
+// block l holds P_l over G_l's edges.
 int orc_sparsify_levels(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
                         int K, int steps, int levels, double omega, uint64_t seed, int mode,
                         double budget_frac, int budget_unit, double eta, uint8_t* mask_out,
-                        int64_t* stats);
+                        int64_t* stats, int32_t* agg_all = nullptr, uint8_t* pmask_all = nullptr);
 
 int orc_sparsify(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
                  int K, int steps, int levels, double omega, uint64_t seed, int mode,
@@ -689,7 +691,7 @@ int orc_sparsify(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, con
 int orc_sparsify_levels(int32_t n, int64_t m, const int32_t* cu, const int32_t* cv, const float* cw,
                         int K, int steps, int levels, double omega, uint64_t seed, int mode,
                         double budget_frac, int budget_unit, double eta, uint8_t* mask_out,
-                        int64_t* stats) {
+                        int64_t* stats, int32_t* agg_all, uint8_t* pmask_all) {
     Params P{K, steps, levels, omega, seed, mode, budget_frac, budget_unit, eta};
     std::vector<Graph> G(1, make_graph(n, m, cu, cv, cw));
     std::vector<std::vector<int32_t>> AGG(1), F2C(1);
@@ -719,7 +721,10 @@ int orc_sparsify_levels(int32_t n, int64_t m, const int32_t* cu, const int32_t* 
         for (uint8_t b : mk) c += b;
         return c;
     };
-    auto record = [&](int l, int64_t before, int64_t after) {
+    auto record = [&](int l, int64_t before, int64_t after, const std::vector<uint8_t>& mk) {
+        if (pmask_all) std::copy(mk.begin(), mk.end(), pmask_all + (size_t)l * (size_t)m);
+        if (agg_all && l >= 1)
+            std::copy(AGG[(size_t)l].begin(), AGG[(size_t)l].end(), agg_all + (size_t)(l - 1) * (size_t)n);
         if (!stats) return;
         const Graph& gl = G[(size_t)l];
         int64_t* s = stats + 5 * l;
@@ -730,7 +735,7 @@ int orc_sparsify_levels(int32_t n, int64_t m, const int32_t* cu, const int32_t* 
         kruskal_max(G[(size_t)lf], nullptr, pm.data());
         const int64_t before = count(pm);
         sparsify_flat(G[(size_t)lf], P, level_seed(seed, lf), pm.data());
-        record(lf, before, count(pm));
+        record(lf, before, count(pm), pm);
     }
     for (int l = lf; l >= 1; --l) {  // Algorithm 1, level loop
         const Graph& f = G[(size_t)l - 1];
@@ -738,7 +743,7 @@ int orc_sparsify_levels(int32_t n, int64_t m, const int32_t* cu, const int32_t* 
         backward_map(f, AGG[(size_t)l].data(), F2C[(size_t)l].data(), G[(size_t)l], pm.data(), pf.data());
         const int64_t before = count(pf);
         recover_edges(f, XG[(size_t)l - 1], P, level_seed(seed, l - 1), pf.data());
-        record(l - 1, before, count(pf));
+        record(l - 1, before, count(pf), pf);
         pm.swap(pf);
     }
     std::copy(pm.begin(), pm.end(), mask_out);

@@ -1,6 +1,14 @@
 // Batched flat sparsification of many graphs (a batch of independent problems, e.g. many small
 // k-NN graphs) in one set of launches.
 //
+// The work splits in two. A batch plan (sfg_batch_create) holds everything that depends on the
+// graphs only: their disjoint union, the spanning forests, the union of the forests' Laplacians,
+// the candidate edges and per-graph budgets, the heavy-row segments and the sweep's tuned tile
+// shape. Running the plan (sfg_batch_run) does the numeric part -- seeded blocks, sweeps on both
+// unions, per-graph projection statistics, scores, per-graph top-k, masks -- as kernel launches and
+// stream-ordered allocations only: no host synchronisation, so a run can be captured in a CUDA
+// graph and replayed.
+//
 // The graphs are joined into their disjoint union U: canonical lists, CSR rows and entries are
 // concatenated with node and edge offsets, which keeps every list sorted and every edge id order,
 // so no sort is needed. On U, one Boruvka run gives every graph's spanning forest (the forests of
@@ -138,12 +146,38 @@ struct GraphGuard {
 
 }  // namespace
 
-extern "C" sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* const* gs,
-                                           const sfg_params* P, uint8_t* const* masks_out,
-                                           int64_t* n_selected_host) {
-    if (!ctx) return SFG_EINVAL;
-    SFG_DEVICE(ctx);
-    if (ng < 1 || !gs || !P || !masks_out) return sfg_fail(ctx, SFG_EINVAL, "bad batch arguments");
+
+// The plan of one batch (see the file comment). Device arrays are owned here.
+struct sfg_batch {
+    int device = -1;
+    int ng = 0;
+    sfg_params P{};
+    int32_t n = 0;
+    int64_t m = 0, ncand = 0, k_total = 0;
+    sfg_graph* U = nullptr;    // union of the graphs
+    sfg_graph* PU = nullptr;   // union of their spanning forests
+    int32_t* d_noff = nullptr; // ng + 1 node offsets
+    int64_t* d_eoff = nullptr; // ng + 1 edge offsets
+    int64_t* d_coff = nullptr; // ng + 1 candidate offsets
+    int64_t* d_k = nullptr;    // per-graph budgets
+    uint8_t* forest = nullptr; // m: the forests' edges
+    int32_t* cand = nullptr;   // ncand candidate ids (union edge ids, ascending, grouped by graph)
+    std::vector<int64_t> eoff, counts;
+    cudaStream_t stream = nullptr;
+};
+
+static void batch_free(sfg_batch* b) {
+    if (!b) return;
+    SfgDeviceGuard guard(b->device);
+    sfg_graph_free(b->U);
+    sfg_graph_free(b->PU);
+    void* ptrs[] = {b->d_noff, b->d_eoff, b->d_coff, b->d_k, b->forest, b->cand};
+    for (void* p : ptrs)
+        if (p) cudaFreeAsync(p, b->stream);
+    delete b;
+}
+
+static sfg_status check_batch_params(sfg_ctx* ctx, const sfg_params* P) {
     if (P->levels != 0)
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "the batched form is flat (levels = 0)");
     if (!sfg_k_supported(P->K, P->storage))
@@ -154,13 +188,23 @@ extern "C" sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph
         (P->budget_unit != 0 && P->budget_unit != 1) ||
         (P->mode != SFG_SCORE_RATIO && P->mode != SFG_SCORE_G && P->mode != SFG_SCORE_P))
         return sfg_fail(ctx, SFG_EINVAL, "invalid sfg_params");
+    return SFG_OK;
+}
+
+static sfg_status batch_build(sfg_ctx* ctx, int ng, const sfg_graph* const* gs, const sfg_params* P,
+                              int autotune, sfg_batch* b) {
+    b->device = ctx->device;
+    b->stream = ctx->stream;
+    b->ng = ng;
+    b->P = *P;
     std::vector<int32_t> noff(ng + 1, 0);
-    std::vector<int64_t> eoff(ng + 1, 0);
+    std::vector<int64_t>& eoff = b->eoff;
+    eoff.assign(ng + 1, 0);
     std::vector<GDesc> desc(ng);
     for (int g = 0; g < ng; ++g) {
         const sfg_graph* G = gs[g];
         if (!G) return sfg_fail(ctx, SFG_EINVAL, "graph %d is NULL", g);
-        if (G->m > 0) SFG_TRY(sfg_check_dev(ctx, masks_out[g], "masks_out[g]"));
+        if (G->device != ctx->device) return sfg_fail(ctx, SFG_EINVAL, "graph %d is on another device", g);
         if ((int64_t)noff[g] + G->n >= (1ll << 31) || 2 * (eoff[g] + G->m) >= (1ll << 31))
             return sfg_fail(ctx, SFG_EINVAL, "batch too large for int32 indices");
         noff[g + 1] = noff[g] + G->n;
@@ -170,48 +214,44 @@ extern "C" sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph
     }
     const int32_t n = noff[ng];
     const int64_t m = eoff[ng];
+    b->n = n;
+    b->m = m;
     Scratch s(ctx);
     GDesc* d_desc;
-    int32_t* d_noff;
-    int64_t *d_eoff, *d_coff, *d_k;
-    uint8_t** d_outs;
     unsigned long long* d_cnt;
     SFG_TRY(s.get(&d_desc, ng));
-    SFG_TRY(s.get(&d_noff, ng + 1));
-    SFG_TRY(s.get(&d_eoff, ng + 1));
-    SFG_TRY(s.get(&d_coff, ng + 1));
-    SFG_TRY(s.get(&d_k, ng));
-    SFG_TRY(s.get(&d_outs, ng));
     SFG_TRY(s.get(&d_cnt, ng));
+    SFG_TRY(sfg_alloc(ctx, (void**)&b->d_noff, 4 * (size_t)(ng + 1)));
+    SFG_TRY(sfg_alloc(ctx, (void**)&b->d_eoff, 8 * (size_t)(ng + 1)));
+    SFG_TRY(sfg_alloc(ctx, (void**)&b->d_coff, 8 * (size_t)(ng + 1)));
+    SFG_TRY(sfg_alloc(ctx, (void**)&b->d_k, 8 * (size_t)ng));
+    SFG_TRY(sfg_alloc(ctx, (void**)&b->forest, (size_t)m + 16));
     SFG_CUDA(ctx, cudaMemcpyAsync(d_desc, desc.data(), sizeof(GDesc) * ng, cudaMemcpyHostToDevice, ctx->stream));
-    SFG_CUDA(ctx, cudaMemcpyAsync(d_noff, noff.data(), 4 * (ng + 1), cudaMemcpyHostToDevice, ctx->stream));
-    SFG_CUDA(ctx, cudaMemcpyAsync(d_eoff, eoff.data(), 8 * (ng + 1), cudaMemcpyHostToDevice, ctx->stream));
-    SFG_CUDA(ctx, cudaMemcpyAsync(d_outs, masks_out, sizeof(uint8_t*) * ng, cudaMemcpyHostToDevice, ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(b->d_noff, noff.data(), 4 * (ng + 1), cudaMemcpyHostToDevice, ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(b->d_eoff, eoff.data(), 8 * (ng + 1), cudaMemcpyHostToDevice, ctx->stream));
 
     // the disjoint union U
-    GraphGuard U;
-    SFG_TRY(sfg_alloc_graph(ctx, n, m, &U.g));
+    SFG_TRY(sfg_alloc_graph(ctx, n, m, &b->U));
     if (m > 0) {
         k_union_edges<<<grid_of(ctx, k_union_edges, m), kBlock, 0, ctx->stream>>>(
-            m, d_desc, ng, d_eoff, U.g->eu, U.g->ev, U.g->ew);
+            m, d_desc, ng, b->d_eoff, b->U->eu, b->U->ev, b->U->ew);
         k_union_entries<<<grid_of(ctx, k_union_entries, 2 * m), kBlock, 0, ctx->stream>>>(
-            m, d_desc, ng, d_eoff, U.g->colval, U.g->eid);
+            m, d_desc, ng, b->d_eoff, b->U->colval, b->U->eid);
         ctx->launches += 2;
     }
     k_union_rows<<<grid_of(ctx, k_union_rows, (int64_t)n + 1), kBlock, 0, ctx->stream>>>(
-        n, m, d_desc, ng, d_noff, U.g->row_ptr, U.g->deg, U.g->invdeg);
+        n, m, d_desc, ng, b->d_noff, b->U->row_ptr, b->U->deg, b->U->invdeg);
     ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_union");
 
     // spanning forests of every graph, per-graph forest sizes
-    uint8_t* mask;
-    SFG_TRY(s.get(&mask, m));
     int64_t n_tree = 0;
-    SFG_TRY(sfg_mst_impl(ctx, U.g, nullptr, mask, &n_tree));
+    SFG_TRY(sfg_mst_impl(ctx, b->U, nullptr, b->forest, &n_tree));
     std::vector<int64_t> tree(ng, 0);
     SFG_CUDA(ctx, cudaMemsetAsync(d_cnt, 0, 8 * ng, ctx->stream));
     if (m > 0) {
-        k_seg_count<<<grid_of(ctx, k_seg_count, m), kBlock, 0, ctx->stream>>>(m, mask, ng, d_eoff, d_cnt);
+        k_seg_count<<<grid_of(ctx, k_seg_count, m), kBlock, 0, ctx->stream>>>(m, b->forest, ng,
+                                                                            b->d_eoff, d_cnt);
         ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_seg_count");
     }
@@ -220,61 +260,141 @@ extern "C" sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph
 
     // per-graph budgets (each graph's P starts as its forest: no edge is over budget)
     std::vector<int64_t> kk(ng), coff(ng + 1, 0);
-    int64_t k_total = 0;
+    b->counts.assign(ng, 0);
     for (int g = 0; g < ng; ++g) {
         const int64_t ng_n = noff[g + 1] - noff[g], ng_m = eoff[g + 1] - eoff[g];
-        const int64_t ncand = ng_m - tree[g];
-        const int64_t base = P->budget_unit == 0 ? ng_n : ncand;
+        const int64_t nc = ng_m - tree[g];
+        const int64_t base = P->budget_unit == 0 ? ng_n : nc;
         int64_t k = round_half_up(P->budget_frac * (double)base);
         if (k < 0) k = 0;
-        if (k > ncand) k = ncand;
+        if (k > nc) k = nc;
         kk[g] = k;
-        k_total += k;
-        coff[g + 1] = coff[g] + ncand;
+        b->k_total += k;
+        coff[g + 1] = coff[g] + nc;
+        b->counts[g] = tree[g] + k;
     }
-    const int64_t ncand = coff[ng];
-    SFG_CUDA(ctx, cudaMemcpyAsync(d_coff, coff.data(), 8 * (ng + 1), cudaMemcpyHostToDevice, ctx->stream));
-    SFG_CUDA(ctx, cudaMemcpyAsync(d_k, kk.data(), 8 * ng, cudaMemcpyHostToDevice, ctx->stream));
-
-    if (k_total > 0) {
+    b->ncand = coff[ng];
+    SFG_CUDA(ctx, cudaMemcpyAsync(b->d_coff, coff.data(), 8 * (ng + 1), cudaMemcpyHostToDevice, ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(b->d_k, kk.data(), 8 * ng, cudaMemcpyHostToDevice, ctx->stream));
+    if (b->k_total > 0) {
         uint8_t* flag;
         int64_t* pos;
-        int32_t *cand, *sel;
-        float* scores;
         SFG_TRY(s.get(&flag, m));
         SFG_TRY(s.get(&pos, m + 1));
-        SFG_TRY(s.get(&cand, ncand));
-        SFG_TRY(s.get(&scores, ncand));
-        SFG_TRY(s.get(&sel, k_total));
-        k_not<<<grid_of(ctx, k_not, m), kBlock, 0, ctx->stream>>>(m, mask, flag);
+        SFG_TRY(sfg_alloc(ctx, (void**)&b->cand, 4 * (size_t)b->ncand + 16));
+        k_not<<<grid_of(ctx, k_not, m), kBlock, 0, ctx->stream>>>(m, b->forest, flag);
         ++ctx->launches;
         SFG_TRY(sfg_scan_u8(ctx, flag, pos, m));
-        k_compact<<<grid_of(ctx, k_compact, m), kBlock, 0, ctx->stream>>>(m, flag, pos, cand);
+        k_compact<<<grid_of(ctx, k_compact, m), kBlock, 0, ctx->stream>>>(m, flag, pos, b->cand);
         ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_compact");
-        GraphGuard PU;
-        SFG_TRY(sfg_subgraph_impl(ctx, U.g, mask, &PU.g));
-        SFG_TRY(sfg_filter_score_batched_impl(ctx, U.g, PU.g, ng, d_noff, P->K, P->steps, P->omega,
-                                              P->seed, P->storage, cand, ncand, P->mode, scores));
-        SFG_TRY(sfg_topk_segmented_impl(ctx, scores, cand, ncand, ng, d_coff, d_k, k_total, sel));
-        k_mark<<<grid_of(ctx, k_mark, k_total), kBlock, 0, ctx->stream>>>(k_total, sel, mask);
-        ++ctx->launches;
-        SFG_LAUNCH_CHECK(ctx, "k_mark");
+        SFG_TRY(sfg_subgraph_impl(ctx, b->U, b->forest, &b->PU));
+        // one-time per-graph structures the sweeps use, built here so that runs never synchronise
+        SFG_TRY(sfg_heavy_prepare(ctx, b->U));
+        SFG_TRY(sfg_heavy_prepare(ctx, b->PU));
+        if (autotune) {
+            SFG_TRY(sfg_autotune_impl(ctx, b->U, P->K, P->storage, nullptr, nullptr));
+            SFG_TRY(sfg_autotune_impl(ctx, b->PU, P->K, P->storage, nullptr, nullptr));
+        }
     }
-    if (m > 0) {
-        k_split<<<grid_of(ctx, k_split, m), kBlock, 0, ctx->stream>>>(m, mask, ng, d_eoff, d_outs);
+    SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return SFG_OK;
+}
+
+// The numeric part: forest copied into mask (m entries, union edge order), then the top-scored
+// candidates of every graph added. Launches and stream-ordered allocations only.
+static sfg_status batch_run(sfg_ctx* ctx, const sfg_batch* b, uint64_t seed, uint8_t* mask) {
+    if (b->m > 0)
+        SFG_CUDA(ctx, cudaMemcpyAsync(mask, b->forest, (size_t)b->m, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (b->k_total == 0) return SFG_OK;
+    Scratch s(ctx);
+    int32_t* sel;
+    float* scores;
+    SFG_TRY(s.get(&scores, b->ncand));
+    SFG_TRY(s.get(&sel, b->k_total));
+    const sfg_params& P = b->P;
+    SFG_TRY(sfg_filter_score_batched_impl(ctx, b->U, b->PU, b->ng, b->d_noff, P.K, P.steps, P.omega,
+                                          seed, P.storage, b->cand, b->ncand, P.mode, scores));
+    SFG_TRY(sfg_topk_segmented_impl(ctx, scores, b->cand, b->ncand, b->ng, b->d_coff, b->d_k,
+                                    b->k_total, sel));
+    k_mark<<<grid_of(ctx, k_mark, b->k_total), kBlock, 0, ctx->stream>>>(b->k_total, sel, mask);
+    ++ctx->launches;
+    SFG_LAUNCH_CHECK(ctx, "k_mark");
+    return SFG_OK;
+}
+
+extern "C" {
+
+sfg_status sfg_batch_create(sfg_ctx* ctx, int ng, const sfg_graph* const* gs, const sfg_params* P,
+                            int autotune, sfg_batch** out) {
+    if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
+    if (!out) return sfg_fail(ctx, SFG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ng < 1 || !gs || !P) return sfg_fail(ctx, SFG_EINVAL, "bad batch arguments");
+    SFG_TRY(check_batch_params(ctx, P));
+    sfg_batch* b = new sfg_batch();
+    const sfg_status st = batch_build(ctx, ng, gs, P, autotune, b);
+    if (st != SFG_OK) {
+        batch_free(b);
+        return st;
+    }
+    *out = b;
+    return SFG_OK;
+}
+
+sfg_status sfg_batch_info(const sfg_batch* b, int* ng_host, int64_t* edges_host,
+                          int64_t* edge_offsets_host, int64_t* n_selected_host) {
+    if (!b) return SFG_EINVAL;
+    if (ng_host) *ng_host = b->ng;
+    if (edges_host) *edges_host = b->m;
+    if (edge_offsets_host)
+        for (int g = 0; g <= b->ng; ++g) edge_offsets_host[g] = b->eoff[(size_t)g];
+    if (n_selected_host)
+        for (int g = 0; g < b->ng; ++g) n_selected_host[g] = b->counts[(size_t)g];
+    return SFG_OK;
+}
+
+sfg_status sfg_batch_run(sfg_ctx* ctx, const sfg_batch* b, uint64_t seed, uint8_t* mask_out) {
+    if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
+    if (!b) return sfg_fail(ctx, SFG_EINVAL, "batch is NULL");
+    if (b->device != ctx->device) return sfg_fail(ctx, SFG_EINVAL, "batch is on another device");
+    if (b->m == 0) return SFG_OK;
+    SFG_TRY(sfg_check_dev(ctx, mask_out, "mask_out"));
+    return batch_run(ctx, b, seed, mask_out);
+}
+
+void sfg_batch_destroy(sfg_batch* b) { batch_free(b); }
+
+sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* const* gs,
+                                const sfg_params* P, uint8_t* const* masks_out,
+                                int64_t* n_selected_host) {
+    if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
+    if (ng < 1 || !gs || !P || !masks_out) return sfg_fail(ctx, SFG_EINVAL, "bad batch arguments");
+    SFG_TRY(check_batch_params(ctx, P));
+    for (int g = 0; g < ng; ++g)
+        if (gs[g] && gs[g]->m > 0) SFG_TRY(sfg_check_dev(ctx, masks_out[g], "masks_out[g]"));
+    sfg_batch* b = new sfg_batch();
+    struct Owner { sfg_batch* b; ~Owner() { batch_free(b); } } owner{b};
+    SFG_TRY(batch_build(ctx, ng, gs, P, 0, b));
+    Scratch s(ctx);
+    uint8_t* mask;
+    uint8_t** d_outs;
+    SFG_TRY(s.get(&mask, b->m));
+    SFG_TRY(s.get(&d_outs, ng));
+    SFG_CUDA(ctx, cudaMemcpyAsync(d_outs, masks_out, sizeof(uint8_t*) * ng, cudaMemcpyHostToDevice, ctx->stream));
+    SFG_TRY(batch_run(ctx, b, P->seed, mask));
+    if (b->m > 0) {
+        k_split<<<grid_of(ctx, k_split, b->m), kBlock, 0, ctx->stream>>>(b->m, mask, ng, b->d_eoff, d_outs);
         ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_split");
     }
-    if (n_selected_host) {
-        SFG_CUDA(ctx, cudaMemsetAsync(d_cnt, 0, 8 * ng, ctx->stream));
-        if (m > 0) {
-            k_seg_count<<<grid_of(ctx, k_seg_count, m), kBlock, 0, ctx->stream>>>(m, mask, ng, d_eoff, d_cnt);
-            ++ctx->launches;
-            SFG_LAUNCH_CHECK(ctx, "k_seg_count");
-        }
-        SFG_CUDA(ctx, cudaMemcpyAsync(n_selected_host, d_cnt, 8 * ng, cudaMemcpyDeviceToHost, ctx->stream));
-        SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    }
+    SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // d_outs' host source goes out of scope
+    if (n_selected_host)
+        for (int g = 0; g < ng; ++g) n_selected_host[g] = b->counts[(size_t)g];
     return SFG_OK;
 }
+
+}  // extern "C"

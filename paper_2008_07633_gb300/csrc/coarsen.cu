@@ -137,8 +137,9 @@ static sfg_status aggregate(sfg_ctx* ctx, const sfg_graph* L, const double* delt
     return SFG_OK;
 }
 
-sfg_status sfg_coarsen_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K, int32_t* agg,
-                            int32_t* f2c, int32_t* nc_host, sfg_graph** coarse) {
+sfg_status sfg_coarsen_impl(sfg_ctx* ctx, const sfg_graph* L, const void* X, int K,
+                            sfg_dtype storage, int32_t* agg, int32_t* f2c, int32_t* nc_host,
+                            sfg_graph** coarse) {
     *coarse = nullptr;
     Scratch s(ctx);
     double* delta;
@@ -146,7 +147,7 @@ sfg_status sfg_coarsen_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, in
     SFG_TRY(s.get(&delta, L->m));
     SFG_TRY(s.get(&cu, L->m));
     SFG_TRY(s.get(&cv, L->m));
-    SFG_TRY(sfg_affinity_impl(ctx, L, X, K, delta));
+    SFG_TRY(sfg_affinity_impl(ctx, L, X, K, storage, delta));
     int32_t nc = 0;
     SFG_TRY(aggregate(ctx, L, delta, agg, &nc));
     if (L->m > 0) {
@@ -186,19 +187,22 @@ sfg_status sfg_backward_impl(sfg_ctx* ctx, const sfg_graph* fine, const int32_t*
 
 extern "C" {
 
-sfg_status sfg_coarsen(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K, int32_t* agg_out,
-                       int32_t* fine2coarse_out, int32_t* n_coarse_host, sfg_graph** coarse_out) {
+sfg_status sfg_coarsen(sfg_ctx* ctx, const sfg_graph* L, const void* X, int K, sfg_dtype storage,
+                       int32_t* agg_out, int32_t* fine2coarse_out, int32_t* n_coarse_host,
+                       sfg_graph** coarse_out) {
     if (!ctx) return SFG_EINVAL;
     SFG_DEVICE(ctx);
     if (!L || !coarse_out || !n_coarse_host) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
     if (K < 1) return sfg_fail(ctx, SFG_EINVAL, "K must be >= 1");
+    if (storage != SFG_F32 && storage != SFG_BF16)
+        return sfg_fail(ctx, SFG_EINVAL, "unknown storage type %d", (int)storage);
     SFG_TRY(sfg_check_dev(ctx, X, "X"));
     SFG_TRY(sfg_check_dev(ctx, agg_out, "agg_out"));
     if (fine2coarse_out && L->m > 0) SFG_TRY(sfg_check_dev(ctx, fine2coarse_out, "fine2coarse_out"));
     Scratch s(ctx);
     int32_t* f2c = fine2coarse_out;
     if (!f2c) SFG_TRY(s.get(&f2c, L->m));
-    return sfg_coarsen_impl(ctx, L, X, K, agg_out, f2c, n_coarse_host, coarse_out);
+    return sfg_coarsen_impl(ctx, L, X, K, storage, agg_out, f2c, n_coarse_host, coarse_out);
 }
 
 sfg_status sfg_backward_map(sfg_ctx* ctx, const sfg_graph* fine, const int32_t* agg,

@@ -15,9 +15,6 @@ constexpr int kBlock = 256;
 #ifndef SFG_SCORE_U
 #define SFG_SCORE_U 2
 #endif
-#ifndef SFG_SCORE_IMPL
-#define SFG_SCORE_IMPL 2
-#endif
 
 template <int LPR>
 __device__ __forceinline__ unsigned group_mask(int lane) {
@@ -26,133 +23,22 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 }
 
 // Scorer, warp-tile schedule: a warp scores U consecutive tiles of GPW = 32 / LPR list entries
-// each (one LPR-lane group per edge) and moves by grid stride over such tile groups. Lane
-// l < GPW loads the l-th edge id of each tile and then that edge's endpoints and weight; groups
-// take theirs by shuffle. The next group's endpoints and the ids of the group after it are loaded
+// each (one LPR-lane group per edge) and moves by grid stride over such tile groups. Every lane
+// of a group loads its edge's id, endpoints and weight itself (group-uniform addresses are served
+// as one broadcast). The next group's endpoints and the ids of the group after it are loaded
 // before this group's 4U row gathers are consumed, so one gather round is the exposed latency per
-// U tiles. Gathered rows stay packed (16 bytes per gather) until they are used.
+// U tiles; gathered rows stay packed (16 bytes per gather) until they are used. The two squared
+// distances are folded together: at the first step the even lane of each pair keeps the G partial
+// and the odd lane the P partial, so one shuffle per level moves both, and one more hands the P
+// sum to the group's first lane (LPR = 8: 4 shuffles per edge). The score formula is fixed at
+// compile time (MODE).
 // SCALED: the blocks are raw smoothed blocks and column k of each is multiplied by its projection
 // scale (sg, sp) on the fly; the projection's mean removal cancels in X_p - X_q.
 // SCALED = 2: the scales are per graph of a disjoint union (graph g's rows start at node_off[g]),
 // looked up from each edge's first endpoint.
-template <typename T, int LPR, int SCALED, int U>
-__global__ void __launch_bounds__(kBlock, U > 1 ? 4 : 1)
-    k_score(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
-            const int32_t* __restrict__ ev, const float* __restrict__ ew,
-            const T* __restrict__ XG, const T* __restrict__ XP, int mode, float eta,
-            const float* __restrict__ sg, const float* __restrict__ sp,
-            const int32_t* __restrict__ node_off, int ngraphs, float* __restrict__ out) {
-    constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR;
-    const int lane = threadIdx.x & 31, grp = lane / LPR, sub = lane % LPR;
-    const unsigned gm = group_mask<LPR>(lane);
-    const int64_t wid = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
-    const int64_t ntiles = (ne + GPW - 1) / GPW;
-    const int64_t ngroups = (ntiles + U - 1) / U;
-    const T* __restrict__ Xg = XG + sub * E;
-    const T* __restrict__ Xp = XP + sub * E;
-    // projection scales: shared-memory table for one block (SCALED = 1), read at use
-    __shared__ float s_scale[2][SCALED == 1 ? K : 1];
-    if (SCALED == 1) {
-        for (int k = threadIdx.x; k < K; k += kBlock) {
-            s_scale[0][k] = sg[k];
-            s_scale[1][k] = sp[k];
-        }
-        __syncthreads();
-    }
-    auto load_id = [&](int64_t t) -> int32_t {
-        const int64_t i = t * GPW + lane;
-        return (lane < GPW && i < ne) ? ids[i] : -1;
-    };
-    struct Edge { int32_t p, q; float w; };
-    auto load_edge = [&](int32_t e) {
-        Edge d{0, 0, 0.f};
-        if (e >= 0) { d.p = eu[e]; d.q = ev[e]; d.w = ew[e]; }
-        return d;
-    };
-    int64_t g = wid;
-    Edge cur[U];
-    int32_t idn[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        cur[u] = load_edge(load_id(g * U + u));
-        idn[u] = load_id((g + nw) * U + u);
-    }
-    for (; g < ngroups; g += nw) {
-        Edge nxt[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            nxt[u] = load_edge(idn[u]);            // next group's endpoints
-            idn[u] = load_id((g + 2 * nw) * U + u);  // ids of the group after it
-        }
-        uint4 rgp[U], rgq[U], rpp[U], rpq[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t p = __shfl_sync(0xffffffffu, cur[u].p, grp);
-            const int64_t q = __shfl_sync(0xffffffffu, cur[u].q, grp);
-            rgp[u] = Vec<T>::load_raw(Xg + p * K);
-            rgq[u] = Vec<T>::load_raw(Xg + q * K);
-            rpp[u] = Vec<T>::load_raw(Xp + p * K);
-            rpq[u] = Vec<T>::load_raw(Xp + q * K);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = (g * U + u) * GPW + grp;
-            const float w = __shfl_sync(0xffffffffu, cur[u].w, grp);
-            const float* sc_g = nullptr;  // this edge's scales (SCALED = 2: of its graph)
-            const float* sc_p = nullptr;
-            if (SCALED == 1) {
-                sc_g = s_scale[0] + sub * E;
-                sc_p = s_scale[1] + sub * E;
-            } else if (SCALED == 2) {
-                const int32_t p = __shfl_sync(0xffffffffu, cur[u].p, grp);
-                int lo = 0, hi = ngraphs;  // graph of row p
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (node_off[mid] <= p) lo = mid; else hi = mid;
-                }
-                sc_g = sg + (size_t)lo * K + sub * E;
-                sc_p = sp + (size_t)lo * K + sub * E;
-            }
-            float gp[E], gq[E], pp[E], pq[E];
-            Vec<T>::unpack(rgp[u], gp);
-            Vec<T>::unpack(rgq[u], gq);
-            Vec<T>::unpack(rpp[u], pp);
-            Vec<T>::unpack(rpq[u], pq);
-            float dg = 0.f, dp = 0.f;
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                float a = gp[k] - gq[k], b = pp[k] - pq[k];
-                if (SCALED) {
-                    a *= sc_g[k];
-                    b *= sc_p[k];
-                }
-                dg = fmaf(a, a, dg);
-                dp = fmaf(b, b, dp);
-            }
-#pragma unroll
-            for (int o = 1; o < LPR; o <<= 1) {
-                dg += __shfl_xor_sync(gm, dg, o, LPR);
-                dp += __shfl_xor_sync(gm, dp, o, LPR);
-            }
-            if (sub == 0 && i < ne) {
-                const float sgv = w * dg, spv = w * dp;
-                out[i] = mode == SFG_SCORE_G ? sgv : (mode == SFG_SCORE_P ? spv : spv / (sgv + eta));
-            }
-            cur[u] = nxt[u];
-        }
-    }
-}
-
-// Scorer with fewer shuffles (same tiles and pipeline as k_score): every lane of a group loads
-// its edge's id, endpoints and weight itself (group-uniform addresses are served as one
-// broadcast), and the two squared distances are folded together: at the first step the even lane
-// of each pair keeps the G partial and the odd lane the P partial, so one shuffle per level moves
-// both, and one more hands the P sum to the group's first lane (LPR = 8: 4 shuffles per edge
-// instead of 9). The score formula is fixed at compile time (MODE).
 template <typename T, int LPR, int SCALED, int U, int MODE>
 __global__ void __launch_bounds__(kBlock, U > 1 ? 4 : 1)
-    k_score2(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
+    k_score(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
              const int32_t* __restrict__ ev, const float* __restrict__ ew,
              const T* __restrict__ XG, const T* __restrict__ XP, float eta,
              const float* __restrict__ sg, const float* __restrict__ sp,
@@ -265,13 +151,18 @@ __global__ void __launch_bounds__(kBlock, U > 1 ? 4 : 1)
     }
 }
 
+// Stored block entry widened to FP64 (exact for FP32 and BF16).
+__device__ __forceinline__ double widen(float x) { return (double)x; }
+__device__ __forceinline__ double widen(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
 // ||X_p||^2 in FP64, increasing k, no fused multiply-add.
-__global__ void k_rownorm(int32_t n, const float* __restrict__ X, int K, double* __restrict__ nn) {
+template <typename T>
+__global__ void k_rownorm(int32_t n, const T* __restrict__ X, int K, double* __restrict__ nn) {
     for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * kBlock) {
         double s = 0.0;
         for (int k = 0; k < K; ++k) {
-            const double x = (double)X[p * K + k];
+            const double x = widen(X[p * K + k]);
             s = __dadd_rn(s, __dmul_rn(x, x));
         }
         nn[p] = s;
@@ -280,15 +171,16 @@ __global__ void k_rownorm(int32_t n, const float* __restrict__ X, int K, double*
 
 // delta_e = 1 - (X_p . X_q)^2 / (||X_p||^2 ||X_q||^2) in FP64, same operation order as the
 // definition, no fused multiply-add; a zero row gives 1.
+template <typename T>
 __global__ void k_affinity(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-                           const float* __restrict__ X, int K, const double* __restrict__ nn,
+                           const T* __restrict__ X, int K, const double* __restrict__ nn,
                            double* __restrict__ delta) {
     for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * kBlock) {
         const int64_t p = eu[e], q = ev[e];
         double dot = 0.0;
         for (int k = 0; k < K; ++k)
-            dot = __dadd_rn(dot, __dmul_rn((double)X[p * K + k], (double)X[q * K + k]));
+            dot = __dadd_rn(dot, __dmul_rn(widen(X[p * K + k]), widen(X[q * K + k])));
         const double den = __dmul_rn(nn[p], nn[q]);
         delta[e] = den > 0.0 ? __dsub_rn(1.0, __ddiv_rn(__dmul_rn(dot, dot), den)) : 1.0;
     }
@@ -303,23 +195,15 @@ sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const
     constexpr int U = SFG_SCORE_U;
     const T *xg = (const T*)XG, *xp = (const T*)XP;
     float eta = 1e-30f;
-#if SFG_SCORE_IMPL == 2
     const int sc = node_off ? 2 : (sg ? 1 : 0);
     static void* const tab[3][3] = {
-        {(void*)k_score2<T, LPR, 0, U, 0>, (void*)k_score2<T, LPR, 0, U, 1>, (void*)k_score2<T, LPR, 0, U, 2>},
-        {(void*)k_score2<T, LPR, 1, U, 0>, (void*)k_score2<T, LPR, 1, U, 1>, (void*)k_score2<T, LPR, 1, U, 2>},
-        {(void*)k_score2<T, LPR, 2, U, 0>, (void*)k_score2<T, LPR, 2, U, 1>, (void*)k_score2<T, LPR, 2, U, 2>}};
+        {(void*)k_score<T, LPR, 0, U, 0>, (void*)k_score<T, LPR, 0, U, 1>, (void*)k_score<T, LPR, 0, U, 2>},
+        {(void*)k_score<T, LPR, 1, U, 0>, (void*)k_score<T, LPR, 1, U, 1>, (void*)k_score<T, LPR, 1, U, 2>},
+        {(void*)k_score<T, LPR, 2, U, 0>, (void*)k_score<T, LPR, 2, U, 1>, (void*)k_score<T, LPR, 2, U, 2>}};
     const void* k = tab[sc][mode];
     void* args[] = {(void*)&ne, (void*)&ids, (void*)&LG->eu, (void*)&LG->ev, (void*)&LG->ew,
                     (void*)&xg, (void*)&xp, (void*)&eta, (void*)&sg, (void*)&sp,
                     (void*)&node_off, (void*)&ngraphs, (void*)&out};
-#else
-    const void* k = node_off ? (const void*)k_score<T, LPR, 2, U>
-                             : (sg ? (const void*)k_score<T, LPR, 1, U> : (const void*)k_score<T, LPR, 0, U>);
-    void* args[] = {(void*)&ne, (void*)&ids, (void*)&LG->eu, (void*)&LG->ev, (void*)&LG->ew,
-                    (void*)&xg, (void*)&xp, (void*)&mode, (void*)&eta, (void*)&sg, (void*)&sp,
-                    (void*)&node_off, (void*)&ngraphs, (void*)&out};
-#endif
     const int grid = sfg_grid(ctx, k, kBlock, 0, (ne + U - 1) / U * LPR);
     sfg_tic(ctx, "score");
     const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kBlock), args, 0, ctx->stream);
@@ -365,22 +249,33 @@ sfg_status sfg_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, con
                                   0);
 }
 
-sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
-                             double* delta) {
+namespace {
+template <typename T>
+sfg_status affinity_t(sfg_ctx* ctx, const sfg_graph* L, const T* X, int K, double* delta) {
     Scratch s(ctx);
     double* nn;
     SFG_TRY(s.get(&nn, (size_t)L->n));
-    k_rownorm<<<sfg_grid(ctx, (const void*)k_rownorm, kBlock, 0, L->n), kBlock, 0, ctx->stream>>>(
-        L->n, X, K, nn); ++ctx->launches;
+    k_rownorm<T><<<sfg_grid(ctx, (const void*)k_rownorm<T>, kBlock, 0, L->n), kBlock, 0,
+                   ctx->stream>>>(L->n, X, K, nn);
+    ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_rownorm");
     if (L->m > 0) {
         sfg_tic(ctx, "affinity");
-        k_affinity<<<sfg_grid(ctx, (const void*)k_affinity, kBlock, 0, L->m), kBlock, 0,
-                     ctx->stream>>>(L->m, L->eu, L->ev, X, K, nn, delta); ++ctx->launches;
+        k_affinity<T><<<sfg_grid(ctx, (const void*)k_affinity<T>, kBlock, 0, L->m), kBlock, 0,
+                        ctx->stream>>>(L->m, L->eu, L->ev, X, K, nn, delta);
+        ++ctx->launches;
         sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_affinity");
     }
     return SFG_OK;
+}
+}  // namespace
+
+sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const void* X, int K,
+                             sfg_dtype storage, double* delta) {
+    if (storage == SFG_BF16)
+        return affinity_t(ctx, L, (const __nv_bfloat16*)X, K, delta);
+    return affinity_t(ctx, L, (const float*)X, K, delta);
 }
 
 extern "C" {
@@ -415,7 +310,7 @@ sfg_status sfg_affinity(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
     if (K < 1) return sfg_fail(ctx, SFG_EINVAL, "K must be >= 1");
     SFG_TRY(sfg_check_dev(ctx, X, "X"));
     if (L->m > 0) SFG_TRY(sfg_check_dev(ctx, delta_out, "delta_out"));
-    return sfg_affinity_impl(ctx, L, X, K, delta_out);
+    return sfg_affinity_impl(ctx, L, X, K, SFG_F32, delta_out);
 }
 
 }  // extern "C"

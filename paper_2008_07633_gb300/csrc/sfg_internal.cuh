@@ -222,8 +222,9 @@ sfg_status sfg_filter_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_gr
                                  float* scores);
 sfg_status sfg_topk_impl(sfg_ctx* ctx, const float* scores, const int32_t* ids, int64_t ne,
                          int64_t k, int32_t* out);
-sfg_status sfg_coarsen_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
-                            int32_t* agg, int32_t* f2c, int32_t* nc, sfg_graph** coarse);
+sfg_status sfg_coarsen_impl(sfg_ctx* ctx, const sfg_graph* L, const void* X, int K,
+                            sfg_dtype storage, int32_t* agg, int32_t* f2c, int32_t* nc,
+                            sfg_graph** coarse);
 sfg_status sfg_backward_impl(sfg_ctx* ctx, const sfg_graph* fine, const int32_t* agg,
                              const int32_t* f2c, const sfg_graph* coarse, const uint8_t* pmask_c,
                              uint8_t* pmask_f);
@@ -268,8 +269,8 @@ sfg_status sfg_smooth_gs_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps
                               uint64_t seed, sfg_dtype storage, void* X_out);
 sfg_status sfg_pointer_jump(sfg_ctx* ctx, int32_t n, const int32_t* comp, int32_t* parent);
 sfg_status sfg_count_mask(sfg_ctx* ctx, const uint8_t* mask, int64_t m, int64_t* count_host);
-sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const float* X, int K,
-                             double* delta);
+sfg_status sfg_affinity_impl(sfg_ctx* ctx, const sfg_graph* L, const void* X, int K,
+                             sfg_dtype storage, double* delta);
 // Resolve (once per device, with ctx's device current) the device address of the file-scope
 // scratch of the allocation-free entry points (noalloc.cu); called by sfg_ctx_create.
 sfg_status sfg_noalloc_prepare(sfg_ctx* ctx);

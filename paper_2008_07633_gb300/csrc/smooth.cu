@@ -23,9 +23,6 @@
 namespace {
 
 constexpr int kBlock = 256;
-#ifndef SFG_JACOBI_HINT
-#define SFG_JACOBI_HINT 0
-#endif
 // Tile-shape variants of the sweep, chosen per (K, storage, degree bucket) by sfg_autotune:
 // TPI = consecutive row tiles a warp sweeps before its grid-stride jump, MINB = resident CTAs per
 // SM requested from the compiler (4 caps registers at 64, 3 at 80).
@@ -155,19 +152,12 @@ __device__ __forceinline__ void gather_slots(const Chunk<LPR>& ch, int s0, unsig
                                              const T* __restrict__ Xl, float (&acc)[Vec<T>::E]) {
     constexpr int K = LPR * Vec<T>::E, C = Chunk<LPR>::C;
     uint4 xv[NS];
-#if SFG_JACOBI_HINT
-    const uint64_t keep = l2_policy_evict_last();
-#endif
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
         const int slot = s0 + u;
         if (slot < C) {
             const int c = __shfl_sync(gm, ch.cv[slot / LPR].x, slot % LPR, LPR);
-#if SFG_JACOBI_HINT
-            xv[u] = ld_hint(Xl + (int64_t)c * K, keep);
-#else
             xv[u] = Vec<T>::load_raw(Xl + (int64_t)c * K);
-#endif
         }
     }
 #pragma unroll
@@ -275,11 +265,7 @@ __global__ void __launch_bounds__(kBlock, MINB)
 #pragma unroll
                 for (int e = 0; e < E; ++e) y[e] = xs[e] - m[e];
             }
-#if SFG_JACOBI_HINT >= 2
-            st_hint(Y + (int64_t)r * K + sub * E, Vec<T>::pack(y), l2_policy_evict_first());
-#else
             Vec<T>::store(Y + (int64_t)r * K + sub * E, y);
-#endif
             if (STATS)
 #pragma unroll
                 for (int e = 0; e < E; ++e) {

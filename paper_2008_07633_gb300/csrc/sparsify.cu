@@ -32,12 +32,6 @@ __global__ void k_set_mask(int64_t k, const int32_t* __restrict__ ids, uint8_t* 
         mask[ids[i]] = 1;
 }
 
-__global__ void k_f32_to_bf16(int64_t n, const float* __restrict__ x, __nv_bfloat16* __restrict__ y) {
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * kBlock)
-        y[i] = __float2bfloat16_rn(x[i]);
-}
-
 // Smoother choice and its omega range: weighted Jacobi (0, 1], Gauss-Seidel / SOR (0, 2).
 bool omega_ok(const sfg_params* P) {
     if (P->smoother == SFG_SMOOTH_JACOBI) return P->omega > 0.0 && P->omega <= 1.0;
@@ -58,11 +52,12 @@ int64_t round_half_up(double x) { return (int64_t)std::floor(x + 0.5); }
 
 size_t elem_size(sfg_dtype dt) { return dt == SFG_BF16 ? 2 : 4; }
 
-// Edge recovery at one level (Sec. 3.5; the embedding, scoring and selection steps of Algorithm 1). `mask` holds the current
-// sparsifier of g and receives the added edges. XG_f32: the FP32 embedding of g from this level's
-// seed (may be NULL: computed here in the requested storage).
+// Edge recovery at one level (Sec. 3.5; the embedding, scoring and selection steps of
+// Algorithm 1). `mask` holds the current sparsifier of g and receives the added edges. XG: the
+// embedding of g from this level's seed in P->storage, cached from coarsening (may be NULL:
+// computed here).
 sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64_t seed,
-                   int64_t forest, const float* XG_f32, uint8_t* mask) {
+                   int64_t forest, const void* XG, uint8_t* mask) {
     const int64_t m = g->m;
     const int64_t base = P->budget_unit == 0 ? (int64_t)g->n : m - forest;
     const int64_t target = round_half_up(P->budget_frac * (double)base);
@@ -99,36 +94,26 @@ sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64
         // P sweeps in G's colour order (a proper colouring of P as well): no second colouring
         SFG_TRY(sfg_gs_inherit(ctx, pg, g));
         const size_t blk = (size_t)g->n * P->K * elem_size(P->storage);
-        void *xg, *xp;
+        void* xp;
+        const void* xg = XG;
         SFG_TRY(s.get((char**)&xp, blk));
-        if (XG_f32 && P->storage == SFG_F32) {
-            xg = const_cast<float*>(XG_f32);
-        } else {
-            SFG_TRY(s.get((char**)&xg, blk));
-            SFG_TRY(sfg_smooth_gs_impl(ctx, g, P->K, P->steps, P->omega, seed, P->storage, xg));
+        if (!xg) {
+            void* x;
+            SFG_TRY(s.get((char**)&x, blk));
+            SFG_TRY(sfg_smooth_gs_impl(ctx, g, P->K, P->steps, P->omega, seed, P->storage, x));
+            xg = x;
         }
         SFG_TRY(sfg_smooth_gs_impl(ctx, pg, P->K, P->steps, P->omega, seed, P->storage, xp));
         SFG_TRY(sfg_score_impl(ctx, g, xg, xp, P->K, P->storage, cand, ncand, P->mode, scores));
-    } else if (!XG_f32) {  // embed G and P from one seeded block and score in one pass
+    } else if (!XG) {  // embed G and P from one seeded block and score in one pass
         SFG_TRY(sfg_filter_score_impl(ctx, g, pg, P->K, P->steps, P->omega, seed, P->storage, cand,
                                       ncand, P->mode, scores));
-    } else {  // reuse the level's cached FP32 embedding of G
+    } else {  // reuse the level's cached embedding of G
         const size_t blk = (size_t)g->n * P->K * elem_size(P->storage);
         void* xp;
         SFG_TRY(s.get((char**)&xp, blk));
-        const void* xg = XG_f32;
-        if (P->storage != SFG_F32) {
-            void* x;
-            SFG_TRY(s.get((char**)&x, blk));
-            const int64_t cnt = (int64_t)g->n * P->K;
-            k_f32_to_bf16<<<sfg_grid(ctx, (const void*)k_f32_to_bf16, kBlock, 0, cnt), kBlock, 0,
-                            ctx->stream>>>(cnt, XG_f32, (__nv_bfloat16*)x);
-            ++ctx->launches;
-            SFG_LAUNCH_CHECK(ctx, "k_f32_to_bf16");
-            xg = x;
-        }
         SFG_TRY(sfg_smooth_impl(ctx, pg, P->K, P->steps, P->omega, seed, P->storage, xp));
-        SFG_TRY(sfg_score_impl(ctx, g, xg, xp, P->K, P->storage, cand, ncand, P->mode, scores));
+        SFG_TRY(sfg_score_impl(ctx, g, XG, xp, P->K, P->storage, cand, ncand, P->mode, scores));
     }
     SFG_TRY(sfg_topk_impl(ctx, scores, cand, ncand, k, sel));
     k_set_mask<<<sfg_grid(ctx, (const void*)k_set_mask, kBlock, 0, k), kBlock, 0, ctx->stream>>>(
@@ -141,17 +126,42 @@ struct Level {
     sfg_graph* g = nullptr;   // G_l (level 0 borrowed)
     int32_t* agg = nullptr;   // map G_{l-1} -> G_l (l >= 1)
     int32_t* f2c = nullptr;   // fine edge of G_{l-1} -> edge of G_l
-    float* xg = nullptr;      // FP32 embedding of G_l used for coarsening (l < lf)
+    void* xg = nullptr;       // embedding of G_l used for coarsening (l < lf), in P->storage
+    uint8_t* pmask = nullptr; // the level's sparsifier P_l over G_l's edges
 };
 
 }  // namespace
 
+// The coarsening hierarchy of one sfg_sparsify call (Algorithm 1's [G_1 .. G_lf; H_1 .. H_lf]
+// with each level's sparsifier): device arrays owned here, freed by sfg_hierarchy_destroy.
+struct sfg_hierarchy {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    const sfg_graph* g0 = nullptr;        // the input graph (borrowed)
+    std::vector<Level> lv;                // levels 0..lf (level 0's graph is g0)
+};
+
+static void hierarchy_free(sfg_hierarchy* h) {
+    if (!h) return;
+    SfgDeviceGuard guard(h->device);
+    for (size_t l = 0; l < h->lv.size(); ++l) {
+        Level& v = h->lv[l];
+        if (l > 0) sfg_graph_free(v.g);
+        void* ptrs[] = {v.agg, v.f2c, v.pmask};
+        for (void* p : ptrs)
+            if (p) cudaFreeAsync(p, h->stream);
+    }
+    delete h;
+}
+
 extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* P,
-                                   uint8_t* mask_out, int64_t* n_selected_host) {
+                                   uint8_t* mask_out, int64_t* n_selected_host,
+                                   sfg_hierarchy** hier_out) {
     if (!ctx) return SFG_EINVAL;
     SFG_DEVICE(ctx);
+    if (hier_out) *hier_out = nullptr;
     if (!G || !P) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
-    if (!sfg_k_supported(P->K, P->storage) || !sfg_k_supported(P->K, SFG_F32))
+    if (!sfg_k_supported(P->K, P->storage))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K,
                         (int)P->storage);
     if (P->steps < 0 || P->levels < 0 || !omega_ok(P) ||
@@ -160,35 +170,46 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
         return sfg_fail(ctx, SFG_EINVAL, "invalid sfg_params");
     if (G->m > 0) SFG_TRY(sfg_check_dev(ctx, mask_out, "mask_out"));
 
-    std::vector<Level> lv(1);
-    lv[0].g = const_cast<sfg_graph*>(G);
+    // The levels live in a hierarchy object; it goes to the caller when asked for (and on
+    // success), else it is freed on return.
+    sfg_hierarchy* h = new sfg_hierarchy();
+    h->device = ctx->device;
+    h->stream = ctx->stream;
+    h->g0 = G;
+    h->lv.resize(1);
+    h->lv[0].g = const_cast<sfg_graph*>(G);
+    struct Owner {
+        sfg_hierarchy* h;
+        ~Owner() { hierarchy_free(h); }
+    } owner{h};
+    std::vector<Level>& lv = h->lv;
     Scratch s(ctx);
-    struct Cleanup {
-        std::vector<Level>* lv;
-        ~Cleanup() {
-            for (size_t i = 1; i < lv->size(); ++i) sfg_graph_free((*lv)[i].g);
-        }
-    } cleanup{&lv};
+    const size_t es = elem_size(P->storage);
 
     // Algorithm 1, coarsening phase: multilevel spectral graph reduction
     for (int l = 1; l <= P->levels; ++l) {
-        Level& f = lv.back();
-        if (f.g->m == 0) break;
-        SFG_TRY(s.get(&f.xg, (size_t)f.g->n * P->K));
-        SFG_TRY(smooth_any(ctx, P, f.g, level_seed(P->seed, l - 1), SFG_F32, f.xg));
-        Level c;
-        SFG_TRY(s.get(&c.agg, f.g->n));
-        SFG_TRY(s.get(&c.f2c, f.g->m));
+        if (lv.back().g->m == 0) break;
+        {
+            Level& f = lv.back();
+            char* xg;
+            SFG_TRY(s.get(&xg, (size_t)f.g->n * P->K * es));
+            f.xg = xg;
+            SFG_TRY(smooth_any(ctx, P, f.g, level_seed(P->seed, l - 1), P->storage, f.xg));
+        }
+        lv.emplace_back();
+        Level& f = lv[lv.size() - 2];
+        Level& c = lv.back();
+        SFG_TRY(sfg_alloc(ctx, (void**)&c.agg, (size_t)f.g->n * 4 + 16));
+        SFG_TRY(sfg_alloc(ctx, (void**)&c.f2c, (size_t)f.g->m * 4 + 16));
         int32_t nc = 0;
-        SFG_TRY(sfg_coarsen_impl(ctx, f.g, f.xg, P->K, c.agg, c.f2c, &nc, &c.g));
-        lv.push_back(c);
+        SFG_TRY(sfg_coarsen_impl(ctx, f.g, f.xg, P->K, P->storage, c.agg, c.f2c, &nc, &c.g));
     }
     const int lf = (int)lv.size() - 1;
 
     // coarsest level: spanning forest + recovered off-tree edges
     const sfg_graph* gc = lv[lf].g;
-    uint8_t* pm;
-    SFG_TRY(s.get(&pm, gc->m));
+    SFG_TRY(sfg_alloc(ctx, (void**)&lv[lf].pmask, (size_t)gc->m + 16));
+    uint8_t* pm = lv[lf].pmask;
     int64_t n_tree = 0;
     SFG_TRY(sfg_mst_impl(ctx, gc, nullptr, pm, &n_tree));
     const int64_t comps = (int64_t)gc->n - n_tree;  // same at every level: aggregates are connected
@@ -197,18 +218,75 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
     // Algorithm 1, level loop: map back and recover edges level by level
     for (int l = lf; l >= 1; --l) {
         const sfg_graph* f = lv[l - 1].g;
-        uint8_t* pf;
-        SFG_TRY(s.get(&pf, f->m));
+        SFG_TRY(sfg_alloc(ctx, (void**)&lv[l - 1].pmask, (size_t)f->m + 16));
+        uint8_t* pf = lv[l - 1].pmask;
         SFG_TRY(sfg_backward_impl(ctx, f, lv[l].agg, lv[l].f2c, lv[l].g, pm, pf));
         SFG_TRY(recover(ctx, f, P, level_seed(P->seed, l - 1), (int64_t)f->n - comps, lv[l - 1].xg,
                         pf));
         pm = pf;
     }
+    for (Level& v : lv) v.xg = nullptr;  // scratch, freed with s
     if (G->m > 0)
         SFG_CUDA(ctx, cudaMemcpyAsync(mask_out, pm, G->m, cudaMemcpyDeviceToDevice, ctx->stream));
     if (n_selected_host) SFG_TRY(sfg_count_mask(ctx, mask_out, G->m, n_selected_host));
+    if (hier_out) {
+        *hier_out = h;
+        owner.h = nullptr;
+    }
     return SFG_OK;
 }
+
+extern "C" {
+
+sfg_status sfg_hierarchy_levels(const sfg_hierarchy* h, int* levels_host) {
+    if (!h || !levels_host) return SFG_EINVAL;
+    *levels_host = (int)h->lv.size() - 1;
+    return SFG_OK;
+}
+
+sfg_status sfg_hierarchy_graph(const sfg_hierarchy* h, int level, const sfg_graph** out) {
+    if (!h || !out || level < 0 || level >= (int)h->lv.size()) return SFG_EINVAL;
+    *out = h->lv[(size_t)level].g;
+    return SFG_OK;
+}
+
+sfg_status sfg_hierarchy_map(sfg_ctx* ctx, const sfg_hierarchy* h, int level, int32_t* agg_out,
+                             int32_t* fine2coarse_out) {
+    if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
+    if (!h || level < 1 || level >= (int)h->lv.size())
+        return sfg_fail(ctx, SFG_EINVAL, "level must be in [1, levels]");
+    const Level& c = h->lv[(size_t)level];
+    const sfg_graph* f = h->lv[(size_t)level - 1].g;
+    if (agg_out && f->n > 0) {
+        SFG_TRY(sfg_check_dev(ctx, agg_out, "agg_out"));
+        SFG_CUDA(ctx, cudaMemcpyAsync(agg_out, c.agg, (size_t)f->n * 4, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+    }
+    if (fine2coarse_out && f->m > 0) {
+        SFG_TRY(sfg_check_dev(ctx, fine2coarse_out, "fine2coarse_out"));
+        SFG_CUDA(ctx, cudaMemcpyAsync(fine2coarse_out, c.f2c, (size_t)f->m * 4,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return SFG_OK;
+}
+
+sfg_status sfg_hierarchy_mask(sfg_ctx* ctx, const sfg_hierarchy* h, int level, uint8_t* mask_out) {
+    if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
+    if (!h || level < 0 || level >= (int)h->lv.size())
+        return sfg_fail(ctx, SFG_EINVAL, "level must be in [0, levels]");
+    const Level& v = h->lv[(size_t)level];
+    if (v.g->m == 0) return SFG_OK;
+    SFG_TRY(sfg_check_dev(ctx, mask_out, "mask_out"));
+    SFG_CUDA(ctx, cudaMemcpyAsync(mask_out, v.pmask, (size_t)v.g->m, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    return SFG_OK;
+}
+
+void sfg_hierarchy_destroy(sfg_hierarchy* h) { hierarchy_free(h); }
+
+}  // extern "C"
 
 extern "C" sfg_status sfg_sparsify_learned(sfg_ctx* ctx, const sfg_graph* G, const sfg_params* P,
                                            const sfg_mlp* net, int feat_steps, double propose_frac,
@@ -219,7 +297,7 @@ extern "C" sfg_status sfg_sparsify_learned(sfg_ctx* ctx, const sfg_graph* G, con
     if (P->levels != 0) return sfg_fail(ctx, SFG_EUNSUPPORTED, "learned proposals are flat (levels = 0)");
     if (P->smoother != SFG_SMOOTH_JACOBI)
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "learned proposals use the Jacobi smoother only");
-    if (!net || !(propose_frac < 1.0)) return sfg_sparsify(ctx, G, P, mask_out, n_selected_host);
+    if (!net || !(propose_frac < 1.0)) return sfg_sparsify(ctx, G, P, mask_out, n_selected_host, nullptr);
     if (!sfg_k_supported(P->K, P->storage))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K, (int)P->storage);
     if (feat_steps < 0 || !(propose_frac > 0.0) || P->steps < 0 || !(P->omega > 0.0 && P->omega <= 1.0) ||

@@ -6,30 +6,6 @@
 template <typename T>
 struct Vec;
 
-// L2 eviction-priority hints (PTX createpolicy + L2::cache_hint): gathered neighbour rows ask to
-// be kept (evict_last), streamed output rows to go first (evict_first).
-__device__ __forceinline__ uint64_t l2_policy_evict_last() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t l2_policy_evict_first() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint4 ld_hint(const void* ptr, uint64_t pol) {
-    uint4 r;
-    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(ptr), "l"(pol));
-    return r;
-}
-__device__ __forceinline__ void st_hint(void* ptr, uint4 v, uint64_t pol) {
-    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;"
-                 :: "l"(ptr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol) : "memory");
-}
-
 template <>
 struct Vec<float> {
     static constexpr int E = 4;

@@ -29,7 +29,10 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_trim", "sfg_ctx_set_str
            "sfg_mlp_gradient", "sfg_mlp_train", "sfg_edge_features", "sfg_sparsify_learned",
            "sfg_autotune", "sfg_tune_set", "sfg_tune_table",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify", "sfg_kappa",
-           "sfg_sparsify_to_kappa", "sfg_smooth_gs", "sfg_coloring", "sfg_solve_pcg"]
+           "sfg_sparsify_to_kappa", "sfg_smooth_gs", "sfg_coloring", "sfg_solve_pcg",
+           "sfg_hierarchy_levels", "sfg_hierarchy_graph", "sfg_hierarchy_map",
+           "sfg_hierarchy_mask", "sfg_hierarchy_destroy", "sfg_batch_create", "sfg_batch_info",
+           "sfg_batch_run", "sfg_batch_destroy"]
 
 
 class SfgError(RuntimeError):
@@ -86,9 +89,19 @@ def lib():
             "sfg_spanning_tree": [_vp, _vp, _vp, _vp, _pi64],
             "sfg_affinity": [_vp, _vp, _vp, _int, _vp],
             "sfg_affinity_noalloc": [_vp, _vp, _vp, _int, _vp],
-            "sfg_coarsen": [_vp, _vp, _vp, _int, _vp, _vp, _pi32, ctypes.POINTER(_vp)],
+            "sfg_coarsen": [_vp, _vp, _vp, _int, _int, _vp, _vp, _pi32, ctypes.POINTER(_vp)],
             "sfg_backward_map": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
-            "sfg_sparsify": [_vp, _vp, ctypes.POINTER(sfg_params), _vp, _pi64],
+            "sfg_sparsify": [_vp, _vp, ctypes.POINTER(sfg_params), _vp, _pi64, ctypes.POINTER(_vp)],
+            "sfg_hierarchy_levels": [_vp, ctypes.POINTER(_int)],
+            "sfg_hierarchy_graph": [_vp, _int, ctypes.POINTER(_vp)],
+            "sfg_hierarchy_map": [_vp, _vp, _int, _vp, _vp],
+            "sfg_hierarchy_mask": [_vp, _vp, _int, _vp],
+            "sfg_hierarchy_destroy": [_vp],
+            "sfg_batch_create": [_vp, _int, ctypes.POINTER(_vp), ctypes.POINTER(sfg_params), _int,
+                                 ctypes.POINTER(_vp)],
+            "sfg_batch_info": [_vp, ctypes.POINTER(_int), _pi64, _pi64, _pi64],
+            "sfg_batch_run": [_vp, _vp, _u64, _vp],
+            "sfg_batch_destroy": [_vp],
             "sfg_sparsify_batched": [_vp, _int, ctypes.POINTER(_vp), ctypes.POINTER(sfg_params),
                                      ctypes.POINTER(_vp), _pi64],
             "sfg_kappa": [_vp, _vp, _vp, _int, _u64, _pdbl, _pdbl],
@@ -113,7 +126,8 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = None if name in ("sfg_ctx_destroy", "sfg_graph_destroy",
-                                         "sfg_mlp_destroy") else _int
+                                         "sfg_mlp_destroy", "sfg_hierarchy_destroy",
+                                         "sfg_batch_destroy") else _int
         L.sfg_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
@@ -342,12 +356,12 @@ def sfg_affinity_noalloc(ctx, g, X, out=None):
 
 
 def sfg_coarsen(ctx, g, X):
-    assert X.dtype == torch.float32 and X.is_contiguous()
+    assert X.dtype in (torch.float32, torch.bfloat16) and X.is_contiguous()
     agg = torch.empty(g.n, dtype=torch.int32, device=ctx.device)
     f2c = torch.empty(g.m, dtype=torch.int32, device=ctx.device)
     nc = _i32()
     h = _vp()
-    ctx.check(lib().sfg_coarsen(ctx.h, g.h, _ptr(X), X.shape[1], _ptr(agg), _ptr(f2c),
+    ctx.check(lib().sfg_coarsen(ctx.h, g.h, _ptr(X), X.shape[1], _dt(X.dtype), _ptr(agg), _ptr(f2c),
                                 ctypes.byref(nc), ctypes.byref(h)))
     return agg, f2c, Graph(ctx, h)
 
@@ -359,15 +373,76 @@ def sfg_backward_map(ctx, fine, agg, f2c, coarse, pmask_c):
     return out
 
 
+class Hierarchy:
+    """Owner of an sfg_hierarchy handle: the levels of one sfg_sparsify call."""
+
+    def __init__(self, ctx, h, g0):
+        self.ctx, self.h, self._g0 = ctx, h, g0
+        lv = _int()
+        ctx.check(lib().sfg_hierarchy_levels(h, ctypes.byref(lv)))
+        self.levels = lv.value
+        self.graphs = [g0]
+        for lvl in range(1, self.levels + 1):
+            gh = _vp()
+            ctx.check(lib().sfg_hierarchy_graph(h, lvl, ctypes.byref(gh)))
+            self.graphs.append(_BorrowedGraph(gh, self))
+
+    def graph(self, level):
+        """G_level (level 0 is the input graph)."""
+        return self.graphs[level]
+
+    def map(self, level):
+        """H_level: (agg over G_{level-1}'s nodes, fine2coarse over G_{level-1}'s edges)."""
+        f = self.graphs[level - 1]
+        agg = torch.empty(f.n, dtype=torch.int32, device=self.ctx.device)
+        f2c = torch.empty(max(f.m, 1), dtype=torch.int32, device=self.ctx.device)[:f.m]
+        self.ctx.check(lib().sfg_hierarchy_map(self.ctx.h, self.h, level, _ptr(agg), _ptr(f2c)))
+        return agg, f2c
+
+    def mask(self, level):
+        """P_level over G_level's canonical edges."""
+        g = self.graphs[level]
+        out = torch.empty(max(g.m, 1), dtype=torch.uint8, device=self.ctx.device)[:g.m]
+        self.ctx.check(lib().sfg_hierarchy_mask(self.ctx.h, self.h, level, _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sfg_hierarchy_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _BorrowedGraph(Graph):
+    """A graph owned by a hierarchy (never destroyed through this handle)."""
+
+    def __init__(self, h, owner):
+        self.owner = owner
+        super().__init__(owner.ctx, h)
+
+    def close(self):
+        self.h = None
+
+
 def sfg_sparsify(ctx, g, K=8, steps=10, levels=0, omega=0.7, seed=0, mode=SFG_SCORE_RATIO,
                  budget_frac=0.1, budget_unit=1, storage=torch.float32, out=None,
-                 smoother=SFG_SMOOTH_JACOBI):
+                 smoother=SFG_SMOOTH_JACOBI, hierarchy=False):
+    """Returns (mask, edges in P), plus a Hierarchy when hierarchy=True."""
     p = sfg_params(K, steps, levels, omega, seed & (2**64 - 1), mode, budget_frac, budget_unit,
                    _dt(storage), smoother)
     if out is None:
         out = torch.empty(g.m, dtype=torch.uint8, device=ctx.device)
     ns = _i64()
-    ctx.check(lib().sfg_sparsify(ctx.h, g.h, ctypes.byref(p), _ptr(out), ctypes.byref(ns)))
+    hp = _vp()
+    ctx.check(lib().sfg_sparsify(ctx.h, g.h, ctypes.byref(p), _ptr(out), ctypes.byref(ns),
+                                 ctypes.byref(hp) if hierarchy else None))
+    if hierarchy:
+        return out, ns.value, Hierarchy(ctx, hp, g)
     return out, ns.value
 
 
@@ -532,3 +607,47 @@ def sfg_tune_table(ctx):
     buf = ctypes.create_string_buffer(n.value + 1)
     ctx.check(lib().sfg_tune_table(ctx.h, buf, n.value + 1, ctypes.byref(n)))
     return json.loads(buf.value.decode())
+
+
+class Batch:
+    """Owner of an sfg_batch plan (see include/sfg.h): build once, run many times."""
+
+    def __init__(self, ctx, graphs, K=16, steps=15, omega=0.7, mode=SFG_SCORE_RATIO,
+                 budget_frac=0.05, budget_unit=0, storage=torch.float32, autotune=False):
+        self.ctx = ctx
+        p = sfg_params(K, steps, 0, omega, 0, mode, budget_frac, budget_unit, _dt(storage),
+                       SFG_SMOOTH_JACOBI)
+        arr = (_vp * len(graphs))(*[g.h for g in graphs])
+        h = _vp()
+        ctx.check(lib().sfg_batch_create(ctx.h, len(graphs), arr, ctypes.byref(p),
+                                         1 if autotune else 0, ctypes.byref(h)))
+        self.h = h
+        ng, m = _int(), _i64()
+        offs = (ctypes.c_int64 * (len(graphs) + 1))()
+        cnt = (ctypes.c_int64 * len(graphs))()
+        ctx.check(lib().sfg_batch_info(h, ctypes.byref(ng), ctypes.byref(m),
+                                       ctypes.cast(offs, _pi64), ctypes.cast(cnt, _pi64)))
+        self.ng, self.m = ng.value, m.value
+        self.offsets = list(offs)
+        self.counts = list(cnt)
+
+    def run(self, seed, out=None):
+        """All graphs' sparsifiers for one seed, as one mask over the concatenated edge lists."""
+        if out is None:
+            out = torch.empty(max(self.m, 1), dtype=torch.uint8, device=self.ctx.device)[:self.m]
+        self.ctx.check(lib().sfg_batch_run(self.ctx.h, self.h, seed & (2**64 - 1), _ptr(out)))
+        return out
+
+    def split(self, mask):
+        return [mask[self.offsets[g]:self.offsets[g + 1]] for g in range(self.ng)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sfg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,84 @@
+"""The batch plan (sfg_batch_create / sfg_batch_run): the batched flat method with its
+graph-dependent part built once and its numeric part run without host synchronisation, so that a
+run can be captured in a CUDA graph and replayed."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2008_07633_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2008_07633_gb300.sfg as S
+
+    S.lib()
+    return S
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _specs():
+    rng = np.random.default_rng(91)
+    specs = [gen.knn3d(int(np.exp(rng.uniform(np.log(300), np.log(3000)))), k=10, seed=500 + i)
+             for i in range(12)]
+    specs.append(gen.hub_graph(seed=33))                                   # rows over 256 entries
+    specs.append(gen.random_graph(700, 1500, seed=12, connected=False))    # forest + isolated nodes
+    specs.append(gen.path(40, weights="uniform"))                          # a tree: nothing to add
+    return specs
+
+
+def test_batch_plan_matches_sparsify_batched(S):
+    ctx = S.sfg_ctx_create(0)
+    gs = [S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w)) for n, u, v, w in _specs()]
+    kw = dict(K=16, steps=15, budget_frac=0.05)
+    masks, counts = S.sfg_sparsify_batched(ctx, gs, seed=7, **kw)
+    plan = S.Batch(ctx, gs, **kw)
+    assert plan.ng == len(gs) and plan.m == sum(g.m for g in gs)
+    assert plan.counts == list(counts)
+    out = plan.run(7)
+    for mb, part, c in zip(masks, plan.split(out), plan.counts):
+        assert torch.equal(mb, part)
+        assert int(part.sum().item()) == c
+    # a second seed gives another sparsifier of the same sizes
+    other = plan.run(8)
+    assert [int(p.sum().item()) for p in plan.split(other)] == plan.counts
+    assert not torch.equal(other, out)
+
+
+def test_batch_run_captured_in_a_cuda_graph(S):
+    stream = torch.cuda.Stream()
+    ctx = S.sfg_ctx_create(0, stream)
+    with torch.cuda.stream(stream):
+        gs = [S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w)) for n, u, v, w in _specs()]
+        plan = S.Batch(ctx, gs, K=32, steps=12, budget_frac=0.05, autotune=True)
+        ref = plan.run(11)
+        out = torch.empty_like(ref)
+    stream.synchronize()
+    for g in gs:          # the plan keeps its own copy of the graphs
+        g.close()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        plan.run(11, out=out)
+    for _ in range(3):
+        out.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+
+
+def test_batch_plan_rejects_bad_arguments(S):
+    ctx = S.sfg_ctx_create(0)
+    n, u, v, w = gen.grid2d(8, 8)
+    g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
+    with pytest.raises(S.SfgError) as e:
+        S.Batch(ctx, [g], K=12)
+    assert e.value.status == 6
+    with pytest.raises(S.SfgError) as e:
+        S.Batch(ctx, [g], omega=1.5)
+    assert e.value.status == 1
