@@ -285,8 +285,9 @@ enum { SFG_SMOOTH_JACOBI = 0, SFG_SMOOTH_GAUSS_SEIDEL = 1 };
 
 /* The method (Algorithm 1 of Sec. 3.6: graph in; sparsifier and coarsening hierarchy out).
  * mask_out[e] (m entries) = 1 for the edges of the sparsifier P of G. Flat: maximum spanning
- * forest, then the top-scored off-tree edges. Multilevel: coarsen `levels` times (each level
- * embedded in params->storage; stopping early if a level has no edges left), sparsify the
+ * forest, then the top-scored off-tree edges. Multilevel: coarsen `levels` times (the
+ * aggregation always from FP32 embeddings, so params->storage changes only the edge-recovery
+ * blocks; stopping early if a level has no edges left), sparsify the
  * coarsest graph flat, then at each finer level map the sparsifier back (sfg_backward_map),
  * re-embed, score the edges outside it and add the top ones. Budget at each level: the level's
  * sparsifier gets round-half-up(beta * base) edges beyond N_l - c_l (c_l = number of components),
@@ -358,8 +359,9 @@ SFG_API void sfg_batch_destroy(sfg_batch* b);
  * remaining core by preconditioned CG to a relative residual of 1e-13 of its own right-hand side
  * or 1e-12 of the whole one (not in the paper: its experiments report kappa but not how it is
  * computed). The iteration stops early when the Krylov space is exhausted (beta below 1e-10 of
- * the largest alpha, a vanishing residual, or a core solve that fails after the first step, which
- * happens only on a right-hand side made of rounding noise). kappa_host receives kappa (+infinity
+ * the largest alpha, a vanishing residual, or a core solve that fails once at least half of the
+ * Krylov dimension has been explored, which happens on a right-hand side made of rounding noise).
+ * kappa_host receives kappa (+infinity
  * if P does not span every component of G; 1 if G has no edges). lambda_min is exactly 1 when
  * G \ P has more components than G (L_G >= L_P, with equality on the vectors that are constant on
  * the components of G \ P); that case is detected and used instead of the Ritz value. info_host
@@ -367,7 +369,8 @@ SFG_API void sfg_batch_destroy(sfg_batch* b);
  * iterations in all, 1 if the last step ended on a failed core solve else 0, 1 if lambda_min = 1
  * was certified by the component count else 0}. Deterministic. Errors: SFG_EINVAL
  * (bad arguments), SFG_ENOMEM (it keeps 2 (steps + 1) FP64 vectors of n entries), SFG_ETIMEOUT
- * (the core CG did not converge on the first step). Synchronises. */
+ * (the core CG did not converge before half of the Krylov dimension: a core too ill-conditioned
+ * for CG at the tolerance; no kappa is returned then). Synchronises. */
 SFG_API sfg_status sfg_kappa(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int steps,
                              uint64_t seed, double* kappa_host, double* info_host);
 
@@ -429,11 +432,22 @@ SFG_API void sfg_mlp_destroy(sfg_mlp* net);
 /* Copy the FP32 parameters out / in (set also clears the Adam state). */
 SFG_API sfg_status sfg_mlp_params(sfg_ctx* ctx, const sfg_mlp* net, float* theta_out);
 SFG_API sfg_status sfg_mlp_set_params(sfg_ctx* ctx, sfg_mlp* net, const float* theta);
-/* out[i] = network output for feature row i (ne rows). */
+/* out[i] = network output for feature row i (ne rows), on the tcgen05 tensor cores. Queued
+ * without synchronisation (it can be captured in a CUDA graph); every completion wait inside the
+ * kernel is bounded by a clock, and a wait that runs out is reported by the next sfg_mlp_check
+ * (or by a synchronising call of the network: sfg_mlp_gradient / sfg_mlp_train with loss_host,
+ * sfg_sparsify_learned) as SFG_ETIMEOUT. */
 SFG_API sfg_status sfg_mlp_forward(sfg_ctx* ctx, const sfg_mlp* net, const float* feats,
                                    int64_t ne, float* out);
+/* Synchronise ctx's stream; SFG_ETIMEOUT (once) if a bounded completion wait of this network's
+ * tensor-core kernels ran out since the last check, else SFG_OK. */
+SFG_API sfg_status sfg_mlp_check(sfg_ctx* ctx, const sfg_mlp* net);
 /* Gradient of mean((y - targets)^2) over the ne rows (grad_out: SFG_MLP_NPARAM FP32, may be
- * NULL); loss_host (may be NULL) receives the loss and synchronises. */
+ * NULL); loss_host (may be NULL) receives the loss and synchronises. Forward and backward run on
+ * the tcgen05 tensor cores, 128 rows per tile: BF16 operands (features, W1, W2, the first hidden
+ * layer and the two backward deltas), FP32 accumulation in TMEM; the weight gradients contract
+ * over each tile's rows and accumulate in TMEM across the tiles of a CTA, the CTAs' partial
+ * gradients are added in a fixed order (deterministic). */
 SFG_API sfg_status sfg_mlp_gradient(sfg_ctx* ctx, sfg_mlp* net, const float* feats,
                                     const float* targets, int64_t ne, float* grad_out,
                                     double* loss_host);

@@ -89,6 +89,26 @@ def forward(theta, X):
     return y, (z1, h1, z2, h2)
 
 
+def round_bf16(a):
+    """Round to the nearest BF16 number, ties to even (the upper 16 bits of the FP32 pattern after
+    adding 0x7fff plus the lowest kept bit), returned as float64."""
+    f = np.asarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_kernel_precision(theta, X):
+    """The network with the library's BF16 rounding points -- features, W1, W2 and the first
+    hidden layer rounded to BF16, everything else exact: the precision in which the library's
+    tensor-core kernels take the proposal decision."""
+    p = unflatten(theta)
+    z1 = round_bf16(X) @ round_bf16(p["W1"]) + p["b1"]
+    h1 = round_bf16(np.maximum(z1, 0.0))
+    z2 = h1 @ round_bf16(p["W2"]) + p["b2"]
+    return np.maximum(z2, 0.0) @ p["w3"] + p["b3"][0]
+
+
 def loss(theta, X, t):
     y, _ = forward(theta, X)
     return float(np.mean((y - t) ** 2))

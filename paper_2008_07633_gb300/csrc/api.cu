@@ -184,6 +184,7 @@ sfg_status sfg_ctx_create(sfg_ctx** out, int device, void* cuda_stream) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (c->num_sms < 1) c->num_sms = 1;
     if (const char* f = std::getenv("SFG_FAULT_ALLOC")) c->fail_alloc_at = std::atoll(f);
+    if (const char* f = std::getenv("SFG_FAULT_MMA_WAIT")) c->withhold_mma = std::atoi(f) != 0;
     c->pool = device_pool(device);
     if (!c->pool) {
         delete c;

@@ -944,6 +944,7 @@ sfg_status kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int
     Scratch s(ctx);
     int32_t* root = nullptr;
     bool lmin_exact = false;
+    int64_t kdim = 0;  // dimension of the Krylov space: n minus the components of G
     {  // P must span every component of G, else kappa is infinite
         uint8_t* tm;
         SFG_TRY(s.get(&tm, G->m));
@@ -958,6 +959,7 @@ sfg_status kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int
             return SFG_OK;
         }
         const int64_t dim = (int64_t)n - ((int64_t)n - tg);  // complement of the null space
+        kdim = dim;
         if (steps > dim) steps = (int)dim;
         // lambda_min = 1 exactly when Q = G \ P has more components than G: L_G = L_P + L_Q >= L_P,
         // and a vector constant on the components of Q but not on those of G has L_G x = L_P x
@@ -1039,10 +1041,12 @@ sfg_status kappa_impl(sfg_ctx* ctx, const sfg_graph* G, const uint8_t* mask, int
         }
         {
             const sfg_status ss = S.solve(r, tmp);
-            // The core CG fails only on an inconsistent right-hand side, i.e. when v_j is
-            // rounding noise after the Krylov space ran out: that is a breakdown, and T_j (without
-            // this step) holds the Ritz values. On the first step it is an error.
-            if (ss == SFG_ETIMEOUT && j > 0) {
+            // A core CG that does not converge once the Krylov space has run out (v_j is rounding
+            // noise: an inconsistent right-hand side) marks a breakdown, and T_j (without this
+            // step) holds the Ritz values. That can only happen late, after at least half of the
+            // Krylov dimension; an earlier failure (a core too ill-conditioned for CG to reach
+            // the tolerance) is reported as an error instead of a kappa from a truncated space.
+            if (ss == SFG_ETIMEOUT && j > 0 && 2 * (int64_t)(j + 1) >= kdim) {
                 stop_cg = true;
                 break;
             }

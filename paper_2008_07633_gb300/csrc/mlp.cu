@@ -1,17 +1,10 @@
 // Learned edge-proposal scorer (an addition to the paper's method; the proposals it makes are
-// rescored by the plain method before selection): per-edge features from a short embedding, a 16 -> 64 -> 64 -> 1 ReLU network evaluated
-// on the tcgen05 tensor cores (inference, k_mlp_forward_tc below) and trained on BF16 warp-level
-// tensor-core MMA (mma.sync m16n8k16, FP32 accumulation), Adam in FP32.
-//
-// Training forward, per warp and 16 edges: the feature rows are the A operand; layer outputs stay in the
-// accumulator fragments, whose layout is exactly the A-operand layout of the next layer once two
-// n-tiles are packed to BF16, so hidden activations never leave registers. The last layer (64 -> 1)
-// is a dot product folded across the four lanes that share a row.
-// Backward, per CTA (4 warps, 64 edges): delta_1 = delta_2 W2^T reuses the same register trick
-// with a fragment copy of W2^T; the weight gradients H1^T delta_2 and X^T delta_1 contract over
-// the edges, so the warps stage H1, delta_2, delta_1 and X in shared memory and read transposed
-// operands with ldmatrix.trans. Every CTA writes its own partial gradient; a second kernel folds
-// the partials in a fixed order, so gradients are deterministic.
+// rescored by the plain method before selection): per-edge features from a short embedding and a
+// 16 -> 64 -> 64 -> 1 ReLU network, evaluated (k_mlp_forward_tc) and trained (k_mlp_fwdbwd_tc,
+// forward and backward) on the 5th-generation tensor cores: BF16 operands in shared memory, FP32
+// accumulators in TMEM, completion through mbarriers with bounded waits. Adam in FP32 on the
+// CUDA cores. Every CTA of the training kernel writes its own partial gradient and a second
+// kernel folds the partials in a fixed order, so gradients are deterministic.
 #include "sfg_internal.cuh"
 
 namespace {
@@ -19,94 +12,10 @@ namespace {
 constexpr int kF = 16, kH = 64;
 constexpr int OFF_W1 = 0, OFF_B1 = 1024, OFF_W2 = 1088, OFF_B2 = 5184, OFF_W3 = 5248,
               OFF_B3 = 5312, NP = 5313;
-constexpr int kMlpBlock = 128;  // 4 warps
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
-}
-
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void* smem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(s));
-}
-
-struct Net {  // device pointers of one network
-    const float* theta;
-    const uint2* w1f;   // [8 n-tiles][32 lanes]
-    const uint2* w2f;   // [8 n-tiles][4 k-steps][32 lanes]
-    const uint2* w2tf;  // B fragments of W2^T, same shape
-};
-
-// Forward of 16 edges [e0, e0 + 16) of a warp. x: feature rows (FP32, 16 per row). Returns the
-// post-ReLU layer outputs in accumulator layout (rows g and g + 8, columns 8j + 2t + {0, 1}) and
-// y for rows g, g + 8 (valid in all four lanes of the row).
-struct Tile {
-    float h1[8][4], h2[8][4];
-    uint32_t a1[4];
-    float y0, y1;
-};
-
-__device__ __forceinline__ void forward_tile(const Net& net, const float* __restrict__ x,
-                                             int64_t e0, int64_t ne, Tile& T) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int64_t r0 = min(e0 + g, ne - 1), r1 = min(e0 + g + 8, ne - 1);
-    const float2 x00 = *reinterpret_cast<const float2*>(x + r0 * kF + 2 * t);
-    const float2 x10 = *reinterpret_cast<const float2*>(x + r1 * kF + 2 * t);
-    const float2 x01 = *reinterpret_cast<const float2*>(x + r0 * kF + 8 + 2 * t);
-    const float2 x11 = *reinterpret_cast<const float2*>(x + r1 * kF + 8 + 2 * t);
-    T.a1[0] = pack_bf16(x00.x, x00.y);
-    T.a1[1] = pack_bf16(x10.x, x10.y);
-    T.a1[2] = pack_bf16(x01.x, x01.y);
-    T.a1[3] = pack_bf16(x11.x, x11.y);
-    const float* b1 = net.theta + OFF_B1;
-    const float* b2 = net.theta + OFF_B2;
-    const float* w3 = net.theta + OFF_W3;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float c0 = b1[8 * j + 2 * t], c1 = b1[8 * j + 2 * t + 1];
-        T.h1[j][0] = c0; T.h1[j][1] = c1; T.h1[j][2] = c0; T.h1[j][3] = c1;
-        mma16816(T.h1[j], T.a1, net.w1f[j * 32 + lane]);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) T.h1[j][c] = fmaxf(T.h1[j][c], 0.f);
-    }
-    uint32_t a2[4][4];
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        a2[kk][0] = pack_bf16(T.h1[2 * kk][0], T.h1[2 * kk][1]);
-        a2[kk][1] = pack_bf16(T.h1[2 * kk][2], T.h1[2 * kk][3]);
-        a2[kk][2] = pack_bf16(T.h1[2 * kk + 1][0], T.h1[2 * kk + 1][1]);
-        a2[kk][3] = pack_bf16(T.h1[2 * kk + 1][2], T.h1[2 * kk + 1][3]);
-    }
-    float y0 = 0.f, y1 = 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float c0 = b2[8 * j + 2 * t], c1 = b2[8 * j + 2 * t + 1];
-        T.h2[j][0] = c0; T.h2[j][1] = c1; T.h2[j][2] = c0; T.h2[j][3] = c1;
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) mma16816(T.h2[j], a2[kk], net.w2f[(j * 4 + kk) * 32 + lane]);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) T.h2[j][c] = fmaxf(T.h2[j][c], 0.f);
-        const float v0 = w3[8 * j + 2 * t], v1 = w3[8 * j + 2 * t + 1];
-        y0 = fmaf(T.h2[j][0], v0, fmaf(T.h2[j][1], v1, y0));
-        y1 = fmaf(T.h2[j][2], v0, fmaf(T.h2[j][3], v1, y1));
-    }
-    y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
-    y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
-    y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
-    y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
-    T.y0 = y0 + net.theta[OFF_B3];
-    T.y1 = y1 + net.theta[OFF_B3];
 }
 
 // ---- inference on the 5th-generation tensor cores (tcgen05, accumulators in TMEM) ----
@@ -122,7 +31,7 @@ __device__ __forceinline__ void forward_tile(const Net& net, const float* __rest
 //   H1 = BF16(ReLU(D)) in one cvt.rn.relu.bf16x2 per column pair, written over chunks 0-3
 //   layer 2: D = [H1 | 1 1 0..] [W2 ; b2_hi ; b2_lo ; 0..]          (5 MMAs)
 //   y = sum_j ReLU(D_j) w3_j + b3 in FP32 by the owning thread.
-// BF16 rounding points: features, W1, W2, H1 (as in the warp-level kernel). Completion of each MMA
+// BF16 rounding points: features, W1, W2, H1. Completion of each MMA
 // group is signalled through an mbarrier by tcgen05.commit; every wait on it is bounded.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -149,13 +58,23 @@ __device__ __forceinline__ void umma_commit(uint64_t* mbar) {
                  :: "r"(smem_u32(mbar)) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the mbarrier phase, giving up after about two seconds
+__device__ __forceinline__ bool mbar_wait_timed(uint64_t* mbar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
     uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; ++it)
+    while (true) {
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
-    return done != 0;
+        if (done) return true;
+        if (global_ns() - t0 > 2000000000ull) return false;
+    }
 }
 
 // 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread)
@@ -198,7 +117,8 @@ constexpr int kKB1 = 32; // K of layer 1's B: W1 (16) + bias chunk (16)
 
 __global__ void __launch_bounds__(128, 6) k_mlp_forward_tc(const float* __restrict__ theta,
                                                          const float* __restrict__ x, int64_t ne,
-                                                         float* __restrict__ out, int* __restrict__ err) {
+                                                         float* __restrict__ out, int* __restrict__ err,
+                                                         int withhold) {
     __shared__ __align__(1024) __nv_bfloat16 sA[128 * kKA];   // 20 KB
     __shared__ __align__(1024) __nv_bfloat16 sB1[kH * kKB1];  // W1 and b1 as N x K, 4 KB
     __shared__ __align__(1024) __nv_bfloat16 sB2[kH * kKA];   // W2 and b2 as N x K, 10 KB
@@ -268,12 +188,12 @@ __global__ void __launch_bounds__(128, 6) k_mlp_forward_tc(const float* __restri
         if (tile + gridDim.x < ntiles) load_row(tile + gridDim.x);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_sync();  // also orders the previous tile's TMEM reads before this tile's MMAs
-        if (tid == 0) {
+        if (tid == 0 && !withhold) {
             umma_f16(tmem, umma_desc(a0, 128, kSboA), umma_desc(b10, 128, kSboB1), 0);
             umma_f16(tmem, umma_desc(a0 + 256 * 4, 128, kSboA), umma_desc(b10 + 256, 128, kSboB1), 1);
             umma_commit(&mbar);
         }
-        ok = __syncthreads_and(mbar_wait(&mbar, phase));  // one decision for the whole CTA
+        ok = __syncthreads_and(mbar_wait_timed(&mbar, phase));  // one decision for the whole CTA
         phase ^= 1;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -290,13 +210,13 @@ __global__ void __launch_bounds__(128, 6) k_mlp_forward_tc(const float* __restri
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_sync();
-        if (tid == 0) {
+        if (tid == 0 && !withhold) {
 #pragma unroll
             for (int c = 0; c < kKA / 16; ++c)
                 umma_f16(tmem, umma_desc(a0 + 256 * c, 128, kSboA), umma_desc(b20 + 256 * c, 128, kSboA), c > 0);
             umma_commit(&mbar);
         }
-        ok = __syncthreads_and(mbar_wait(&mbar, phase));
+        ok = __syncthreads_and(mbar_wait_timed(&mbar, phase));
         phase ^= 1;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -316,185 +236,303 @@ __global__ void __launch_bounds__(128, 6) k_mlp_forward_tc(const float* __restri
         }
         if (row < ne) out[row] = y + b3;
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok && tid == 0) {
+        atomicExch(err, 1);
+        mbar_wait_timed(&mbar, phase ^ 1);  // the group in flight completes before TMEM is released
+    }
     tc_sync();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(64) : "memory");
 }
 
 
-constexpr int kS64 = 72;  // shared-memory row stride (BF16) of the 64-wide tiles
-constexpr int kS16 = 24;  // and of the 16-wide feature tile
+// ---- training on the 5th-generation tensor cores ----
+// Gradient of L = (1/ne) sum (y - t)^2, one CTA of 128 threads per 128-edge tile (thread r owns
+// edge row r = TMEM lane r), the tiles of a CTA in grid-stride order. Shared-memory operands, all
+// BF16 in the K-major, non-swizzled core-matrix layout (8 rows x 16 bytes per core matrix):
+//   sA  (128 x 96): H1 (columns 0-63) | X, the features (64-79) | constant chunk (1, 1, 0, ..) (80-95)
+//   sD  (128 x 128): delta_2 (columns 0-63) | delta_1 (64-127)
+//   sB1 (64 x 32): layer-1 B, (n = unit, k) = [W1 | b1_hi, b1_lo, 0 ..]
+//   sB2 (64 x 96): layer-2 B, (n = unit j, k) = [W2 (k = i) | 0 (facing X) | b2_hi, b2_lo, 0 ..]
+//   sB2T (64 x 64): (n = i, k = j) = W2[i][j], the B operand of delta_1 = delta_2 W2^T
+// Per tile, each step an MMA group signalled through one mbarrier (waits bounded by a clock):
+//   z1 = [X | 1] [W1; b1]               (A = sA columns 64-95, K = 32)   -> TMEM columns 0-63
+//   H1 = BF16(ReLU(z1)) into sA; z2 = [H1 | X | 1] [W2; 0; b2]  (K = 96) -> TMEM columns 0-63
+//   y = ReLU(z2) w3 + b3 (FP32, per thread); delta_3 = 2 (y - t) / ne; delta_2 = delta_3 w3 (.) [z2 > 0]
+//   delta_1 = (delta_2 W2^T) (.) [z1 > 0]        (A = sD columns 0-63)   -> TMEM columns 0-63
+//   G += [delta_2 | delta_1]^T [H1 | X | 1]      (K = the tile's 128 rows) -> TMEM columns 64-159
+// The last product reads sD and sA as MN-major operands (the rows of the tile are its K), so the
+// weight gradients need no transposed copies: G rows 0-63 (j) x columns 0-63 (i) = dW2[i][j],
+// column 80 = db2[j]; G rows 64-127 (i) x columns 64-79 (f) = dW1[f][i], column 80 = db1[i]. G
+// accumulates over the CTA's tiles in TMEM; dw3 = sum h2 delta_3 and db3 = sum delta_3 accumulate
+// per thread in FP32. Each CTA writes its partial gradient; k_mlp_fold adds them in CTA order.
+// BF16 rounding points: features, W1, W2, H1, delta_2, delta_1 (as in the inference kernel).
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, operand majors (0: K-major, 1: MN-major)
+// at bits 15 (A) and 16 (B), N / 8 at bit 17, M / 16 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int a_mn, int b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
-// Gradient of L = (1/ne) sum (y - t)^2 over [0, ne): one partial per CTA, part[cta][NP + 1]
-// (the last entry is the CTA's sum of squared errors).
-__global__ void __launch_bounds__(kMlpBlock) k_mlp_fwdbwd(Net net, const float* __restrict__ x,
-                                                          const float* __restrict__ target,
-                                                          int64_t ne, float* __restrict__ part) {
-    __shared__ __align__(16) __nv_bfloat16 sH1[64 * kS64];
-    __shared__ __align__(16) __nv_bfloat16 sD2[64 * kS64];
-    __shared__ __align__(16) __nv_bfloat16 sD1[64 * kS64];
-    __shared__ __align__(16) __nv_bfloat16 sX[64 * kS16];
-    __shared__ float sred[4][3 * kH + 2];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    const float* w3 = net.theta + OFF_W3;
+__device__ __forceinline__ void umma_f16_id(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                            uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+}
+
+// Descriptor of an MN-major operand (no swizzle): the byte step between 8-row groups along K goes
+// in the leading-byte-offset field and the step between 8-element groups along M (or N) in the
+// stride-byte-offset field -- the roles the two fields have for a K-major operand swapped.
+__device__ __forceinline__ uint64_t umma_desc_mn(uint32_t addr, uint32_t mn, uint32_t kg) {
+    return umma_desc(addr, kg, mn);
+}
+
+constexpr int kTA = 96, kTD = 128, kTB1 = 32;
+constexpr int kTColsTmem = 256;  // layer accumulator (64) + gradient (96), rounded to a power of two
+constexpr size_t kTrainSmA = 128 * kTA * 2, kTrainSmD = 128 * kTD * 2, kTrainSmB1 = kH * kTB1 * 2,
+                 kTrainSmB2 = kH * kTA * 2, kTrainSmB2T = kH * kH * 2;
+constexpr size_t kTrainSmem = kTrainSmA + kTrainSmD + kTrainSmB1 + kTrainSmB2 + kTrainSmB2T + 1024;  // + alignment
+
+__global__ void __launch_bounds__(128, 2)
+    k_mlp_fwdbwd_tc(const float* __restrict__ theta, const float* __restrict__ x,
+                    const float* __restrict__ target, int64_t ne, float* __restrict__ part,
+                    int* __restrict__ err, int withhold) {
+    extern __shared__ __align__(1024) uint8_t dsm[];
+    uint8_t* base = dsm + ((1024 - (smem_u32(dsm) & 1023)) & 1023);  // 1024-byte aligned
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* sD = reinterpret_cast<__nv_bfloat16*>(base + kTrainSmA);
+    __nv_bfloat16* sB1 = reinterpret_cast<__nv_bfloat16*>(base + kTrainSmA + kTrainSmD);
+    __nv_bfloat16* sB2 = reinterpret_cast<__nv_bfloat16*>(base + kTrainSmA + kTrainSmD + kTrainSmB1);
+    __nv_bfloat16* sB2T = reinterpret_cast<__nv_bfloat16*>(base + kTrainSmA + kTrainSmD + kTrainSmB1 + kTrainSmB2);
+    __shared__ __align__(16) float sw3[kH];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_base)), "r"(kTColsTmem) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    auto split = [](float b, bool lo) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+        return lo ? __float2bfloat16_rn(b - __bfloat162float(hi)) : hi;
+    };
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    for (int i = tid; i < kH * kTB1; i += 128) {
+        const int h = i / kTB1, k = i % kTB1;
+        sB1[core_idx<kTB1>(h, k)] = k < kF ? __float2bfloat16_rn(theta[OFF_W1 + k * kH + h])
+                                  : k < kF + 2 ? split(theta[OFF_B1 + h], k == kF + 1) : zero;
+    }
+    for (int i = tid; i < kH * kTA; i += 128) {
+        const int j = i / kTA, k = i % kTA;
+        sB2[core_idx<kTA>(j, k)] = k < kH ? __float2bfloat16_rn(theta[OFF_W2 + k * kH + j])
+                                 : (k == 80 || k == 81) ? split(theta[OFF_B2 + j], k == 81) : zero;
+    }
+    for (int i = tid; i < kH * kH; i += 128) {
+        const int a = i / kH, b = i % kH;   // (n = i, k = j) = W2[i][j]
+        sB2T[core_idx<kH>(a, b)] = __float2bfloat16_rn(theta[OFF_W2 + a * kH + b]);
+    }
+    if (tid < kH) sw3[tid] = theta[OFF_W3 + tid];
+    {   // this row's constant chunk (1, 1, 0, ..., 0) at columns 80-95
+        const uint32_t one2 = pack_bf16(1.f, 1.f);
+        *reinterpret_cast<uint4*>(&sA[core_idx<kTA>(tid, 80)]) = make_uint4(one2, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(&sA[core_idx<kTA>(tid, 88)]) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const float b3 = theta[OFF_B3];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const uint32_t acc_z = tmem + lane_off, acc_g = tmem + lane_off + 64;
+    const uint32_t a0 = smem_u32(sA), d0 = smem_u32(sD), b10 = smem_u32(sB1), b20 = smem_u32(sB2),
+                   bt0 = smem_u32(sB2T);
+    constexpr uint32_t kSboA = kTA / 8 * 128, kSboD = kTD / 8 * 128, kSboB1 = kTB1 / 8 * 128,
+                       kSboB2T = kH / 8 * 128;
+    constexpr uint32_t kId1 = idesc_f16(128, 64, 0, 0), kIdG = idesc_f16(128, 96, 1, 1);
+    uint32_t phase = 0;
+    bool ok = true;
     const float inv_n = 1.0f / (float)ne;
-    float acc2[8][4], acc1[2][4];
-    float db1[16], db2[16], dw3[16];
+    float gw3[kH];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < kH; ++j) gw3[j] = 0.f;
+    float gb3 = 0.f, sse = 0.f;
+    const int64_t ntiles = (ne + 127) / 128;
+    float4 f[4];
+    auto load_row = [&](int64_t tile) {
+        const float4* xr = reinterpret_cast<const float4*>(x + min(tile * 128 + tid, ne - 1) * kF);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc2[j][c] = 0.f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc1[0][c] = acc1[1][c] = 0.f;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) db1[i] = db2[i] = dw3[i] = 0.f;
-    float db3 = 0.f, sse = 0.f;
-
-    for (int64_t c0 = (int64_t)blockIdx.x * 64; c0 < ne; c0 += (int64_t)gridDim.x * 64) {
-        const int64_t e0 = c0 + warp * 16;
-        Tile T;
-        forward_tile(net, x, e0, ne, T);
-        const bool v0 = e0 + g < ne, v1 = e0 + g + 8 < ne;
-        const float r0 = v0 ? T.y0 - target[e0 + g] : 0.f;
-        const float r1 = v1 ? T.y1 - target[e0 + g + 8] : 0.f;
-        if (t == 0) {
-            sse = fmaf(r0, r0, fmaf(r1, r1, sse));
-            db3 += 2.f * (r0 + r1) * inv_n;
+        for (int c = 0; c < 4; ++c) f[c] = xr[c];
+    };
+    auto step = [&](auto&& issue) {  // one MMA group: issue, commit, bounded wait (CTA-wide)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+        if (tid == 0 && !withhold) {
+            issue();
+            umma_commit(&mbar);
         }
-        const float d30 = 2.f * r0 * inv_n, d31 = 2.f * r1 * inv_n;
-        // delta_2 = delta_3 w3 (.) [z2 > 0]; db2, dw3
-        float d2[8][4];
+        ok = __syncthreads_and(mbar_wait_timed(&mbar, phase));
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return ok;
+    };
+    int done_tiles = 0;
+    if ((int64_t)blockIdx.x < ntiles) load_row(blockIdx.x);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++done_tiles) {
+        const int64_t row = tile * 128 + tid;
+        const bool valid = row < ne;
+        const float tgt = valid ? target[row] : 0.f;
+        // features -> BF16 at columns 64-79 (the previous tile's gradient product has completed)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float v0w = w3[8 * j + 2 * t], v1w = w3[8 * j + 2 * t + 1];
-            dw3[2 * j] += T.h2[j][0] * d30 + T.h2[j][2] * d31;
-            dw3[2 * j + 1] += T.h2[j][1] * d30 + T.h2[j][3] * d31;
-            d2[j][0] = T.h2[j][0] > 0.f ? d30 * v0w : 0.f;
-            d2[j][1] = T.h2[j][1] > 0.f ? d30 * v1w : 0.f;
-            d2[j][2] = T.h2[j][2] > 0.f ? d31 * v0w : 0.f;
-            d2[j][3] = T.h2[j][3] > 0.f ? d31 * v1w : 0.f;
-            db2[2 * j] += d2[j][0] + d2[j][2];
-            db2[2 * j + 1] += d2[j][1] + d2[j][3];
+        for (int c = 0; c < 2; ++c)
+            *reinterpret_cast<uint4*>(&sA[core_idx<kTA>(tid, 64 + 8 * c)]) =
+                make_uint4(pack_bf16(f[2 * c].x, f[2 * c].y), pack_bf16(f[2 * c].z, f[2 * c].w),
+                           pack_bf16(f[2 * c + 1].x, f[2 * c + 1].y), pack_bf16(f[2 * c + 1].z, f[2 * c + 1].w));
+        if (tile + gridDim.x < ntiles) load_row(tile + gridDim.x);
+        // layer 1: [X | 1] [W1; b1]
+        if (!step([&] {
+                umma_f16_id(tmem, umma_desc(a0 + 8 * 128, 128, kSboA), umma_desc(b10, 128, kSboB1), kId1, 0);
+                umma_f16_id(tmem, umma_desc(a0 + 10 * 128, 128, kSboA), umma_desc(b10 + 256, 128, kSboB1), kId1, 1);
+            }))
+            break;
+        uint32_t m1[2] = {0u, 0u};  // z1 > 0, one bit per hidden unit
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float v[32];
+            tmem_ld32(acc_z + 32 * half, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) m1[half] |= (v[i] > 0.f ? 1u : 0u) << i;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                *reinterpret_cast<uint4*>(&sA[core_idx<kTA>(tid, 32 * half + 8 * c)]) =
+                    make_uint4(relu_bf16x2(v[8 * c], v[8 * c + 1]), relu_bf16x2(v[8 * c + 2], v[8 * c + 3]),
+                               relu_bf16x2(v[8 * c + 4], v[8 * c + 5]), relu_bf16x2(v[8 * c + 6], v[8 * c + 7]));
         }
-        uint32_t ad2[4][4];
+        // layer 2: [H1 | X | 1] [W2; 0; b2]
+        if (!step([&] {
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            ad2[kk][0] = pack_bf16(d2[2 * kk][0], d2[2 * kk][1]);
-            ad2[kk][1] = pack_bf16(d2[2 * kk][2], d2[2 * kk][3]);
-            ad2[kk][2] = pack_bf16(d2[2 * kk + 1][0], d2[2 * kk + 1][1]);
-            ad2[kk][3] = pack_bf16(d2[2 * kk + 1][2], d2[2 * kk + 1][3]);
-        }
-        // delta_1 = (delta_2 W2^T) (.) [z1 > 0]; db1
-        float d1[8][4];
+                for (int c = 0; c < kTA / 16; ++c)
+                    umma_f16_id(tmem, umma_desc(a0 + 256 * c, 128, kSboA), umma_desc(b20 + 256 * c, 128, kSboA), kId1, c > 0);
+            }))
+            break;
+        {
+            // two passes over z2 in halves (y needs all of it before delta_2): fewer live registers
+            float y = b3;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+            for (int half = 0; half < 2; ++half) {
+                float z[32];
+                tmem_ld32(acc_z + 32 * half, z);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) d1[j][c] = 0.f;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) mma16816(d1[j], ad2[kk], net.w2tf[(j * 4 + kk) * 32 + lane]);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) d1[j][c] = T.h1[j][c] > 0.f ? d1[j][c] : 0.f;
-            db1[2 * j] += d1[j][0] + d1[j][2];
-            db1[2 * j + 1] += d1[j][1] + d1[j][3];
-        }
-        // stage H1, delta_2, delta_1 and X (BF16) for the contractions over edges
-        const int er0 = warp * 16 + g, er1 = er0 + 8;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int col = 8 * j + 2 * t;
-            *reinterpret_cast<uint32_t*>(&sH1[er0 * kS64 + col]) = v0 ? pack_bf16(T.h1[j][0], T.h1[j][1]) : 0u;
-            *reinterpret_cast<uint32_t*>(&sH1[er1 * kS64 + col]) = v1 ? pack_bf16(T.h1[j][2], T.h1[j][3]) : 0u;
-            *reinterpret_cast<uint32_t*>(&sD2[er0 * kS64 + col]) = pack_bf16(d2[j][0], d2[j][1]);
-            *reinterpret_cast<uint32_t*>(&sD2[er1 * kS64 + col]) = pack_bf16(d2[j][2], d2[j][3]);
-            *reinterpret_cast<uint32_t*>(&sD1[er0 * kS64 + col]) = pack_bf16(d1[j][0], d1[j][1]);
-            *reinterpret_cast<uint32_t*>(&sD1[er1 * kS64 + col]) = pack_bf16(d1[j][2], d1[j][3]);
-        }
-        *reinterpret_cast<uint32_t*>(&sX[er0 * kS16 + 2 * t]) = v0 ? T.a1[0] : 0u;
-        *reinterpret_cast<uint32_t*>(&sX[er1 * kS16 + 2 * t]) = v1 ? T.a1[1] : 0u;
-        *reinterpret_cast<uint32_t*>(&sX[er0 * kS16 + 8 + 2 * t]) = v0 ? T.a1[2] : 0u;
-        *reinterpret_cast<uint32_t*>(&sX[er1 * kS16 + 8 + 2 * t]) = v1 ? T.a1[3] : 0u;
-        __syncthreads();
-        // dW2[j][i] = sum_e H1[e][j] delta_2[e][i]: this warp owns rows j in [16 warp, 16 warp + 16)
-        // dW1[f][j] = sum_e X[e][f] delta_1[e][j]: this warp owns columns j in [16 warp, 16 warp + 16)
-        const int mat = lane >> 3, rr = lane & 7;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-            const int eb = ks * 16;
-            uint32_t a[4];
-            ldsm_x4_trans(a, &sH1[(eb + rr + 8 * (mat >> 1)) * kS64 + warp * 16 + 8 * (mat & 1)]);
-#pragma unroll
-            for (int nt = 0; nt < 8; nt += 2) {
-                uint32_t b[4];
-                ldsm_x4_trans(b, &sD2[(eb + rr + 8 * (mat & 1)) * kS64 + nt * 8 + 8 * (mat >> 1)]);
-                mma16816(acc2[nt], a, make_uint2(b[0], b[1]));
-                mma16816(acc2[nt + 1], a, make_uint2(b[2], b[3]));
+                for (int j = 0; j < 32; ++j) y = fmaf(fmaxf(z[j], 0.f), sw3[32 * half + j], y);
             }
-            uint32_t ax[4], bx[4];
-            ldsm_x4_trans(ax, &sX[(eb + rr + 8 * (mat >> 1)) * kS16 + 8 * (mat & 1)]);
-            ldsm_x4_trans(bx, &sD1[(eb + rr + 8 * (mat & 1)) * kS64 + warp * 16 + 8 * (mat >> 1)]);
-            mma16816(acc1[0], ax, make_uint2(bx[0], bx[1]));
-            mma16816(acc1[1], ax, make_uint2(bx[2], bx[3]));
+            const float r3 = valid ? y - tgt : 0.f;
+            const float d3 = 2.f * r3 * inv_n;
+            sse = fmaf(r3, r3, sse);
+            gb3 += d3;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float z[32];
+                tmem_ld32(acc_z + 32 * half, z);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) gw3[32 * half + j] = fmaf(fmaxf(z[j], 0.f), d3, gw3[32 * half + j]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float d[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        d[e] = z[8 * c + e] > 0.f ? d3 * sw3[32 * half + 8 * c + e] : 0.f;
+                    *reinterpret_cast<uint4*>(&sD[core_idx<kTD>(tid, 32 * half + 8 * c)]) =
+                        make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
+                                   pack_bf16(d[6], d[7]));
+                }
+            }
         }
-        __syncthreads();
+        // delta_1 before the mask: delta_2 W2^T
+        if (!step([&] {
+#pragma unroll
+                for (int c = 0; c < kH / 16; ++c)
+                    umma_f16_id(tmem, umma_desc(d0 + 256 * c, 128, kSboD), umma_desc(bt0 + 256 * c, 128, kSboB2T), kId1, c > 0);
+            }))
+            break;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float v[32];
+            tmem_ld32(acc_z + 32 * half, v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float d[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) d[e] = (m1[half] >> (8 * c + e)) & 1u ? v[8 * c + e] : 0.f;
+                *reinterpret_cast<uint4*>(&sD[core_idx<kTD>(tid, 64 + 32 * half + 8 * c)]) =
+                    make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
+                               pack_bf16(d[6], d[7]));
+            }
+        }
+        // G += [delta_2 | delta_1]^T [H1 | X | 1]: both operands MN-major, K = the 128 rows
+        const bool first = done_tiles == 0;
+        if (!step([&] {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    umma_f16_id(acc_g - lane_off, umma_desc_mn(d0 + 2 * kSboD * c, 128, kSboD),
+                                umma_desc_mn(a0 + 2 * kSboA * c, 128, kSboA), kIdG, (first && c == 0) ? 0u : 1u);
+            }))
+            break;
     }
-
-    // write this CTA's partial gradient
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        // the group in flight (if any) completes before its operands and TMEM are released
+        if (tid == 0) mbar_wait_timed(&mbar, phase ^ 1);
+        tc_sync();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTColsTmem) : "memory");
+        return;
+    }
+    // this CTA's partial gradient
     float* P = part + (size_t)blockIdx.x * (NP + 1);
+    if (done_tiles > 0) {
+        float g0[32], g1[32], g2[32];
+        tmem_ld32(acc_g, g0);
+        tmem_ld32(acc_g + 32, g1);
+        tmem_ld32(acc_g + 64, g2);
+        if (tid < kH) {
+            const int j = tid;
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int j = warp * 16 + g, i = nt * 8 + 2 * t;
-        P[OFF_W2 + j * kH + i] = acc2[nt][0];
-        P[OFF_W2 + j * kH + i + 1] = acc2[nt][1];
-        P[OFF_W2 + (j + 8) * kH + i] = acc2[nt][2];
-        P[OFF_W2 + (j + 8) * kH + i + 1] = acc2[nt][3];
-    }
+            for (int i = 0; i < 32; ++i) {
+                P[OFF_W2 + i * kH + j] = g0[i];
+                P[OFF_W2 + (32 + i) * kH + j] = g1[i];
+            }
+            P[OFF_B2 + j] = g2[16];
+        } else {
+            const int i = tid - kH;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int j = warp * 16 + q * 8 + 2 * t;
-        P[OFF_W1 + g * kH + j] = acc1[q][0];
-        P[OFF_W1 + g * kH + j + 1] = acc1[q][1];
-        P[OFF_W1 + (g + 8) * kH + j] = acc1[q][2];
-        P[OFF_W1 + (g + 8) * kH + j + 1] = acc1[q][3];
-    }
-    // column sums over the rows held by lanes with the same t, then over warps
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-            db1[i] += __shfl_xor_sync(0xffffffffu, db1[i], o);
-            db2[i] += __shfl_xor_sync(0xffffffffu, db2[i], o);
-            dw3[i] += __shfl_xor_sync(0xffffffffu, dw3[i], o);
+            for (int fi = 0; fi < kF; ++fi) P[OFF_W1 + fi * kH + i] = g2[fi];
+            P[OFF_B1 + i] = g2[16];
         }
-#pragma unroll
-    for (int o = 4; o < 32; o <<= 1) {
-        db3 += __shfl_xor_sync(0xffffffffu, db3, o);
-        sse += __shfl_xor_sync(0xffffffffu, sse, o);
+    } else {
+        for (int i = tid; i < OFF_W3; i += 128) P[i] = 0.f;
     }
-    if (lane < 4) {
+    // dw3, db3 and the squared errors: per-thread sums added over the CTA in thread order
+    tc_sync();
+    float* red = reinterpret_cast<float*>(base);  // the operand tiles are free now
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            sred[warp][8 * j + 2 * t] = db1[2 * j];
-            sred[warp][8 * j + 2 * t + 1] = db1[2 * j + 1];
-            sred[warp][kH + 8 * j + 2 * t] = db2[2 * j];
-            sred[warp][kH + 8 * j + 2 * t + 1] = db2[2 * j + 1];
-            sred[warp][2 * kH + 8 * j + 2 * t] = dw3[2 * j];
-            sred[warp][2 * kH + 8 * j + 2 * t + 1] = dw3[2 * j + 1];
-        }
-        if (lane == 0) {
-            sred[warp][3 * kH] = db3;
-            sred[warp][3 * kH + 1] = sse;
-        }
-    }
+    for (int j = 0; j < kH; ++j) red[tid * 68 + j] = gw3[j];
+    red[tid * 68 + 64] = gb3;
+    red[tid * 68 + 65] = sse;
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * kH + 2; i += kMlpBlock) {
-        const float s = sred[0][i] + sred[1][i] + sred[2][i] + sred[3][i];
-        if (i < kH) P[OFF_B1 + i] = s;
-        else if (i < 2 * kH) P[OFF_B2 + i - kH] = s;
-        else if (i < 3 * kH) P[OFF_W3 + i - 2 * kH] = s;
-        else if (i == 3 * kH) P[OFF_B3] = s;
+    if (tid < 66) {
+        float s = 0.f;
+        for (int r = 0; r < 128; ++r) s += red[r * 68 + tid];
+        if (tid < kH) P[OFF_W3 + tid] = s;
+        else if (tid == 64) P[OFF_B3] = s;
         else P[NP] = s;
     }
+    tc_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTColsTmem) : "memory");
 }
 
 // grad[i] = sum over CTAs (in order) of part[cta][i]; loss = sum of squared errors / ne
@@ -519,29 +557,6 @@ __global__ void k_mlp_adam(float* __restrict__ theta, float* __restrict__ m, flo
     m[i] = mi;
     v[i] = vi;
     theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-}
-
-// B-operand fragments of W1, W2 and W2^T from the FP32 parameters.
-__global__ void k_mlp_frags(const float* __restrict__ theta, uint2* __restrict__ w1f,
-                            uint2* __restrict__ w2f, uint2* __restrict__ w2tf) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // [0, 256) W1, then 1024 each W2, W2^T
-    const float* W1 = theta + OFF_W1;
-    const float* W2 = theta + OFF_W2;
-    if (i < 256) {
-        const int j = i >> 5, lane = i & 31, g = lane >> 2, t = lane & 3, n = 8 * j + g;
-        w1f[i] = make_uint2(pack_bf16(W1[(2 * t) * kH + n], W1[(2 * t + 1) * kH + n]),
-                            pack_bf16(W1[(2 * t + 8) * kH + n], W1[(2 * t + 9) * kH + n]));
-    } else if (i < 256 + 1024) {
-        const int q = i - 256, lane = q & 31, kk = (q >> 5) & 3, j = q >> 7, g = lane >> 2, t = lane & 3;
-        const int n = 8 * j + g, k0 = 16 * kk + 2 * t;
-        w2f[q] = make_uint2(pack_bf16(W2[k0 * kH + n], W2[(k0 + 1) * kH + n]),
-                            pack_bf16(W2[(k0 + 8) * kH + n], W2[(k0 + 9) * kH + n]));
-    } else if (i < 256 + 2048) {
-        const int q = i - 1280, lane = q & 31, kk = (q >> 5) & 3, j = q >> 7, g = lane >> 2, t = lane & 3;
-        const int n = 8 * j + g, k0 = 16 * kk + 2 * t;  // B[k][n] = W2[n][k]
-        w2tf[q] = make_uint2(pack_bf16(W2[n * kH + k0], W2[n * kH + k0 + 1]),
-                             pack_bf16(W2[n * kH + k0 + 8], W2[n * kH + k0 + 9]));
-    }
 }
 
 // Kaiming-uniform initial weights from the counter-based generator, biases 0.
@@ -590,25 +605,16 @@ __global__ void k_mlp_features(int64_t ne, const int32_t* __restrict__ ids,
 
 struct sfg_mlp {
     float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
-    uint2 *w1f = nullptr, *w2f = nullptr, *w2tf = nullptr;
     int64_t step = 0;
     cudaStream_t stream = nullptr;
     int device = -1;
+    int* err = nullptr;  // set by a tensor-core kernel whose completion wait ran out
 };
-
-static Net net_of(const sfg_mlp* n) { return Net{n->theta, n->w1f, n->w2f, n->w2tf}; }
-
-static sfg_status refresh_frags(sfg_ctx* ctx, sfg_mlp* n) {
-    k_mlp_frags<<<ceil_div_u(256 + 2048, 256), 256, 0, ctx->stream>>>(n->theta, n->w1f, n->w2f, n->w2tf);
-    ++ctx->launches;
-    SFG_LAUNCH_CHECK(ctx, "k_mlp_frags");
-    return SFG_OK;
-}
 
 static void mlp_free(sfg_mlp* n) {
     if (!n) return;
     SfgDeviceGuard guard(n->device);
-    void* ptrs[] = {n->theta, n->m, n->v, n->grad, n->w1f, n->w2f, n->w2tf};
+    void* ptrs[] = {n->theta, n->m, n->v, n->grad, n->err};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, n->stream);
     delete n;
@@ -617,28 +623,31 @@ static void mlp_free(sfg_mlp* n) {
 // gradient (and loss) of the network on [feats, targets) into n->grad
 static sfg_status mlp_grad(sfg_ctx* ctx, sfg_mlp* n, const float* feats, const float* targets,
                            int64_t ne, double* loss_dev) {
-    const int grid = (int)std::min<int64_t>((ne + 63) / 64,
-                                            (int64_t)sfg_grid(ctx, (const void*)k_mlp_fwdbwd,
-                                                              kMlpBlock, 0, ne * 2));
+    // two CTAs per SM (each holds 256 TMEM columns and about 113 KB of shared memory)
+    const auto key = std::make_tuple((const void*)k_mlp_fwdbwd_tc, 128, kTrainSmem);
+    if (ctx->occupancy.find(key) == ctx->occupancy.end()) {
+        SFG_CUDA(ctx, cudaFuncSetAttribute(k_mlp_fwdbwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kTrainSmem));
+        ctx->occupancy.emplace(key, 2);
+    }
+    const int grid = (int)std::min<int64_t>((ne + 127) / 128, (int64_t)ctx->num_sms * 2);
     Scratch s(ctx);
     float* part;
     SFG_TRY(s.get(&part, (size_t)grid * (NP + 1)));
     sfg_tic(ctx, "mlp_fwdbwd");
-    k_mlp_fwdbwd<<<grid, kMlpBlock, 0, ctx->stream>>>(net_of(n), feats, targets, ne, part);
+    k_mlp_fwdbwd_tc<<<grid, 128, kTrainSmem, ctx->stream>>>(n->theta, feats, targets, ne, part, n->err,
+                                                             ctx->withhold_mma ? 1 : 0);
     sfg_toc(ctx);
     k_mlp_fold<<<ceil_div_u(NP + 1, 256), 256, 0, ctx->stream>>>(part, grid, ne, n->grad, loss_dev);
     ctx->launches += 2;
-    SFG_LAUNCH_CHECK(ctx, "k_mlp_fwdbwd");
+    SFG_LAUNCH_CHECK(ctx, "k_mlp_fwdbwd_tc");
     return SFG_OK;
 }
 
 sfg_status sfg_mlp_forward_impl(sfg_ctx* ctx, const sfg_mlp* net, const float* feats, int64_t ne,
                                 float* out) {
     if (ne == 0) return SFG_OK;
-    Scratch s(ctx);
-    int* err;
-    SFG_TRY(s.get(&err, 1));
-    SFG_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+    int* err = net->err;
     const int64_t ntiles = (ne + 127) / 128;
     // One wave of resident CTAs, counted from the kernel's registers and static shared memory
     // (each CTA also holds 64 of the SM's 512 TMEM columns, so at most 8 fit); kept per context,
@@ -664,14 +673,24 @@ sfg_status sfg_mlp_forward_impl(sfg_ctx* ctx, const sfg_mlp* net, const float* f
     }
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * per_sm);
     sfg_tic(ctx, "mlp_forward");
-    k_mlp_forward_tc<<<grid, 128, 0, ctx->stream>>>(net->theta, feats, ne, out, err);
+    k_mlp_forward_tc<<<grid, 128, 0, ctx->stream>>>(net->theta, feats, ne, out, err,
+                                                     ctx->withhold_mma ? 1 : 0);
     sfg_toc(ctx);
     ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_mlp_forward_tc");
+    return SFG_OK;
+}
+
+// Synchronise and report (then clear) a completion wait of this network's tensor-core kernels
+// that ran out since the last check.
+sfg_status sfg_mlp_check_impl(sfg_ctx* ctx, const sfg_mlp* net) {
     int h = 0;
-    SFG_CUDA(ctx, cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SFG_CUDA(ctx, cudaMemcpyAsync(&h, net->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (h) return sfg_fail(ctx, SFG_ETIMEOUT, "MLP forward: a tensor-core completion wait ran out");
+    if (h) {
+        SFG_CUDA(ctx, cudaMemsetAsync(net->err, 0, sizeof(int), ctx->stream));
+        return sfg_fail(ctx, SFG_ETIMEOUT, "a tensor-core completion wait of the network ran out");
+    }
     return SFG_OK;
 }
 
@@ -709,19 +728,17 @@ sfg_status sfg_mlp_create(sfg_ctx* ctx, uint64_t seed, sfg_mlp** out) {
     A((void**)&n->m, 4 * NP);
     A((void**)&n->v, 4 * NP);
     A((void**)&n->grad, 4 * NP);
-    A((void**)&n->w1f, sizeof(uint2) * 256);
-    A((void**)&n->w2f, sizeof(uint2) * 1024);
-    A((void**)&n->w2tf, sizeof(uint2) * 1024);
+    A((void**)&n->err, sizeof(int));
     if (st != SFG_OK) {
         mlp_free(n);
         return st;
     }
+    SFG_CUDA(ctx, cudaMemsetAsync(n->err, 0, sizeof(int), ctx->stream));
     SFG_CUDA(ctx, cudaMemsetAsync(n->m, 0, 4 * NP, ctx->stream));
     SFG_CUDA(ctx, cudaMemsetAsync(n->v, 0, 4 * NP, ctx->stream));
     k_mlp_init<<<ceil_div_u(NP, 256), 256, 0, ctx->stream>>>(seed, n->theta);
     ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_mlp_init");
-    SFG_TRY(refresh_frags(ctx, n));
     *out = n;
     return SFG_OK;
 }
@@ -744,7 +761,7 @@ sfg_status sfg_mlp_set_params(sfg_ctx* ctx, sfg_mlp* net, const float* theta) {
     SFG_CUDA(ctx, cudaMemsetAsync(net->m, 0, 4 * NP, ctx->stream));
     SFG_CUDA(ctx, cudaMemsetAsync(net->v, 0, 4 * NP, ctx->stream));
     net->step = 0;
-    return refresh_frags(ctx, net);
+    return SFG_OK;
 }
 
 sfg_status sfg_mlp_forward(sfg_ctx* ctx, const sfg_mlp* net, const float* feats, int64_t ne,
@@ -775,7 +792,7 @@ sfg_status sfg_mlp_gradient(sfg_ctx* ctx, sfg_mlp* net, const float* feats, cons
     }
     if (loss_host) {
         SFG_CUDA(ctx, cudaMemcpyAsync(loss_host, loss, 8, cudaMemcpyDeviceToHost, ctx->stream));
-        SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        SFG_TRY(sfg_mlp_check_impl(ctx, net));
     }
     return SFG_OK;
 }
@@ -800,7 +817,6 @@ sfg_status sfg_mlp_train(sfg_ctx* ctx, sfg_mlp* net, const float* feats, const f
                                                                      1e-8f, c1, c2);
             ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_mlp_adam");
-            SFG_TRY(refresh_frags(ctx, net));
         }
     if (loss_host) {
         Scratch s(ctx);
@@ -808,9 +824,16 @@ sfg_status sfg_mlp_train(sfg_ctx* ctx, sfg_mlp* net, const float* feats, const f
         SFG_TRY(s.get(&loss, 1));
         SFG_TRY(mlp_grad(ctx, net, feats, targets, ne, loss));
         SFG_CUDA(ctx, cudaMemcpyAsync(loss_host, loss, 8, cudaMemcpyDeviceToHost, ctx->stream));
-        SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        SFG_TRY(sfg_mlp_check_impl(ctx, net));
     }
     return SFG_OK;
+}
+
+sfg_status sfg_mlp_check(sfg_ctx* ctx, const sfg_mlp* net) {
+    if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
+    if (!net) return sfg_fail(ctx, SFG_EINVAL, "network is NULL");
+    return sfg_mlp_check_impl(ctx, net);
 }
 
 sfg_status sfg_edge_features(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,

@@ -13,7 +13,10 @@ namespace {
 
 constexpr int kBlock = 256;
 #ifndef SFG_SCORE_U
-#define SFG_SCORE_U 2
+#define SFG_SCORE_U 4
+#endif
+#ifndef SFG_SCORE_MINB
+#define SFG_SCORE_MINB 2
 #endif
 
 template <int LPR>
@@ -37,7 +40,7 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 // SCALED = 2: the scales are per graph of a disjoint union (graph g's rows start at node_off[g]),
 // looked up from each edge's first endpoint.
 template <typename T, int LPR, int SCALED, int U, int MODE>
-__global__ void __launch_bounds__(kBlock, U > 1 ? 4 : 1)
+__global__ void __launch_bounds__(kBlock, U > 1 ? SFG_SCORE_MINB : 1)
     k_score(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
              const int32_t* __restrict__ ev, const float* __restrict__ ew,
              const T* __restrict__ XG, const T* __restrict__ XP, float eta,

@@ -37,6 +37,8 @@ struct sfg_ctx {
     std::map<std::tuple<const void*, int, size_t>, int> occupancy;  // resident CTAs per SM
     int64_t alloc_count = 0;               // for the allocation-failure injection hook
     int64_t fail_alloc_at = -1;            // SFG_FAULT_ALLOC=<n>: the n-th allocation fails
+    bool withhold_mma = false;             // SFG_FAULT_MMA_WAIT=1: tensor-core kernels issue no
+                                           // MMA, so their bounded completion waits run out
 };
 
 struct sfg_graph {
@@ -213,6 +215,7 @@ sfg_status sfg_topk_segmented_impl(sfg_ctx* ctx, const float* scores, const int3
 typedef struct sfg_mlp sfg_mlp;
 sfg_status sfg_mlp_forward_impl(sfg_ctx* ctx, const sfg_mlp* net, const float* feats, int64_t ne,
                                 float* out);
+sfg_status sfg_mlp_check_impl(sfg_ctx* ctx, const sfg_mlp* net);
 sfg_status sfg_edge_features_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_graph* LP, int K,
                                   int steps, double omega, uint64_t seed, sfg_dtype storage,
                                   const int32_t* ids, int64_t ne, float* feats);

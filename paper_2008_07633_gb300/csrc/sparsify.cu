@@ -26,6 +26,12 @@ __global__ void k_compact_ids(int64_t m, const uint8_t* __restrict__ flag,
         if (flag[e]) ids[pos[e]] = (int32_t)e;
 }
 
+__global__ void k_f32_to_bf16(int64_t n, const float* __restrict__ x, __nv_bfloat16* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kBlock)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
 __global__ void k_set_mask(int64_t k, const int32_t* __restrict__ ids, uint8_t* __restrict__ mask) {
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < k;
          i += (int64_t)gridDim.x * kBlock)
@@ -53,11 +59,11 @@ int64_t round_half_up(double x) { return (int64_t)std::floor(x + 0.5); }
 size_t elem_size(sfg_dtype dt) { return dt == SFG_BF16 ? 2 : 4; }
 
 // Edge recovery at one level (Sec. 3.5; the embedding, scoring and selection steps of
-// Algorithm 1). `mask` holds the current sparsifier of g and receives the added edges. XG: the
-// embedding of g from this level's seed in P->storage, cached from coarsening (may be NULL:
-// computed here).
+// Algorithm 1). `mask` holds the current sparsifier of g and receives the added edges. XG_f32: the
+// FP32 embedding of g from this level's seed, cached from coarsening (may be NULL: computed here
+// in the requested storage).
 sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64_t seed,
-                   int64_t forest, const void* XG, uint8_t* mask) {
+                   int64_t forest, const float* XG_f32, uint8_t* mask) {
     const int64_t m = g->m;
     const int64_t base = P->budget_unit == 0 ? (int64_t)g->n : m - forest;
     const int64_t target = round_half_up(P->budget_frac * (double)base);
@@ -95,9 +101,9 @@ sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64
         SFG_TRY(sfg_gs_inherit(ctx, pg, g));
         const size_t blk = (size_t)g->n * P->K * elem_size(P->storage);
         void* xp;
-        const void* xg = XG;
+        const void* xg = XG_f32;
         SFG_TRY(s.get((char**)&xp, blk));
-        if (!xg) {
+        if (!xg || P->storage != SFG_F32) {
             void* x;
             SFG_TRY(s.get((char**)&x, blk));
             SFG_TRY(sfg_smooth_gs_impl(ctx, g, P->K, P->steps, P->omega, seed, P->storage, x));
@@ -105,15 +111,26 @@ sfg_status recover(sfg_ctx* ctx, const sfg_graph* g, const sfg_params* P, uint64
         }
         SFG_TRY(sfg_smooth_gs_impl(ctx, pg, P->K, P->steps, P->omega, seed, P->storage, xp));
         SFG_TRY(sfg_score_impl(ctx, g, xg, xp, P->K, P->storage, cand, ncand, P->mode, scores));
-    } else if (!XG) {  // embed G and P from one seeded block and score in one pass
+    } else if (!XG_f32) {  // embed G and P from one seeded block and score in one pass
         SFG_TRY(sfg_filter_score_impl(ctx, g, pg, P->K, P->steps, P->omega, seed, P->storage, cand,
                                       ncand, P->mode, scores));
-    } else {  // reuse the level's cached embedding of G
+    } else {  // reuse the level's cached FP32 embedding of G (rounded once for BF16 storage)
         const size_t blk = (size_t)g->n * P->K * elem_size(P->storage);
         void* xp;
         SFG_TRY(s.get((char**)&xp, blk));
+        const void* xg = XG_f32;
+        if (P->storage != SFG_F32) {
+            void* x;
+            SFG_TRY(s.get((char**)&x, blk));
+            const int64_t cnt = (int64_t)g->n * P->K;
+            k_f32_to_bf16<<<sfg_grid(ctx, (const void*)k_f32_to_bf16, kBlock, 0, cnt), kBlock, 0,
+                            ctx->stream>>>(cnt, XG_f32, (__nv_bfloat16*)x);
+            ++ctx->launches;
+            SFG_LAUNCH_CHECK(ctx, "k_f32_to_bf16");
+            xg = x;
+        }
         SFG_TRY(sfg_smooth_impl(ctx, pg, P->K, P->steps, P->omega, seed, P->storage, xp));
-        SFG_TRY(sfg_score_impl(ctx, g, XG, xp, P->K, P->storage, cand, ncand, P->mode, scores));
+        SFG_TRY(sfg_score_impl(ctx, g, xg, xp, P->K, P->storage, cand, ncand, P->mode, scores));
     }
     SFG_TRY(sfg_topk_impl(ctx, scores, cand, ncand, k, sel));
     k_set_mask<<<sfg_grid(ctx, (const void*)k_set_mask, kBlock, 0, k), kBlock, 0, ctx->stream>>>(
@@ -126,7 +143,7 @@ struct Level {
     sfg_graph* g = nullptr;   // G_l (level 0 borrowed)
     int32_t* agg = nullptr;   // map G_{l-1} -> G_l (l >= 1)
     int32_t* f2c = nullptr;   // fine edge of G_{l-1} -> edge of G_l
-    void* xg = nullptr;       // embedding of G_l used for coarsening (l < lf), in P->storage
+    float* xg = nullptr;      // FP32 embedding of G_l used for coarsening (l < lf)
     uint8_t* pmask = nullptr; // the level's sparsifier P_l over G_l's edges
 };
 
@@ -161,7 +178,7 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
     SFG_DEVICE(ctx);
     if (hier_out) *hier_out = nullptr;
     if (!G || !P) return sfg_fail(ctx, SFG_EINVAL, "NULL argument");
-    if (!sfg_k_supported(P->K, P->storage))
+    if (!sfg_k_supported(P->K, P->storage) || (P->levels > 0 && !sfg_k_supported(P->K, SFG_F32)))
         return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", P->K,
                         (int)P->storage);
     if (P->steps < 0 || P->levels < 0 || !omega_ok(P) ||
@@ -184,17 +201,16 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
     } owner{h};
     std::vector<Level>& lv = h->lv;
     Scratch s(ctx);
-    const size_t es = elem_size(P->storage);
 
-    // Algorithm 1, coarsening phase: multilevel spectral graph reduction
+    // Algorithm 1, coarsening phase: multilevel spectral graph reduction. The aggregation (an
+    // argmin decided by floating point) is taken on FP32 embeddings whatever the storage of the
+    // edge-recovery blocks, so BF16 storage changes only the recovery scores, not the hierarchy.
     for (int l = 1; l <= P->levels; ++l) {
         if (lv.back().g->m == 0) break;
         {
             Level& f = lv.back();
-            char* xg;
-            SFG_TRY(s.get(&xg, (size_t)f.g->n * P->K * es));
-            f.xg = xg;
-            SFG_TRY(smooth_any(ctx, P, f.g, level_seed(P->seed, l - 1), P->storage, f.xg));
+            SFG_TRY(s.get(&f.xg, (size_t)f.g->n * P->K));
+            SFG_TRY(smooth_any(ctx, P, f.g, level_seed(P->seed, l - 1), SFG_F32, f.xg));
         }
         lv.emplace_back();
         Level& f = lv[lv.size() - 2];
@@ -202,7 +218,7 @@ extern "C" sfg_status sfg_sparsify(sfg_ctx* ctx, const sfg_graph* G, const sfg_p
         SFG_TRY(sfg_alloc(ctx, (void**)&c.agg, (size_t)f.g->n * 4 + 16));
         SFG_TRY(sfg_alloc(ctx, (void**)&c.f2c, (size_t)f.g->m * 4 + 16));
         int32_t nc = 0;
-        SFG_TRY(sfg_coarsen_impl(ctx, f.g, f.xg, P->K, P->storage, c.agg, c.f2c, &nc, &c.g));
+        SFG_TRY(sfg_coarsen_impl(ctx, f.g, f.xg, P->K, SFG_F32, c.agg, c.f2c, &nc, &c.g));
     }
     const int lf = (int)lv.size() - 1;
 
@@ -351,6 +367,7 @@ extern "C" sfg_status sfg_sparsify_learned(sfg_ctx* ctx, const sfg_graph* G, con
             k, sel, mask_out);
         ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_set_mask");
+        SFG_TRY(sfg_mlp_check_impl(ctx, net));
     }
     if (n_selected_host) SFG_TRY(sfg_count_mask(ctx, mask_out, m, n_selected_host));
     return SFG_OK;

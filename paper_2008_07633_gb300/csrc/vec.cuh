@@ -16,10 +16,6 @@ struct Vec<float> {
     __device__ __forceinline__ static void store(float* p, const float (&x)[4]) {
         *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
     }
-    __device__ __forceinline__ static uint4 pack(const float (&x)[4]) {
-        return make_uint4(__float_as_uint(x[0]), __float_as_uint(x[1]), __float_as_uint(x[2]),
-                          __float_as_uint(x[3]));
-    }
     // value as stored (identity for FP32)
     __device__ __forceinline__ static float round(float x) { return x; }
     // raw 16-byte load and a multiply-add of its widened entries
@@ -51,17 +47,14 @@ struct Vec<__nv_bfloat16> {
             x[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
         }
     }
-    __device__ __forceinline__ static uint4 pack(const float (&x)[8]) {
+    __device__ __forceinline__ static void store(__nv_bfloat16* p, const float (&x)[8]) {
         unsigned w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);  // RN-even
             w[i] = *reinterpret_cast<const unsigned*>(&h);
         }
-        return make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    __device__ __forceinline__ static void store(__nv_bfloat16* p, const float (&x)[8]) {
-        *reinterpret_cast<uint4*>(p) = pack(x);
+        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     __device__ __forceinline__ static float round(float x) {
         return __bfloat162float(__float2bfloat16_rn(x));

@@ -32,7 +32,7 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_trim", "sfg_ctx_set_str
            "sfg_sparsify_to_kappa", "sfg_smooth_gs", "sfg_coloring", "sfg_solve_pcg",
            "sfg_hierarchy_levels", "sfg_hierarchy_graph", "sfg_hierarchy_map",
            "sfg_hierarchy_mask", "sfg_hierarchy_destroy", "sfg_batch_create", "sfg_batch_info",
-           "sfg_batch_run", "sfg_batch_destroy"]
+           "sfg_batch_run", "sfg_batch_destroy", "sfg_mlp_check"]
 
 
 class SfgError(RuntimeError):
@@ -116,6 +116,7 @@ def lib():
             "sfg_mlp_params": [_vp, _vp, _vp],
             "sfg_mlp_set_params": [_vp, _vp, _vp],
             "sfg_mlp_forward": [_vp, _vp, _vp, _i64, _vp],
+            "sfg_mlp_check": [_vp, _vp],
             "sfg_mlp_gradient": [_vp, _vp, _vp, _vp, _i64, _vp, _pdbl],
             "sfg_mlp_train": [_vp, _vp, _vp, _vp, _i64, _i64, _int, _dbl, _pdbl],
             "sfg_edge_features": [_vp, _vp, _vp, _int, _int, _dbl, _u64, _int, _vp, _i64, _vp],
@@ -651,3 +652,8 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def sfg_mlp_check(ctx, net):
+    """Synchronise; raise SfgError (SFG_ETIMEOUT) if a tensor-core wait of the network ran out."""
+    ctx.check(lib().sfg_mlp_check(ctx.h, net.h))

@@ -14,7 +14,7 @@ def test_sweep_and_score_bytes():
     assert bench.sweep_bytes(n, nnz_g) == 4 * (n + 1) + 8 * nnz_g + 4 * n + 2 * n * 32 * 4
     assert bench.sweep_bytes(n, nnz_g) == 653_524_996
     assert bench.sweep_bytes(n, nnz_p) == 587_202_548
-    assert bench.score_bytes(n, e_off) == 20 * e_off + 2 * n * 32 * 4
+    assert bench.score_bytes(n, e_off) == 16 * e_off + 2 * n * 32 * 4
     # BF16 blocks halve the vector bytes (2 N K s) only
     assert bench.sweep_bytes(n, nnz_g, s=2) == bench.sweep_bytes(n, nnz_g) - 2 * n * 32 * 2
 

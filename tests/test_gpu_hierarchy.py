@@ -144,15 +144,21 @@ def test_coarsen_bf16_block(S, ctx, K):
     assert np.array_equal(host(agg_b), oagg) and cb.n == nc
 
 
-def test_sparsify_multilevel_bf16_kappa(S, ctx):
-    # the multilevel method with BF16 blocks at every level (coarsening included): kappa within
-    # the BF16 storage tolerance of the FP32 run's
+def test_sparsify_multilevel_bf16_same_hierarchy(S, ctx):
+    # BF16 blocks change only the edge-recovery scores: the aggregation is taken on FP32
+    # embeddings, so the hierarchy is the FP32 run's bit for bit, and kappa stays within the
+    # BF16 storage tolerance of the FP32 run's
     n, u, v, w = gen.grid2d(48, 48, seed=4, weights="logu", lo=-2, hi=2)
     g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
     og = O.canonicalize(n, u, v, w)
     kw = dict(K=16, steps=10, levels=2, seed=17, budget_frac=0.05, budget_unit=0)
-    m32, n32 = S.sfg_sparsify(ctx, g, **kw)
-    m16, n16 = S.sfg_sparsify(ctx, g, storage=torch.bfloat16, **kw)
+    m32, n32, h32 = S.sfg_sparsify(ctx, g, hierarchy=True, **kw)
+    m16, n16, h16 = S.sfg_sparsify(ctx, g, storage=torch.bfloat16, hierarchy=True, **kw)
+    assert h32.levels == h16.levels == 2
+    for l in (1, 2):
+        a32, f32 = h32.map(l)
+        a16, f16 = h16.map(l)
+        assert torch.equal(a32, a16) and torch.equal(f32, f16)
     k32, k16 = O.kappa_dense(og, host(m32)), O.kappa_dense(og, host(m16))
     assert n32 == n16
     assert k16 <= 1.25 * k32, (k16, k32)

@@ -134,3 +134,39 @@ def test_pool_trim_keeps_context_usable(S):
     del g
     ctx.close()
 
+
+
+_WITHHOLD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_2008_07633_gb300.sfg as S
+ctx = S.sfg_ctx_create(0)                      # SFG_FAULT_MMA_WAIT=1: no MMA is ever issued
+net = S.sfg_mlp_create(ctx, seed=1)
+X = torch.randn(1000, 16, device="cuda")
+y = S.sfg_mlp_forward(ctx, net, X)             # queued without synchronisation
+try:
+    S.sfg_mlp_check(ctx, net)
+    print("NOFAIL")
+except S.SfgError as e:
+    print("STATUS", e.status)
+try:
+    S.sfg_mlp_gradient(ctx, net, X, torch.zeros(1000, device="cuda"))
+    print("NOFAIL")
+except S.SfgError as e:
+    print("STATUS", e.status)
+print("OK", bool(torch.isfinite(torch.ones(3, device="cuda")).all()))
+"""
+
+
+def test_tensor_core_wait_runs_out_and_reports_etimeout():
+    # The bounded completion waits of the tensor-core kernels, run out on purpose by withholding
+    # every MMA and commit (host switch read at context creation): nothing is in flight, so the
+    # kernels give up after their time limit, release TMEM and return; the host sees SFG_ETIMEOUT
+    # once per check and the process keeps using the GPU.
+    env = dict(os.environ, SFG_FAULT_MMA_WAIT="1")
+    r = subprocess.run([sys.executable, "-c", _WITHHOLD, ROOT], capture_output=True, text=True,
+                       env=env, timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = r.stdout.split("\n")
+    assert lines[0] == "STATUS 4" and lines[1] == "STATUS 4", r.stdout
+    assert lines[2] == "OK True"

@@ -75,6 +75,63 @@ def test_kappa_versus_budget_thermal(S, ctx):
             assert k1 <= k0 * (1 + 1e-6)
 
 
+def _level_origins(S, ctx, H):
+    """Per level l of a hierarchy: the edges of P_l inside aggregates of the map to level l + 1
+    (inner-cluster spanning-tree edges of the backward mapping), the edges recovered at level l,
+    and |P_l|. Each edge of P_{l+1} maps to exactly one fine edge, so |P_l| = inner_l + |P_{l+1}| +
+    added_l, and at the coarsest level |P_lf| = (forest edges) + added_lf."""
+    rows = []
+    sizes = [int(H.mask(l).sum().item()) for l in range(H.levels + 1)]
+    for l in range(H.levels + 1):
+        g = H.graph(l)
+        pm = H.mask(l)
+        if l < H.levels:
+            _, f2c = H.map(l + 1)
+            inner = int(((f2c < 0) & (pm != 0)).sum().item())
+            added = sizes[l] - inner - sizes[l + 1]
+        else:
+            tree, nt = S.sfg_spanning_tree(ctx, g)
+            inner = nt
+            added = sizes[l] - nt
+        cand = g.m - (sizes[l] - added)
+        rows.append({"level": l, "nodes": g.n, "edges": g.m, "P": sizes[l], "backbone": sizes[l] - added,
+                     "inner_or_forest": inner, "added": added, "candidates": cand,
+                     "sampling_probability": added / cand if cand else 0.0})
+    return rows
+
+
+def test_per_level_sampling_thermal(S, ctx):
+    """Per-level edge sampling on the thermal-like mesh (the paper's figure on per-level sampling
+    probabilities at off-tree budgets of 0.08 N and 0.32 N has no data in the text): for a
+    two-level run at each budget, the edges each level's recovery adds, the candidates it chose
+    from (sampling probability = added / candidates), and the backbone it received. The per-level
+    counts must add up to the final sparsifier: |P_0| = sum_l inner_l + forest_lf + sum_l added_l."""
+    n, u, v, w = gen.thermal3d(48, 48, 24, seed=10)
+    g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
+    lines = []
+    for beta in (0.08, 0.32):
+        mask, cnt, H = S.sfg_sparsify(ctx, g, K=32, steps=20, levels=2, seed=5, budget_frac=beta,
+                                      budget_unit=0, hierarchy=True)
+        rows = _level_origins(S, ctx, H)
+        total = sum(r["inner_or_forest"] for r in rows) + sum(r["added"] for r in rows)
+        assert total == cnt == int(mask.sum().item())
+        # every level ends on its own budget (reading c13): its off-forest count reaches
+        # round(beta N_l) unless the mapped backbone is already over it
+        for r in rows:
+            forest = r["nodes"] - 1                          # the mesh is connected
+            target = int(np.floor(beta * r["nodes"] + 0.5))
+            assert r["P"] == min(r["edges"], max(r["backbone"], forest + target)), r
+        k = S.sfg_kappa(ctx, g, mask, steps=100)[0]
+        lines.append(f"beta={beta} (off-tree budget {beta} N): kappa {k:.1f}, |P| = {cnt}; " + "; ".join(
+            f"level {r['level']}: N={r['nodes']} M={r['edges']} backbone {r['backbone']} added "
+            f"{r['added']} of {r['candidates']} candidates (p = {r['sampling_probability']:.4f})"
+            for r in rows))
+        H.close()
+    report = "PER_LEVEL_SAMPLING thermal3d 48x48x24, K=32, T=20, two levels: " + " | ".join(lines)
+    print("\n" + report)
+    write_report("per_level_sampling_report.txt", report)
+
+
 def _knn_graph(args):
     from paper_2008_07633_gb300 import inputs as g
 

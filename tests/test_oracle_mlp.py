@@ -57,3 +57,23 @@ def test_adam_moves_against_the_gradient_and_reduces_loss():
         g, _ = M.grad(theta, X, t)
         theta, m, v = M.adam_step(theta, m, v, g, step, lr=3e-3)
     assert M.loss(theta, X, t) < 0.2 * L0
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    import numpy as np
+    import oracle.mlp as M
+
+    # exact BF16 numbers stay, halfway cases go to the even neighbour, others to the nearest
+    one = 1.0
+    ulp = 2.0 ** -7                      # BF16 spacing in [1, 2)
+    xs = np.array([one, one + ulp / 2, one + 3 * ulp / 2, one + ulp / 4, -(one + 3 * ulp / 2), 0.0])
+    ref = np.array([one, one, one + 2 * ulp, one, -(one + 2 * ulp), 0.0])
+    assert np.array_equal(M.round_bf16(xs), ref)
+    # the kernel-precision forward equals the exact forward when every rounded value is exact
+    th = np.zeros(M.NPARAM)
+    p = M.unflatten(th)
+    p["W1"][0, 0], p["W2"][0, 0], p["w3"][0], p["b3"][0] = 2.0, 0.5, 3.0, 0.25
+    th = M.flatten(p)
+    X = np.zeros((3, 16))
+    X[:, 0] = [1.0, -1.0, 4.0]
+    assert np.allclose(M.forward_kernel_precision(th, X), M.forward(th, X)[0])
