@@ -766,10 +766,11 @@ def run_ours(args):
             pg.barrier()
         torch.cuda.synchronize()
 
-    if args.mlp_only:  # ncu captures of the tensor-core inference kernel alone
+    if args.mlp_only:  # ncu captures of the tensor-core inference and training kernels alone
         ctx = S.sfg_ctx_create(local)
         if rank == 0:
-            print(json.dumps({"mlp_forward": mlp_report(S, ctx, dev, args.mlp_rows, 3)}), flush=True)
+            print(json.dumps({"mlp_forward": mlp_report(S, ctx, dev, args.mlp_rows, 3),
+                              "mlp_train": mlp_train_report(S, ctx, dev, args.mlp_rows, 3)}), flush=True)
         return 0
     if args.profile and args.profile_workload == "chunglu":
         # ncu captures on the power-law workload: filter+score steps only (default tile shape)
