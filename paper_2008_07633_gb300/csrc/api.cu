@@ -119,7 +119,7 @@ void sfg_toc(sfg_ctx* ctx) {
     cudaEventRecord(ctx->timers.back().stop, ctx->stream);
 }
 
-static uint32_t tune_key(int K, sfg_dtype dt, int bucket) {
+uint32_t sfg_tune_key(int K, sfg_dtype dt, int bucket) {
     return ((uint32_t)K << 16) | ((uint32_t)dt << 8) | (uint32_t)bucket;
 }
 
@@ -132,12 +132,21 @@ int sfg_degree_bucket(const sfg_graph* L) {
 
 int sfg_tuned_variant(const sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L) {
     if (ctx->tune.empty()) return -1;
-    auto it = ctx->tune.find(tune_key(K, dt, sfg_degree_bucket(L)));
+    auto it = ctx->tune.find(sfg_tune_key(K, dt, sfg_degree_bucket(L)));
     return it == ctx->tune.end() ? -1 : it->second;
 }
 
 void sfg_tune_record(sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L, int variant) {
-    ctx->tune[tune_key(K, dt, sfg_degree_bucket(L))] = variant;
+    ctx->tune[sfg_tune_key(K, dt, sfg_degree_bucket(L))] = variant;
+}
+
+int sfg_score_shape(const sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L) {
+    const int b = sfg_degree_bucket(L);
+    if (!ctx->score_tune.empty()) {
+        auto it = ctx->score_tune.find(sfg_tune_key(K, dt, b));
+        if (it != ctx->score_tune.end()) return it->second;
+    }
+    return b <= 2 ? 0 : 1;
 }
 
 extern "C" {
@@ -293,9 +302,21 @@ sfg_status sfg_tune_set(sfg_ctx* ctx, int K, sfg_dtype storage, int degree_bucke
     SFG_DEVICE(ctx);
     if (degree_bucket < 0 || degree_bucket > 15 || variant < -1 || variant >= SFG_SWEEP_VARIANTS)
         return sfg_fail(ctx, SFG_EINVAL, "bad tuning entry");
-    const uint32_t key = tune_key(K, storage, degree_bucket);
+    const uint32_t key = sfg_tune_key(K, storage, degree_bucket);
     if (variant < 0) ctx->tune.erase(key);
     else ctx->tune[key] = variant;
+    return SFG_OK;
+}
+
+sfg_status sfg_tune_set_score(sfg_ctx* ctx, int K, sfg_dtype storage, int degree_bucket,
+                              int shape) {
+    if (!ctx) return SFG_EINVAL;
+    SFG_DEVICE(ctx);
+    if (degree_bucket < 0 || degree_bucket > 15 || shape < -1 || shape >= SFG_SCORE_SHAPES)
+        return sfg_fail(ctx, SFG_EINVAL, "bad tuning entry");
+    const uint32_t key = sfg_tune_key(K, storage, degree_bucket);
+    if (shape < 0) ctx->score_tune.erase(key);
+    else ctx->score_tune[key] = shape;
     return SFG_OK;
 }
 
@@ -304,15 +325,22 @@ sfg_status sfg_tune_table(const sfg_ctx* ctx, char* buf, int64_t cap, int64_t* l
     SFG_DEVICE(ctx);
     static const int tpi[SFG_SWEEP_VARIANTS] = {1, 2, 4, 1, 2, 4};
     static const int minb[SFG_SWEEP_VARIANTS] = {4, 4, 4, 3, 3, 3};
+    std::map<uint32_t, std::pair<int, int>> keys;  // key -> (sweep variant, scorer shape)
+    for (auto& kv : ctx->tune) keys[kv.first] = {kv.second, -1};
+    for (auto& kv : ctx->score_tune) {
+        auto it = keys.find(kv.first);
+        if (it == keys.end()) keys[kv.first] = {-1, kv.second};
+        else it->second.second = kv.second;
+    }
     std::string j = "[";
-    for (auto& kv : ctx->tune) {
-        char item[160];
-        const int v = kv.second;
+    for (auto& kv : keys) {
+        char item[224];
+        const int v = kv.second.first, s = kv.second.second;
         snprintf(item, sizeof item,
                  "%s{\"K\": %u, \"dtype\": %u, \"degree_bucket\": %u, \"variant\": %d, "
-                 "\"tiles_per_warp\": %d, \"ctas_per_sm\": %d}",
+                 "\"tiles_per_warp\": %d, \"ctas_per_sm\": %d, \"score_shape\": %d}",
                  j.size() > 1 ? ", " : "", kv.first >> 16, (kv.first >> 8) & 0xff, kv.first & 0xff,
-                 v, tpi[v], minb[v]);
+                 v, v >= 0 ? tpi[v] : 0, v >= 0 ? minb[v] : 0, s);
         j += item;
     }
     j += "]";

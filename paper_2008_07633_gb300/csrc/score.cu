@@ -3,21 +3,23 @@
 // smoothed blocks; the scoring and selection steps of Algorithm 1). (2) Algebraic-distance affinity that drives node
 // aggregation in coarsening (Sec. 3.2).
 //
-// Scorer schedule: the same LPR-lane group per item as the smoother. For each listed edge the
-// group gathers the two endpoint rows of both blocks (4 x 16 B per lane), forms the two squared
-// distances in FP32 and folds them with xor-shuffles inside the group.
+// Scorer schedule: one LPR-lane group per listed edge; the group gathers the two endpoint rows of
+// both blocks (one 32-byte load per row and lane), forms the two squared distances in FP32 and
+// folds them with xor-shuffles inside the group.
 #include "sfg_internal.cuh"
 #include "vec.cuh"
 
 namespace {
 
 constexpr int kBlock = 256;
-#ifndef SFG_SCORE_U
-#define SFG_SCORE_U 4
-#endif
-#ifndef SFG_SCORE_MINB
-#define SFG_SCORE_MINB 2
-#endif
+
+// One 32-byte read-only global load (sm_100 and later) into two 16-byte vectors; p must be 32-byte
+// aligned.
+__device__ __forceinline__ void load_raw32(const void* p, uint4& a, uint4& b) {
+    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(p));
+}
 
 template <int LPR>
 __device__ __forceinline__ unsigned group_mask(int lane) {
@@ -26,35 +28,40 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 }
 
 // Scorer, warp-tile schedule: a warp scores U consecutive tiles of GPW = 32 / LPR list entries
-// each (one LPR-lane group per edge) and moves by grid stride over such tile groups. Every lane
-// of a group loads its edge's id, endpoints and weight itself (group-uniform addresses are served
-// as one broadcast). The next group's endpoints and the ids of the group after it are loaded
-// before this group's 4U row gathers are consumed, so one gather round is the exposed latency per
-// U tiles; gathered rows stay packed (16 bytes per gather) until they are used. The two squared
-// distances are folded together: at the first step the even lane of each pair keeps the G partial
-// and the odd lane the P partial, so one shuffle per level moves both, and one more hands the P
-// sum to the group's first lane (LPR = 8: 4 shuffles per edge). The score formula is fixed at
-// compile time (MODE).
+// each (one LPR-lane group per edge) and moves by grid stride over such tile groups. Lane s of a
+// group holds V consecutive 16-byte vectors of a row (entries [s V E, (s + 1) V E)); with V = 2 a
+// row is read by one 32-byte load per lane when both blocks are 32-byte aligned (WIDE, the usual
+// case) and by two 16-byte loads otherwise, with the same arithmetic. Every lane of a group
+// loads its edge's id, endpoints and weight itself (group-uniform addresses are served as one
+// broadcast). The next group's endpoints and the ids of the group after it are loaded before this
+// group's 4U row gathers are consumed, so one gather round is the exposed latency per U tiles;
+// gathered rows stay packed until they are used. The two squared distances are folded together:
+// at the first step the even lane of each pair keeps the G partial and the odd lane the P partial,
+// so one shuffle per level moves both, and one more hands the P sum to the group's first lane.
+// The score formula is fixed at compile time (MODE); U and MINB (CTAs per SM) are the launch
+// shape.
 // SCALED: the blocks are raw smoothed blocks and column k of each is multiplied by its projection
 // scale (sg, sp) on the fly; the projection's mean removal cancels in X_p - X_q.
 // SCALED = 2: the scales are per graph of a disjoint union (graph g's rows start at node_off[g]),
 // looked up from each edge's first endpoint.
-template <typename T, int LPR, int SCALED, int U, int MODE>
-__global__ void __launch_bounds__(kBlock, U > 1 ? SFG_SCORE_MINB : 1)
+template <typename T, int LPR, int V, bool WIDE, int SCALED, int U, int MINB, int MODE>
+__global__ void __launch_bounds__(kBlock, MINB)
     k_score(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
              const int32_t* __restrict__ ev, const float* __restrict__ ew,
              const T* __restrict__ XG, const T* __restrict__ XP, float eta,
              const float* __restrict__ sg, const float* __restrict__ sp,
              const int32_t* __restrict__ node_off, int ngraphs, float* __restrict__ out) {
-    constexpr int E = Vec<T>::E, K = LPR * E, GPW = 32 / LPR;
+    static_assert(V == 1 || V == 2, "one or two vectors per lane");
+    constexpr int E = Vec<T>::E, K = LPR * E * V, GPW = 32 / LPR;
     const int lane = threadIdx.x & 31, grp = lane / LPR, sub = lane % LPR;
     const unsigned gm = group_mask<LPR>(lane);
     const int64_t wid = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
     const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
     const int64_t ntiles = (ne + GPW - 1) / GPW;
     const int64_t ngroups = (ntiles + U - 1) / U;
-    const T* __restrict__ Xg = XG + sub * E;
-    const T* __restrict__ Xp = XP + sub * E;
+    const int sub0 = sub * V * E;  // first entry of this lane
+    const T* __restrict__ Xg = XG + sub0;
+    const T* __restrict__ Xp = XP + sub0;
     __shared__ float s_scale[2][SCALED == 1 ? K : 1];
     if (SCALED == 1) {
         for (int k = threadIdx.x; k < K; k += kBlock) {
@@ -89,14 +96,24 @@ __global__ void __launch_bounds__(kBlock, U > 1 ? SFG_SCORE_MINB : 1)
             nxt[u] = load_edge(idn[u]);
             idn[u] = load_id((g + 2 * nw) * U + u);
         }
-        uint4 rgp[U], rgq[U], rpp[U], rpq[U];
+        uint4 rgp[U][V], rgq[U][V], rpp[U][V], rpq[U][V];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t p = cur[u].p, q = cur[u].q;
-            rgp[u] = Vec<T>::load_raw(Xg + p * K);
-            rgq[u] = Vec<T>::load_raw(Xg + q * K);
-            rpp[u] = Vec<T>::load_raw(Xp + p * K);
-            rpq[u] = Vec<T>::load_raw(Xp + q * K);
+            if constexpr (V == 2 && WIDE) {
+                load_raw32(Xg + p * K, rgp[u][0], rgp[u][V - 1]);
+                load_raw32(Xg + q * K, rgq[u][0], rgq[u][V - 1]);
+                load_raw32(Xp + p * K, rpp[u][0], rpp[u][V - 1]);
+                load_raw32(Xp + q * K, rpq[u][0], rpq[u][V - 1]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    rgp[u][v] = Vec<T>::load_raw(Xg + p * K + v * E);
+                    rgq[u][v] = Vec<T>::load_raw(Xg + q * K + v * E);
+                    rpp[u][v] = Vec<T>::load_raw(Xp + p * K + v * E);
+                    rpq[u][v] = Vec<T>::load_raw(Xp + q * K + v * E);
+                }
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -104,8 +121,8 @@ __global__ void __launch_bounds__(kBlock, U > 1 ? SFG_SCORE_MINB : 1)
             const float* sc_g = nullptr;
             const float* sc_p = nullptr;
             if (SCALED == 1) {
-                sc_g = s_scale[0] + sub * E;
-                sc_p = s_scale[1] + sub * E;
+                sc_g = s_scale[0] + sub0;
+                sc_p = s_scale[1] + sub0;
             } else if (SCALED == 2) {
                 const int32_t p = cur[u].p;
                 int lo = 0, hi = ngraphs;  // graph of row p
@@ -113,24 +130,27 @@ __global__ void __launch_bounds__(kBlock, U > 1 ? SFG_SCORE_MINB : 1)
                     const int mid = (lo + hi) >> 1;
                     if (node_off[mid] <= p) lo = mid; else hi = mid;
                 }
-                sc_g = sg + (size_t)lo * K + sub * E;
-                sc_p = sp + (size_t)lo * K + sub * E;
+                sc_g = sg + (size_t)lo * K + sub0;
+                sc_p = sp + (size_t)lo * K + sub0;
             }
-            float gp[E], gq[E], pp[E], pq[E];
-            Vec<T>::unpack(rgp[u], gp);
-            Vec<T>::unpack(rgq[u], gq);
-            Vec<T>::unpack(rpp[u], pp);
-            Vec<T>::unpack(rpq[u], pq);
             float dg = 0.f, dp = 0.f;
 #pragma unroll
-            for (int k = 0; k < E; ++k) {
-                float a = gp[k] - gq[k], b = pp[k] - pq[k];
-                if (SCALED) {
-                    a *= sc_g[k];
-                    b *= sc_p[k];
+            for (int v = 0; v < V; ++v) {
+                float gp[E], gq[E], pp[E], pq[E];
+                Vec<T>::unpack(rgp[u][v], gp);
+                Vec<T>::unpack(rgq[u][v], gq);
+                Vec<T>::unpack(rpp[u][v], pp);
+                Vec<T>::unpack(rpq[u][v], pq);
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    float a = gp[k] - gq[k], b = pp[k] - pq[k];
+                    if (SCALED) {
+                        a *= sc_g[v * E + k];
+                        b *= sc_p[v * E + k];
+                    }
+                    dg = fmaf(a, a, dg);
+                    dp = fmaf(b, b, dp);
                 }
-                dg = fmaf(a, a, dg);
-                dp = fmaf(b, b, dp);
             }
             if (LPR > 1) {
                 // even lanes: G partial sums, odd lanes: P partial sums
@@ -189,21 +209,33 @@ __global__ void k_affinity(int64_t m, const int32_t* __restrict__ eu, const int3
     }
 }
 
-template <typename T, int LPR>
+// NV: 16-byte vectors per row; each lane takes two of them (one when a row is one vector).
+// Launch shape 0: one tile per warp iteration, four CTAs per SM; shape 1: two tiles, two CTAs per
+// SM (sfg_score_shape). Both compute the same values bit for bit.
+template <typename T, int NV>
 sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
                         const int32_t* ids, int64_t ne, int mode, const float* sg,
                         const float* sp, const int32_t* node_off, int ngraphs, float* out) {
     if (ne == 0) return SFG_OK;
-    // the grid fills the SMs at the occupancy of the variant that is launched
-    constexpr int U = SFG_SCORE_U;
+    constexpr int V = NV >= 2 ? 2 : 1, LPR = NV / V;
+    constexpr int K = NV * 16 / (int)sizeof(T);
     const T *xg = (const T*)XG, *xp = (const T*)XP;
     float eta = 1e-30f;
+    const bool wide = V == 2 && ((((uintptr_t)XG | (uintptr_t)XP) & 31) == 0);
     const int sc = node_off ? 2 : (sg ? 1 : 0);
-    static void* const tab[3][3] = {
-        {(void*)k_score<T, LPR, 0, U, 0>, (void*)k_score<T, LPR, 0, U, 1>, (void*)k_score<T, LPR, 0, U, 2>},
-        {(void*)k_score<T, LPR, 1, U, 0>, (void*)k_score<T, LPR, 1, U, 1>, (void*)k_score<T, LPR, 1, U, 2>},
-        {(void*)k_score<T, LPR, 2, U, 0>, (void*)k_score<T, LPR, 2, U, 1>, (void*)k_score<T, LPR, 2, U, 2>}};
-    const void* k = tab[sc][mode];
+    const int shape = sfg_score_shape(ctx, K, sizeof(T) == 2 ? SFG_BF16 : SFG_F32, LG);
+    constexpr bool W2 = V == 2;  // 32-byte loads exist only for two vectors per lane
+#define SFG_SCORE_ROW(WD, SC, U, MB)                                                                \
+    {(void*)k_score<T, LPR, V, WD, SC, U, MB, 0>, (void*)k_score<T, LPR, V, WD, SC, U, MB, 1>,   \
+     (void*)k_score<T, LPR, V, WD, SC, U, MB, 2>}
+    static void* const tab[2][2][3][3] = {
+        {{SFG_SCORE_ROW(false, 0, 1, 4), SFG_SCORE_ROW(false, 1, 1, 4), SFG_SCORE_ROW(false, 2, 1, 4)},
+         {SFG_SCORE_ROW(false, 0, 2, 2), SFG_SCORE_ROW(false, 1, 2, 2), SFG_SCORE_ROW(false, 2, 2, 2)}},
+        {{SFG_SCORE_ROW(W2, 0, 1, 4), SFG_SCORE_ROW(W2, 1, 1, 4), SFG_SCORE_ROW(W2, 2, 1, 4)},
+         {SFG_SCORE_ROW(W2, 0, 2, 2), SFG_SCORE_ROW(W2, 1, 2, 2), SFG_SCORE_ROW(W2, 2, 2, 2)}}};
+#undef SFG_SCORE_ROW
+    const void* k = tab[wide][shape][sc][mode];
+    const int U = shape == 0 ? 1 : 2;
     void* args[] = {(void*)&ne, (void*)&ids, (void*)&LG->eu, (void*)&LG->ev, (void*)&LG->ew,
                     (void*)&xg, (void*)&xp, (void*)&eta, (void*)&sg, (void*)&sp,
                     (void*)&node_off, (void*)&ngraphs, (void*)&out};
@@ -243,6 +275,57 @@ sfg_status sfg_score_batched_impl(sfg_ctx* ctx, const sfg_graph* LG, const void*
     }
 #undef SFG_SCORE_CASE
     return sfg_fail(ctx, SFG_EUNSUPPORTED, "K=%d unsupported for dtype %d", K, (int)storage);
+}
+
+namespace {
+__global__ void k_iota(int64_t m, int32_t* __restrict__ ids) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < m; i += (int64_t)gridDim.x * kBlock)
+        ids[i] = (int32_t)i;
+}
+}  // namespace
+
+sfg_status sfg_score_autotune_impl(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype storage,
+                                   const void* X) {
+    if (L->m == 0) return SFG_OK;
+    Scratch s(ctx);
+    int32_t* ids;
+    float* out;
+    SFG_TRY(s.get(&ids, (size_t)L->m));
+    SFG_TRY(s.get(&out, (size_t)L->m));
+    k_iota<<<sfg_grid(ctx, (const void*)k_iota, kBlock, 0, L->m), kBlock, 0, ctx->stream>>>(L->m, ids);
+    ++ctx->launches;
+    SFG_LAUNCH_CHECK(ctx, "k_iota");
+    const uint32_t key = sfg_tune_key(K, storage, sfg_degree_bucket(L));
+    const auto it0 = ctx->score_tune.find(key);
+    const int saved = it0 == ctx->score_tune.end() ? -1 : it0->second;
+    cudaEvent_t e0, e1;
+    SFG_CUDA(ctx, cudaEventCreate(&e0));
+    SFG_CUDA(ctx, cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 1e30f;
+    sfg_status st = SFG_OK;
+    for (int shape = 0; shape < SFG_SCORE_SHAPES && st == SFG_OK; ++shape) {
+        ctx->score_tune[key] = shape;
+        for (int r = 0; r < 4 && st == SFG_OK; ++r) {  // one warm-up, three timed
+            if (r == 1) cudaEventRecord(e0, ctx->stream);
+            st = sfg_score_impl(ctx, L, X, X, K, storage, ids, L->m, SFG_SCORE_RATIO, out, nullptr,
+                                nullptr);
+        }
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = shape; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SFG_OK) {
+        if (saved < 0) ctx->score_tune.erase(key);
+        else ctx->score_tune[key] = saved;
+        return st;
+    }
+    ctx->score_tune[key] = best;
+    return SFG_OK;
 }
 
 sfg_status sfg_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,

@@ -34,6 +34,7 @@ struct sfg_ctx {
     std::vector<cudaEvent_t> event_pool;   // free events
     int64_t launches = 0;                  // kernels launched through this context
     std::map<uint32_t, int> tune;          // (K, dtype, degree bucket) -> sweep variant
+    std::map<uint32_t, int> score_tune;    // (K, dtype, degree bucket) -> scorer launch shape
     std::map<std::tuple<const void*, int, size_t>, int> occupancy;  // resident CTAs per SM
     int64_t alloc_count = 0;               // for the allocation-failure injection hook
     int64_t fail_alloc_at = -1;            // SFG_FAULT_ALLOC=<n>: the n-th allocation fails
@@ -237,8 +238,15 @@ sfg_status sfg_alloc_graph(sfg_ctx* ctx, int32_t n, int64_t m, sfg_graph** out);
 bool sfg_k_supported(int K, sfg_dtype dt);
 // Tile-shape tuning table of a context (see sfg_autotune). Variant -1 = none recorded.
 int sfg_degree_bucket(const sfg_graph* L);
+uint32_t sfg_tune_key(int K, sfg_dtype dt, int bucket);
 int sfg_tuned_variant(const sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L);
 void sfg_tune_record(sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L, int variant);
+// Launch shape of the scorer for graphs like L: the recorded one, else 0 (one tile per warp
+// iteration, four CTAs per SM) below an average degree of 8 and 1 (two tiles, two CTAs) above.
+int sfg_score_shape(const sfg_ctx* ctx, int K, sfg_dtype dt, const sfg_graph* L);
+// Times both scorer shapes on every edge of L with X as both blocks and records the faster.
+sfg_status sfg_score_autotune_impl(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype storage,
+                                   const void* X);
 sfg_status sfg_autotune_impl(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype storage,
                              int* best, double* us);
 

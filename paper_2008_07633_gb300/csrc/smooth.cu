@@ -1321,6 +1321,7 @@ struct Smoother {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         sfg_tune_record(ctx, K, Vec<T>::E == 4 ? SFG_F32 : SFG_BF16, L, best);
+        SFG_TRY(sfg_score_autotune_impl(ctx, L, K, Vec<T>::E == 4 ? SFG_F32 : SFG_BF16, x));
         if (best_host) *best_host = best;
         if (us_host) *us_host = best_ms / 3.0 * 1e3;
         return SFG_OK;

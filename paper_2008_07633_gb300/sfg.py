@@ -27,7 +27,7 @@ EXPORTS = ["sfg_ctx_create", "sfg_ctx_destroy", "sfg_ctx_trim", "sfg_ctx_set_str
            "sfg_affinity_noalloc", "sfg_filter_score", "sfg_sparsify_batched", "sfg_mlp_create",
            "sfg_mlp_destroy", "sfg_mlp_params", "sfg_mlp_set_params", "sfg_mlp_forward",
            "sfg_mlp_gradient", "sfg_mlp_train", "sfg_edge_features", "sfg_sparsify_learned",
-           "sfg_autotune", "sfg_tune_set", "sfg_tune_table",
+           "sfg_autotune", "sfg_tune_set", "sfg_tune_set_score", "sfg_tune_table",
            "sfg_coarsen", "sfg_backward_map", "sfg_sparsify", "sfg_kappa",
            "sfg_sparsify_to_kappa", "sfg_smooth_gs", "sfg_coloring", "sfg_solve_pcg",
            "sfg_hierarchy_levels", "sfg_hierarchy_graph", "sfg_hierarchy_map",
@@ -111,6 +111,7 @@ def lib():
             "sfg_mlp_create": [_vp, _u64, ctypes.POINTER(_vp)],
             "sfg_autotune": [_vp, _vp, _int, _int, ctypes.POINTER(_int), _pdbl],
             "sfg_tune_set": [_vp, _int, _int, _int, _int],
+            "sfg_tune_set_score": [_vp, _int, _int, _int, _int],
             "sfg_tune_table": [_vp, ctypes.c_char_p, _i64, _pi64],
             "sfg_mlp_destroy": [_vp],
             "sfg_mlp_params": [_vp, _vp, _vp],
@@ -597,6 +598,10 @@ def sfg_autotune(ctx, g, K, storage=torch.float32):
 
 def sfg_tune_set(ctx, K, storage, degree_bucket, variant):
     ctx.check(lib().sfg_tune_set(ctx.h, K, _dt(storage), degree_bucket, variant))
+
+
+def sfg_tune_set_score(ctx, K, storage, degree_bucket, shape):
+    ctx.check(lib().sfg_tune_set_score(ctx.h, K, _dt(storage), degree_bucket, shape))
 
 
 def sfg_tune_table(ctx):

@@ -237,6 +237,30 @@ def test_score_same_input(S, ctx, mode, K):
     assert score_err(s.astype(np.float64), ref) < TOL_S
 
 
+@pytest.mark.parametrize("K,dt", [(8, torch.float32), (32, torch.float32), (64, torch.float32),
+                                  (16, torch.bfloat16), (64, torch.bfloat16)])
+def test_score_block_alignment(S, ctx, K, dt):
+    """Blocks that start 16 bytes past a 32-byte boundary (the smallest alignment the call
+    accepts) give the same scores, bit for bit, as 32-byte-aligned copies."""
+    n, u, v, w = gen.random_graph(3000, 12000, seed=23)
+    g, og = make(S, ctx, n, u, v, w)
+    xg = torch.from_numpy(gen.gaussian_block(n, K, seed=3)).to(DEV).to(dt)
+    xp = torch.from_numpy(gen.gaussian_block(n, K, seed=4)).to(DEV).to(dt)
+    ids = dev(np.arange(og.m, dtype=np.int32))
+    ref = S.sfg_score_edges(ctx, g, xg, xp, ids)
+    pad = 16 // xg.element_size()
+    for shift_g, shift_p in [(pad, 0), (0, pad), (pad, pad)]:
+        bg = torch.empty(n * K + 64, dtype=dt, device=DEV)
+        bp = torch.empty(n * K + 64, dtype=dt, device=DEV)
+        assert bg.data_ptr() % 32 == 0 and bp.data_ptr() % 32 == 0
+        yg = bg[shift_g:shift_g + n * K].view(n, K)
+        yp = bp[shift_p:shift_p + n * K].view(n, K)
+        yg.copy_(xg)
+        yp.copy_(xp)
+        s = S.sfg_score_edges(ctx, g, yg, yp, ids)
+        assert torch.equal(s, ref)
+
+
 def test_score_pipeline_grid(S, ctx):
     # smoothed on the GPU vs smoothed by the oracle, then scored: RATIO mode
     n, u, v, w = gen.grid2d(64, 64, seed=1)

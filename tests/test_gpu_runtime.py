@@ -42,10 +42,34 @@ def test_autotune_variants_agree_bit_for_bit(S):
     best, us = S.sfg_autotune(ctx, g, 32)
     assert 0 <= best < 6 and us > 0
     table = S.sfg_tune_table(ctx)
+    assert len(table) == 1 and table[0]["score_shape"] in (0, 1)
     assert table == [{"K": 32, "dtype": 0, "degree_bucket": 2, "variant": best,
                       "tiles_per_warp": [1, 2, 4, 1, 2, 4][best],
-                      "ctas_per_sm": [4, 4, 4, 3, 3, 3][best]}]
+                      "ctas_per_sm": [4, 4, 4, 3, 3, 3][best],
+                      "score_shape": table[0]["score_shape"]}]
     assert torch.equal(S.sfg_jacobi(ctx, g, x0.clone(), 7, 0.7), outs[0])
+
+
+@pytest.mark.parametrize("K,dt", [(4, torch.float32), (32, torch.float32), (64, torch.float32),
+                                  (8, torch.bfloat16), (64, torch.bfloat16)])
+def test_score_shapes_agree_bit_for_bit(S, K, dt):
+    # both launch shapes of the scorer, on a mesh (degree bucket 2) and a denser graph (bucket 3)
+    ctx = S.sfg_ctx_create(0)
+    for n, u, v, w in (gen.grid3d(24, seed=2), gen.knn3d(6000, k=10, seed=3)):
+        g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
+        bucket = int(np.floor(np.log2(2 * g.m / g.n)))
+        xg = torch.from_numpy(gen.gaussian_block(g.n, K, seed=5)).to(DEV).to(dt)
+        xp = torch.from_numpy(gen.gaussian_block(g.n, K, seed=6)).to(DEV).to(dt)
+        ids = dev(np.arange(g.m, dtype=np.int32)[::-1].copy())
+        outs = []
+        for shape in (0, 1, -1):
+            S.sfg_tune_set_score(ctx, K, dt, bucket, shape)
+            for mode in (0, 1, 2):
+                outs.append(S.sfg_score_edges(ctx, g, xg, xp, ids, mode=mode))
+        for i in range(3):
+            assert torch.equal(outs[i], outs[3 + i]) and torch.equal(outs[i], outs[6 + i])
+    with pytest.raises(S.SfgError):
+        S.sfg_tune_set_score(ctx, K, dt, 2, 2)
 
 
 def test_filter_score_and_select_capture_in_a_cuda_graph(S):
@@ -170,3 +194,27 @@ def test_tensor_core_wait_runs_out_and_reports_etimeout():
     lines = r.stdout.split("\n")
     assert lines[0] == "STATUS 4" and lines[1] == "STATUS 4", r.stdout
     assert lines[2] == "OK True"
+
+
+def test_entry_points_keep_the_callers_device(S):
+    """Every call runs on its context's device and gives the caller's current device back. With one
+    GPU this checks that nothing changes the current device; with two, the context lives on device
+    0 while device 1 is current."""
+    other = 1 if torch.cuda.device_count() > 1 else 0
+    torch.cuda.set_device(other)
+    try:
+        ctx = S.sfg_ctx_create(0)
+        assert torch.cuda.current_device() == other
+        n, u, v, w = gen.grid2d(24, 24, seed=4)
+        g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
+        assert torch.cuda.current_device() == other
+        tree, _ = S.sfg_spanning_tree(ctx, g)
+        x = S.sfg_smooth(ctx, g, 8, 5, 0.7, 11)
+        mask, _ = S.sfg_sparsify(ctx, g, K=8, steps=5, budget_frac=0.05, budget_unit=0)
+        assert torch.cuda.current_device() == other
+        assert x.device == DEV and mask.device == DEV and tree.device == DEV
+        torch.cuda.synchronize(DEV)
+        assert torch.isfinite(x).all()
+        assert int(mask.sum()) >= n - 1
+    finally:
+        torch.cuda.set_device(0)
