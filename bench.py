@@ -388,26 +388,31 @@ def time_batch(S, ctx, dev, specs, steps, warmup, peak, peak_kind, K_=16, T_=15,
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()
     bctx = S.sfg_ctx_create(dev.index, stream)
-    with torch.cuda.stream(stream):
-        plan = S.Batch(bctx, graphs, K=K_, steps=T_, budget_frac=beta, autotune=True)
-        ref = plan.run(SEED)
-        out = torch.empty_like(ref)
-    stream.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
-        plan.run(SEED, out=out)
-    with torch.cuda.stream(stream):     # replays run on the current stream: time them there
-        for _ in range(warmup):
-            graph.replay()
+    def timed(locality):
+        with torch.cuda.stream(stream):
+            plan = S.Batch(bctx, graphs, K=K_, steps=T_, budget_frac=beta, autotune=True,
+                           locality=locality)
+            ref = plan.run(SEED)
+            out = torch.empty_like(ref)
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+            plan.run(SEED, out=out)
+        with torch.cuda.stream(stream):     # replays run on the current stream: time them there
+            for _ in range(warmup):
+                graph.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                graph.replay()
+            e1.record(stream)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            graph.replay()
-        e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    assert torch.equal(out, ref)
+        assert torch.equal(out, ref)
+        return plan, e0.elapsed_time(e1) / steps
+
+    _, ms_input_order = timed(False)
+    plan, ms = timed(True)
     n_all = sum(g.n for g in graphs)
     m_all = sum(g.m for g in graphs)
     # union sizes: G has 2 m_all entries; P, the forests, 2 (count_g - k_g) entries per graph, with
@@ -422,7 +427,9 @@ def time_batch(S, ctx, dev, specs, steps, warmup, peak, peak_kind, K_=16, T_=15,
            "graphs": len(graphs), "nodes": n_all, "edges": m_all, "ms_per_batch": ms,
            "value": len(graphs) / (ms * 1e-3), "unit": "graphs/s", "bytes_per_batch": b_step,
            "GBps": gbs, "frac_of_peak": gbs / peak, "peak_kind": peak_kind,
-           "how": "sfg_batch_run captured in a CUDA graph and replayed (plan built once)"}
+           "how": "sfg_batch_run captured in a CUDA graph and replayed (plan built once, nodes in "
+                  "locality order)",
+           "ms_per_batch_input_order": ms_input_order}
     return res, graphs, plan, bctx
 
 

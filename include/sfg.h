@@ -336,9 +336,18 @@ SFG_API sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* c
 
 /* Batch plan: the same batched flat method split into a plan, built once per set of graphs, and
  * runs of it. sfg_batch_create (synchronises) joins the graphs, computes every graph's spanning
- * forest, candidate edges and budget (params as sfg_sparsify_batched; params->seed is not used)
- * and, when autotune != 0, times the sweep's tile shapes on the union of the graphs and on the
- * union of their forests and records the fastest in ctx's table (sfg_autotune). sfg_batch_run
+ * forest, candidate edges and budget (params as sfg_sparsify_batched; params->seed is not used).
+ * flags (bits; any other bit is SFG_EINVAL):
+ *  - SFG_BATCH_AUTOTUNE: time the sweep's tile shapes and the scorer's launch shapes on the union
+ *    of the graphs and on the union of their forests and record the fastest in ctx's table
+ *    (sfg_autotune);
+ *  - SFG_BATCH_LOCALITY: renumber each graph's nodes internally by breadth-first level from a
+ *    pseudo-peripheral root (not in the paper; a memory-locality device for graphs whose input
+ *    order scatters neighbours, e.g. k-NN graphs of unsorted points). Seeded rows are drawn from
+ *    the original node ids, forest ties and the selection use the original edge ids, and masks
+ *    come out in the original edge order, so the result is the plan's without the flag up to FP32
+ *    summation order in the sweeps and column statistics.
+ * sfg_batch_run
  * writes the sparsifiers of all graphs for one seed into mask_out (a device buffer of
  * edges_host entries: graph g's m_g edges at [edge_offsets_host[g], edge_offsets_host[g + 1]),
  * in its canonical order); it only queues kernels and stream-ordered allocations on ctx's stream
@@ -348,8 +357,10 @@ SFG_API sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* c
  * NULL). The plan holds its own copy of the graphs: they may be destroyed after
  * sfg_batch_create. */
 typedef struct sfg_batch sfg_batch;
+#define SFG_BATCH_AUTOTUNE 1
+#define SFG_BATCH_LOCALITY 2
 SFG_API sfg_status sfg_batch_create(sfg_ctx* ctx, int ng, const sfg_graph* const* gs,
-                                    const sfg_params* params, int autotune, sfg_batch** out);
+                                    const sfg_params* params, int flags, sfg_batch** out);
 SFG_API sfg_status sfg_batch_info(const sfg_batch* b, int* ng_host, int64_t* edges_host,
                                   int64_t* edge_offsets_host, int64_t* n_selected_host);
 SFG_API sfg_status sfg_batch_run(sfg_ctx* ctx, const sfg_batch* b, uint64_t seed,

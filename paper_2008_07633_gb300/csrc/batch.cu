@@ -17,6 +17,15 @@
 // removal, the projection scales, the budgets and the top-k -- are segmented by graph. Each
 // graph's result is the one sfg_sparsify gives for it alone with the same parameters (up to FP32
 // summation order in the column statistics).
+//
+// Locality order (optional): the nodes of each graph are renumbered by breadth-first level from a
+// pseudo-peripheral root (a stable sort by (graph, level), so ties keep their order), and the
+// plan works on the relabelled union. Neighbours then sit a few levels apart instead of anywhere
+// in the graph, so the sweeps' and the scorer's row gathers hit L2 (random-order k-NN graphs: about
+// twice as fast). Everything that decides the result keeps the original numbering: the seeded row
+// of a node is drawn from its original id, the spanning forest breaks weight ties by original edge
+// id, and top-k selects by original edge id; the masks come out in the original edge order. The
+// result is the unreordered plan's up to FP32 summation order in the sweeps and statistics.
 #include <cmath>
 #include <vector>
 
@@ -132,6 +141,110 @@ __global__ void k_split(int64_t m, const uint8_t* __restrict__ mask, int ng,
     }
 }
 
+// ---- locality order ---------------------------------------------------------------------------
+__global__ void k_bfs_seed(int ng, const int32_t* __restrict__ noff, const int32_t* __restrict__ roots,
+                           int32_t* __restrict__ level) {
+    for (int g = (int)(blockIdx.x * kBlock + threadIdx.x); g < ng; g += gridDim.x * kBlock)
+        if (noff[g + 1] > noff[g]) level[roots ? roots[g] : noff[g]] = 0;
+}
+
+// one breadth-first level: every node of level cur labels its unlabelled neighbours cur + 1 (all
+// writers of a node store the same value)
+__global__ void k_bfs_step(int32_t n, const int32_t* __restrict__ row_ptr, const int2* __restrict__ colval,
+                           int32_t cur, int32_t* __restrict__ level, int* __restrict__ flag) {
+    for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * kBlock) {
+        if (level[v] != cur) continue;
+        bool any = false;
+        for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+            const int32_t w = colval[j].x;
+            if (level[w] < 0) {
+                level[w] = cur + 1;
+                any = true;
+            }
+        }
+        if (any) *flag = 1;
+    }
+}
+
+// per graph, the labelled node of the largest level (ties: the smallest id)
+__global__ void k_bfs_far(int32_t n, const int32_t* __restrict__ noff, int ng,
+                          const int32_t* __restrict__ level, unsigned long long* __restrict__ best) {
+    for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * kBlock) {
+        const int32_t l = level[v];
+        if (l < 0) continue;
+        const int g = seg_of(noff, ng, v);
+        atomicMax(&best[g], ((unsigned long long)(uint32_t)l << 32) | (unsigned long long)(~(uint32_t)v));
+    }
+}
+
+__global__ void k_bfs_roots(int ng, const unsigned long long* __restrict__ best,
+                            const int32_t* __restrict__ noff, int32_t* __restrict__ roots) {
+    for (int g = (int)(blockIdx.x * kBlock + threadIdx.x); g < ng; g += gridDim.x * kBlock)
+        roots[g] = best[g] ? (int32_t)(~(uint32_t)(best[g] & 0xffffffffull)) : noff[g];
+}
+
+// sort key (graph, level; unreached nodes after the deepest level) and the node id as value
+__global__ void k_order_keys(int32_t n, const int32_t* __restrict__ noff, int ng,
+                             const int32_t* __restrict__ level, int32_t unreached, int lbits,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * kBlock) {
+        const int32_t l = level[v] >= 0 ? level[v] : unreached;
+        keys[v] = ((uint64_t)seg_of(noff, ng, v) << lbits) | (uint64_t)l;
+        vals[v] = (uint32_t)v;
+    }
+}
+
+// perm (new -> old) to inv (old -> new) and the original graph-local id of every new row
+__global__ void k_order_maps(int32_t n, const uint32_t* __restrict__ perm, const int32_t* __restrict__ noff,
+                             int ng, int32_t* __restrict__ inv, int32_t* __restrict__ orig_local) {
+    for (int64_t r = (int64_t)blockIdx.x * kBlock + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * kBlock) {
+        const int32_t old = (int32_t)perm[r];
+        inv[old] = (int32_t)r;
+        orig_local[r] = old - noff[seg_of(noff, ng, old)];
+    }
+}
+
+__global__ void k_relabel(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                          const int32_t* __restrict__ inv, int32_t* __restrict__ u2,
+                          int32_t* __restrict__ v2) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock) {
+        u2[e] = inv[eu[e]];
+        v2[e] = inv[ev[e]];
+    }
+}
+
+__global__ void k_invert(int64_t m, const int32_t* __restrict__ f, int32_t* __restrict__ finv) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock)
+        finv[f[e]] = (int32_t)e;
+}
+
+__global__ void k_gather_ids(int64_t k, const int32_t* __restrict__ ids, const int32_t* __restrict__ map,
+                             int32_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < k;
+         i += (int64_t)gridDim.x * kBlock)
+        out[i] = map[ids[i]];
+}
+
+// mask[map[e]] = src[e]: the forest, written in the original edge order
+__global__ void k_scatter_mask(int64_t m, const uint8_t* __restrict__ src, const int32_t* __restrict__ map,
+                               uint8_t* __restrict__ mask) {
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * kBlock)
+        mask[map[e]] = src[e];
+}
+
+int bits_of(int64_t x) {  // bits needed to hold 0 .. x
+    int b = 1;
+    while (b < 62 && (1ll << b) <= x) ++b;
+    return b;
+}
+
 template <typename K>
 int grid_of(sfg_ctx* ctx, K kernel, int64_t work) {
     return sfg_grid(ctx, (const void*)kernel, kBlock, 0, work);
@@ -162,6 +275,11 @@ struct sfg_batch {
     int64_t* d_k = nullptr;    // per-graph budgets
     uint8_t* forest = nullptr; // m: the forests' edges
     int32_t* cand = nullptr;   // ncand candidate ids (union edge ids, ascending, grouped by graph)
+    // locality order (NULL without it): the original graph-local id of every union row, the
+    // original union edge id of every edge, and the candidates' original ids
+    int32_t* orig_local = nullptr;
+    int32_t* orig_edge = nullptr;
+    int32_t* cand_orig = nullptr;
     std::vector<int64_t> eoff, counts;
     cudaStream_t stream = nullptr;
 };
@@ -171,7 +289,8 @@ static void batch_free(sfg_batch* b) {
     SfgDeviceGuard guard(b->device);
     sfg_graph_free(b->U);
     sfg_graph_free(b->PU);
-    void* ptrs[] = {b->d_noff, b->d_eoff, b->d_coff, b->d_k, b->forest, b->cand};
+    void* ptrs[] = {b->d_noff, b->d_eoff, b->d_coff, b->d_k, b->forest, b->cand,
+                    b->orig_local, b->orig_edge, b->cand_orig};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, b->stream);
     delete b;
@@ -191,8 +310,91 @@ static sfg_status check_batch_params(sfg_ctx* ctx, const sfg_params* P) {
     return SFG_OK;
 }
 
+// Breadth-first renumbering of the union (see the file comment): b->U is replaced by its
+// relabelled copy; f2c receives the new id of every original union edge.
+static sfg_status batch_reorder(sfg_ctx* ctx, sfg_batch* b, int32_t* f2c) {
+    const int32_t n = b->n;
+    const int64_t m = b->m;
+    const int ng = b->ng;
+    Scratch s(ctx);
+    int32_t *level, *roots, *inv, *u2, *v2;
+    unsigned long long* best;
+    int* flag;
+    uint64_t *keys, *keys2;
+    uint32_t *vals, *vals2;
+    SFG_TRY(s.get(&level, n));
+    SFG_TRY(s.get(&roots, ng));
+    SFG_TRY(s.get(&best, ng));
+    SFG_TRY(s.get(&flag, 1));
+    SFG_TRY(s.get(&keys, n));
+    SFG_TRY(s.get(&keys2, n));
+    SFG_TRY(s.get(&vals, n));
+    SFG_TRY(s.get(&vals2, n));
+    SFG_TRY(s.get(&inv, n));
+    SFG_TRY(s.get(&u2, m));
+    SFG_TRY(s.get(&v2, m));
+    int* hflag = nullptr;
+    SFG_TRY(sfg_host_word(ctx, 3, &hflag));
+    const sfg_graph* U = b->U;
+    const int gn = grid_of(ctx, k_bfs_step, n), gg = grid_of(ctx, k_bfs_seed, ng);
+    int32_t depth = 0;
+    // two searches: the second starts from the farthest node the first reached in each graph
+    for (int pass = 0; pass < 2; ++pass) {
+        SFG_CUDA(ctx, cudaMemsetAsync(level, 0xff, 4 * (size_t)n, ctx->stream));
+        k_bfs_seed<<<gg, kBlock, 0, ctx->stream>>>(ng, b->d_noff, pass ? roots : nullptr, level);
+        ++ctx->launches;
+        for (depth = 0;; ++depth) {
+            if (depth >= n) return sfg_fail(ctx, SFG_ETIMEOUT, "breadth-first search did not end");
+            SFG_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+            k_bfs_step<<<gn, kBlock, 0, ctx->stream>>>(n, U->row_ptr, U->colval, depth, level, flag);
+            ++ctx->launches;
+            SFG_CUDA(ctx, cudaMemcpyAsync(hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            SFG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            if (!*hflag) break;
+        }
+        if (pass == 0) {
+            SFG_CUDA(ctx, cudaMemsetAsync(best, 0, 8 * (size_t)ng, ctx->stream));
+            k_bfs_far<<<gn, kBlock, 0, ctx->stream>>>(n, b->d_noff, ng, level, best);
+            k_bfs_roots<<<gg, kBlock, 0, ctx->stream>>>(ng, best, b->d_noff, roots);
+            ctx->launches += 2;
+        }
+        SFG_LAUNCH_CHECK(ctx, "breadth-first search");
+    }
+    // stable sort of the nodes by (graph, level): depth is the deepest level
+    const int lbits = bits_of((int64_t)depth + 1);
+    k_order_keys<<<gn, kBlock, 0, ctx->stream>>>(n, b->d_noff, ng, level, depth + 1, lbits, keys, vals);
+    ++ctx->launches;
+    SFG_TRY(sfg_radix_sort_pairs(ctx, &keys, &vals, &keys2, &vals2, n, lbits + bits_of(ng)));
+    SFG_TRY(sfg_alloc(ctx, (void**)&b->orig_local, 4 * (size_t)n + 16));
+    k_order_maps<<<gn, kBlock, 0, ctx->stream>>>(n, vals, b->d_noff, ng, inv, b->orig_local);
+    ++ctx->launches;
+    // the relabelled union, canonicalised again; f2c maps old edge ids to new ones
+    sfg_graph* U2 = nullptr;
+    if (m > 0) {
+        k_relabel<<<grid_of(ctx, k_relabel, m), kBlock, 0, ctx->stream>>>(m, U->eu, U->ev, inv, u2, v2);
+        ++ctx->launches;
+    }
+    SFG_LAUNCH_CHECK(ctx, "locality order");
+    SFG_TRY(sfg_build_graph(ctx, n, m, u2, v2, U->ew, false, &U2, f2c));
+    if (U2->m != m) {
+        sfg_graph_free(U2);
+        return sfg_fail(ctx, SFG_EINVAL, "relabelled union lost edges");
+    }
+    SFG_TRY(sfg_alloc(ctx, (void**)&b->orig_edge, 4 * (size_t)m + 16));
+    if (m > 0) {
+        k_invert<<<grid_of(ctx, k_invert, m), kBlock, 0, ctx->stream>>>(m, f2c, b->orig_edge);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_invert");
+    }
+    sfg_graph_free(b->U);
+    b->U = U2;
+    return SFG_OK;
+}
+
 static sfg_status batch_build(sfg_ctx* ctx, int ng, const sfg_graph* const* gs, const sfg_params* P,
-                              int autotune, sfg_batch* b) {
+                              int flags, sfg_batch* b) {
+    const bool autotune = (flags & SFG_BATCH_AUTOTUNE) != 0;
+    const bool locality = (flags & SFG_BATCH_LOCALITY) != 0;
     b->device = ctx->device;
     b->stream = ctx->stream;
     b->ng = ng;
@@ -244,9 +446,17 @@ static sfg_status batch_build(sfg_ctx* ctx, int ng, const sfg_graph* const* gs, 
     ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_union");
 
-    // spanning forests of every graph, per-graph forest sizes
+    // locality order: the plan continues on the relabelled union
+    int32_t* f2c = nullptr;
+    if (locality && n > 0) {
+        SFG_TRY(s.get(&f2c, m + 1));
+        SFG_TRY(batch_reorder(ctx, b, f2c));
+    }
+
+    // spanning forests of every graph, per-graph forest sizes (weight ties broken by original id)
     int64_t n_tree = 0;
-    SFG_TRY(sfg_mst_impl(ctx, b->U, nullptr, b->forest, &n_tree));
+    SFG_TRY(sfg_mst_impl(ctx, b->U, nullptr, b->forest, &n_tree, nullptr, b->orig_edge,
+                         b->orig_edge ? f2c : nullptr));
     std::vector<int64_t> tree(ng, 0);
     SFG_CUDA(ctx, cudaMemsetAsync(d_cnt, 0, 8 * ng, ctx->stream));
     if (m > 0) {
@@ -288,6 +498,13 @@ static sfg_status batch_build(sfg_ctx* ctx, int ng, const sfg_graph* const* gs, 
         k_compact<<<grid_of(ctx, k_compact, m), kBlock, 0, ctx->stream>>>(m, flag, pos, b->cand);
         ++ctx->launches;
         SFG_LAUNCH_CHECK(ctx, "k_compact");
+        if (b->orig_edge) {  // the candidates under their original ids, for the selection
+            SFG_TRY(sfg_alloc(ctx, (void**)&b->cand_orig, 4 * (size_t)b->ncand + 16));
+            k_gather_ids<<<grid_of(ctx, k_gather_ids, b->ncand), kBlock, 0, ctx->stream>>>(
+                b->ncand, b->cand, b->orig_edge, b->cand_orig);
+            ++ctx->launches;
+            SFG_LAUNCH_CHECK(ctx, "k_gather_ids");
+        }
         SFG_TRY(sfg_subgraph_impl(ctx, b->U, b->forest, &b->PU));
         // one-time per-graph structures the sweeps use, built here so that runs never synchronise
         SFG_TRY(sfg_heavy_prepare(ctx, b->U));
@@ -304,8 +521,14 @@ static sfg_status batch_build(sfg_ctx* ctx, int ng, const sfg_graph* const* gs, 
 // The numeric part: forest copied into mask (m entries, union edge order), then the top-scored
 // candidates of every graph added. Launches and stream-ordered allocations only.
 static sfg_status batch_run(sfg_ctx* ctx, const sfg_batch* b, uint64_t seed, uint8_t* mask) {
-    if (b->m > 0)
+    if (b->m > 0 && b->orig_edge) {
+        k_scatter_mask<<<grid_of(ctx, k_scatter_mask, b->m), kBlock, 0, ctx->stream>>>(
+            b->m, b->forest, b->orig_edge, mask);
+        ++ctx->launches;
+        SFG_LAUNCH_CHECK(ctx, "k_scatter_mask");
+    } else if (b->m > 0) {
         SFG_CUDA(ctx, cudaMemcpyAsync(mask, b->forest, (size_t)b->m, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     if (b->k_total == 0) return SFG_OK;
     Scratch s(ctx);
     int32_t* sel;
@@ -313,10 +536,12 @@ static sfg_status batch_run(sfg_ctx* ctx, const sfg_batch* b, uint64_t seed, uin
     SFG_TRY(s.get(&scores, b->ncand));
     SFG_TRY(s.get(&sel, b->k_total));
     const sfg_params& P = b->P;
-    SFG_TRY(sfg_filter_score_batched_impl(ctx, b->U, b->PU, b->ng, b->d_noff, P.K, P.steps, P.omega,
-                                          seed, P.storage, b->cand, b->ncand, P.mode, scores));
-    SFG_TRY(sfg_topk_segmented_impl(ctx, scores, b->cand, b->ncand, b->ng, b->d_coff, b->d_k,
-                                    b->k_total, sel));
+    SFG_TRY(sfg_filter_score_batched_impl(ctx, b->U, b->PU, b->orig_local, b->ng, b->d_noff, P.K,
+                                          P.steps, P.omega, seed, P.storage, b->cand, b->ncand,
+                                          P.mode, scores));
+    // selection under original edge ids (ties and the output order as without the reordering)
+    SFG_TRY(sfg_topk_segmented_impl(ctx, scores, b->cand_orig ? b->cand_orig : b->cand, b->ncand,
+                                    b->ng, b->d_coff, b->d_k, b->k_total, sel));
     k_mark<<<grid_of(ctx, k_mark, b->k_total), kBlock, 0, ctx->stream>>>(b->k_total, sel, mask);
     ++ctx->launches;
     SFG_LAUNCH_CHECK(ctx, "k_mark");
@@ -326,7 +551,7 @@ static sfg_status batch_run(sfg_ctx* ctx, const sfg_batch* b, uint64_t seed, uin
 extern "C" {
 
 sfg_status sfg_batch_create(sfg_ctx* ctx, int ng, const sfg_graph* const* gs, const sfg_params* P,
-                            int autotune, sfg_batch** out) {
+                            int flags, sfg_batch** out) {
     if (!ctx) return SFG_EINVAL;
     SFG_DEVICE(ctx);
     if (!out) return sfg_fail(ctx, SFG_EINVAL, "out is NULL");
@@ -334,7 +559,11 @@ sfg_status sfg_batch_create(sfg_ctx* ctx, int ng, const sfg_graph* const* gs, co
     if (ng < 1 || !gs || !P) return sfg_fail(ctx, SFG_EINVAL, "bad batch arguments");
     SFG_TRY(check_batch_params(ctx, P));
     sfg_batch* b = new sfg_batch();
-    const sfg_status st = batch_build(ctx, ng, gs, P, autotune, b);
+    if (flags & ~(SFG_BATCH_AUTOTUNE | SFG_BATCH_LOCALITY)) {
+        delete b;
+        return sfg_fail(ctx, SFG_EINVAL, "unknown batch flags %d", flags);
+    }
+    const sfg_status st = batch_build(ctx, ng, gs, P, flags, b);
     if (st != SFG_OK) {
         batch_free(b);
         return st;

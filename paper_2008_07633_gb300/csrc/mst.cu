@@ -45,12 +45,14 @@ struct MstItem {
 __device__ __forceinline__ unsigned long long mst_key(int32_t j, int32_t cp, const int2* __restrict__ colval,
                                                       const int32_t* __restrict__ eid,
                                                       const uint8_t* __restrict__ allow,
-                                                      const int32_t* __restrict__ comp) {
+                                                      const int32_t* __restrict__ comp,
+                                                      const int32_t* __restrict__ key_id) {
     const int2 cv = colval[j];
     if (comp[cv.x] == cp) return 0ull;
     const int32_t e = eid[j];
     if (allow && !allow[e]) return 0ull;
-    return ((unsigned long long)(uint32_t)cv.y << 32) | (unsigned long long)(~(uint32_t)e);
+    const uint32_t id = key_id ? (uint32_t)key_id[e] : (uint32_t)e;
+    return ((unsigned long long)(uint32_t)cv.y << 32) | (unsigned long long)(~id);
 }
 
 template <bool SEG>
@@ -60,6 +62,7 @@ __global__ void __launch_bounds__(kBlock) k_mst_rows(int64_t nitems, const int32
                                                      const int32_t* __restrict__ eid,
                                                      const uint8_t* __restrict__ allow,
                                                      const int32_t* __restrict__ comp,
+                                                     const int32_t* __restrict__ key_id,
                                                      unsigned long long* __restrict__ best) {
     const int sub = threadIdx.x % kMstLanes;
     const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kMstLanes;
@@ -100,14 +103,15 @@ __global__ void __launch_bounds__(kBlock) k_mst_rows(int64_t nitems, const int32
 #pragma unroll
         for (int u = 0; u < kMstItems; ++u) {
             const bool out = comp[cv[u].x] != it[u].cp && (!allow || allow[e[u]]);
+            const uint32_t id = key_id ? (uint32_t)key_id[e[u]] : (uint32_t)e[u];
             it[u].best = out ? ((unsigned long long)(uint32_t)cv[u].y << 32) |
-                                   (unsigned long long)(~(uint32_t)e[u])
+                                   (unsigned long long)(~id)
                              : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < kMstItems; ++u)
             for (int32_t j = it[u].a + sub + kMstLanes; j < it[u].b; j += kMstLanes) {
-                const unsigned long long key = mst_key(j, it[u].cp, colval, eid, allow, comp);
+                const unsigned long long key = mst_key(j, it[u].cp, colval, eid, allow, comp, key_id);
                 it[u].best = key > it[u].best ? key : it[u].best;
             }
 #pragma unroll
@@ -125,8 +129,8 @@ __global__ void __launch_bounds__(kBlock) k_mst_rows(int64_t nitems, const int32
 
 __global__ void k_mst_hook(int32_t n, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
                            const int32_t* __restrict__ comp, const unsigned long long* __restrict__ best,
-                           int32_t* __restrict__ parent, uint8_t* __restrict__ mask,
-                           int* __restrict__ flag) {
+                           const int32_t* __restrict__ key_inv, int32_t* __restrict__ parent,
+                           uint8_t* __restrict__ mask, int* __restrict__ flag) {
     for (int64_t r = (int64_t)blockIdx.x * kBlock + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * kBlock) {
         if (comp[r] != r) continue;  // only component labels act
@@ -135,7 +139,8 @@ __global__ void k_mst_hook(int32_t n, const int32_t* __restrict__ eu, const int3
             parent[r] = (int32_t)r;
             continue;
         }
-        const uint32_t e = ~(uint32_t)(b & 0xffffffffull);
+        const uint32_t id = ~(uint32_t)(b & 0xffffffffull);
+        const uint32_t e = key_inv ? (uint32_t)key_inv[id] : id;
         mask[e] = 1;
         const int32_t a = comp[eu[e]], c = comp[ev[e]];
         parent[r] = (a == r) ? c : a;
@@ -235,7 +240,8 @@ sfg_status sfg_count_mask(sfg_ctx* ctx, const uint8_t* mask, int64_t m, int64_t*
 }
 
 sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, uint8_t* mask,
-                        int64_t* n_tree, int32_t* comp_out) {
+                        int64_t* n_tree, int32_t* comp_out, const int32_t* key_id,
+                        const int32_t* key_inv) {
     const int32_t n = g->n;
     const int64_t m = g->m;
     if (m > 0) SFG_CUDA(ctx, cudaMemsetAsync(mask, 0, m, ctx->stream));
@@ -274,16 +280,18 @@ sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, 
         sfg_toc(ctx);
         sfg_tic(ctx, "mst_rows");
         k_mst_rows<false><<<gr, kBlock, 0, ctx->stream>>>(n, g->row_ptr, nullptr, g->colval, g->eid,
-                                                          allow, comp, best);
+                                                          allow, comp, key_id, best);
         ++ctx->launches;
         if (gs > 0) {
             k_mst_rows<true><<<gs, kBlock, 0, ctx->stream>>>(g->hv_nseg, nullptr, g->hv_seg, g->colval,
-                                                             g->eid, allow, comp, best);
+                                                             g->eid, allow, comp, key_id, best);
             ++ctx->launches;
         }
         sfg_toc(ctx);
         sfg_tic(ctx, "mst_hook");
-        k_mst_hook<<<gn, kBlock, 0, ctx->stream>>>(n, g->eu, g->ev, comp, best, parent, mask, flag); ++ctx->launches;
+        k_mst_hook<<<gn, kBlock, 0, ctx->stream>>>(n, g->eu, g->ev, comp, best, key_inv, parent, mask,
+                                                   flag);
+        ++ctx->launches;
         sfg_toc(ctx);
         SFG_LAUNCH_CHECK(ctx, "k_mst_round");
         // The round's "any hook" flag travels with the pointer-jumping readback: a round in

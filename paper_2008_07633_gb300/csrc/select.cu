@@ -154,7 +154,8 @@ extern "C" sfg_status sfg_select_topk(sfg_ctx* ctx, const float* scores, const i
 // ------------------------------------------------------------------------------------------------
 // Segmented top-k (one selection per graph of a batch): the same MSB-first radix select, with one
 // histogram and one (prefix, remaining k) state per segment. Candidates are contiguous per
-// segment; each lane finds its segment by a binary search seeded once per warp.
+// segment; each warp sweeps one contiguous range of them, 32 at a time, so its segment (found once
+// by a binary search) advances by a few steps at most and its state stays in registers.
 // ------------------------------------------------------------------------------------------------
 namespace {
 
@@ -181,20 +182,36 @@ __global__ void k_segsel_init(int nseg, const int64_t* __restrict__ k, SegSel* _
     }
 }
 
+// The contiguous item range [lo, hi) of this warp: ne split into equal chunks of whole 32-item steps.
+__device__ __forceinline__ void warp_range(int64_t ne, int64_t& lo, int64_t& hi) {
+    const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
+    const int64_t w = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int64_t steps = (ne + 31) / 32, per = (steps + nw - 1) / nw;
+    lo = min(ne, w * per * 32);
+    hi = min(ne, (w + 1) * per * 32);
+}
+
 __global__ void __launch_bounds__(kBlock)
     k_segsel_hist(int64_t ne, const float* __restrict__ scores, const int32_t* __restrict__ ids,
                   int nseg, const int64_t* __restrict__ off, const SegSel* __restrict__ st,
                   int shift, unsigned long long* __restrict__ hist) {
     const int hi = shift + 8;
-    for (int64_t base = (int64_t)blockIdx.x * kBlock + (threadIdx.x & ~31); base < ne;
-         base += (int64_t)gridDim.x * kBlock) {
+    int64_t lo_i, hi_i;
+    warp_range(ne, lo_i, hi_i);
+    if (lo_i >= hi_i) return;
+    int s = seg_of(off, nseg, lo_i);  // this lane's segment, advanced as the range moves on
+    int64_t s_end = off[s + 1];
+    SegSel ss = st[s];
+    for (int64_t base = lo_i; base < hi_i; base += 32) {
         const int64_t i = base + (threadIdx.x & 31);
-        int s = seg_of(off, nseg, base);
         bool take = false;
         int digit = 0;
-        if (i < ne) {
-            while (off[s + 1] <= i) ++s;
-            const SegSel ss = st[s];
+        if (i < hi_i) {
+            if (i >= s_end) {
+                do ++s; while (off[s + 1] <= i);
+                s_end = off[s + 1];
+                ss = st[s];
+            }
             const uint64_t key = sel_key(scores[i], ids[i]);
             take = ss.krem > 0 && (hi >= 64 || (key >> hi) == (ss.prefix >> hi));
             digit = (int)((key >> shift) & 0xff);
@@ -232,14 +249,25 @@ __global__ void k_segsel_pick(int shift, SegSel* __restrict__ st, unsigned long 
     h[d] = 0ull;
 }
 
-__global__ void k_segsel_flags(int64_t ne, const float* __restrict__ scores,
-                               const int32_t* __restrict__ ids, int nseg,
-                               const int64_t* __restrict__ off, const SegSel* __restrict__ st,
-                               const int64_t* __restrict__ k, uint8_t* __restrict__ flag) {
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < ne;
-         i += (int64_t)gridDim.x * kBlock) {
-        const int s = seg_of(off, nseg, i);
-        flag[i] = k[s] > 0 && sel_key(scores[i], ids[i]) >= st[s].prefix;
+__global__ void __launch_bounds__(kBlock)
+    k_segsel_flags(int64_t ne, const float* __restrict__ scores, const int32_t* __restrict__ ids,
+                   int nseg, const int64_t* __restrict__ off, const SegSel* __restrict__ st,
+                   const int64_t* __restrict__ k, uint8_t* __restrict__ flag) {
+    int64_t lo_i, hi_i;
+    warp_range(ne, lo_i, hi_i);
+    if (lo_i >= hi_i) return;
+    int s = seg_of(off, nseg, lo_i);
+    int64_t s_end = off[s + 1];
+    bool on = k[s] > 0;
+    uint64_t thr = st[s].prefix;
+    for (int64_t i = lo_i + (threadIdx.x & 31); i < hi_i; i += 32) {
+        if (i >= s_end) {
+            do ++s; while (off[s + 1] <= i);
+            s_end = off[s + 1];
+            on = k[s] > 0;
+            thr = st[s].prefix;
+        }
+        flag[i] = on && sel_key(scores[i], ids[i]) >= thr;
     }
 }
 

@@ -190,8 +190,12 @@ sfg_status sfg_build_graph(sfg_ctx* ctx, int32_t n, int64_t m, const int32_t* u,
 sfg_status sfg_subgraph_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* mask,
                              sfg_graph** out);
 // comp_out (optional, n entries): each node's component label, a node of that component.
+// key_id (m entries, may be NULL): the id that breaks weight ties for edge e (default e), with
+// key_inv its inverse; a relabelled copy of a graph passes its original edge ids, so that its
+// forest is the original graph's forest edge for edge.
 sfg_status sfg_mst_impl(sfg_ctx* ctx, const sfg_graph* g, const uint8_t* allow, uint8_t* mask,
-                        int64_t* n_tree, int32_t* comp_out = nullptr);
+                        int64_t* n_tree, int32_t* comp_out = nullptr,
+                        const int32_t* key_id = nullptr, const int32_t* key_inv = nullptr);
 sfg_status sfg_smooth_impl(sfg_ctx* ctx, const sfg_graph* L, int K, int steps, double omega,
                            uint64_t seed, sfg_dtype storage, void* X_out);
 // sg, sp (may be NULL): per-column scales applied to raw blocks (projection folded in).
@@ -203,7 +207,10 @@ sfg_status sfg_score_batched_impl(sfg_ctx* ctx, const sfg_graph* LG, const void*
                                   const void* XP, int K, sfg_dtype storage, const int32_t* ids,
                                   int64_t ne, sfg_score_mode mode, float* out, const float* sg,
                                   const float* sp, const int32_t* node_off, int ngraphs);
+// orig_local (n entries, may be NULL): the graph-local node id whose seeded row row r carries
+// (default r - node_off[g]), for unions whose nodes were reordered.
 sfg_status sfg_filter_score_batched_impl(sfg_ctx* ctx, const sfg_graph* U, const sfg_graph* PU,
+                                         const int32_t* orig_local,
                                          int ng, const int32_t* node_off, int K, int steps,
                                          double omega, uint64_t seed, sfg_dtype storage,
                                          const int32_t* ids, int64_t ne, sfg_score_mode mode,

@@ -805,14 +805,16 @@ __device__ __forceinline__ int32_t graph_of(const int32_t* __restrict__ off, int
 template <typename T, int LPR>
 __global__ void __launch_bounds__(kBlock) k_init_batched(int32_t n, uint64_t seed,
                                                          const int32_t* __restrict__ node_off,
-                                                         int ng, T* __restrict__ X) {
+                                                         int ng, const int32_t* __restrict__ orig_local,
+                                                         T* __restrict__ X) {
     constexpr int E = Vec<T>::E, K = LPR * E;
     const int lane = threadIdx.x & 31, sub = lane % LPR;
     const int64_t g0 = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LPR;
     const int64_t ng_ = (int64_t)gridDim.x * kBlock / LPR;
     const uint64_t s0 = sfg_splitmix64(seed);
     for (int64_t row = g0; row < n; row += ng_) {
-        const int64_t local = row - node_off[graph_of(node_off, ng, row)];
+        const int64_t local = orig_local ? (int64_t)orig_local[row]
+                                         : row - node_off[graph_of(node_off, ng, row)];
         float x[E];
 #pragma unroll
         for (int e = 0; e < E; e += 2) {
@@ -825,19 +827,25 @@ __global__ void __launch_bounds__(kBlock) k_init_batched(int32_t n, uint64_t see
     }
 }
 
-// Per-graph column sums and sums of squares (FP64) of X: one CTA per graph; each LPR-lane group
-// folds 64-row chunks in FP32 into FP64, then a fixed-shape tree across the CTA.
+// Per-graph column sums and sums of squares (FP64) of X. Every graph's rows are cut into
+// kSegSlices equal contiguous slices, one CTA per (graph, slice): each LPR-lane group folds 64-row
+// chunks in FP32 (the chunk's rows loaded 8 at a time, accumulated in row order) into FP64, then a
+// fixed-shape tree across the CTA gives the slice's partials; k_seg_reduce adds a graph's slices in
+// slice order. The partition does not depend on the launch, so the sums are deterministic.
 // deg != NULL: sums of d_i x_ik and of d_i instead (the D-weighted means, see k_init).
+constexpr int kSegSlices = 32;
+
 template <typename T, int LPR>
 __global__ void __launch_bounds__(kBlock) k_seg_stats(const T* __restrict__ X,
                                                       const int32_t* __restrict__ node_off,
                                                       const double* __restrict__ deg,
-                                                      double* __restrict__ stats) {
-    constexpr int E = Vec<T>::E, K = LPR * E, GPB = kBlock / LPR;
+                                                      double* __restrict__ part) {
+    constexpr int E = Vec<T>::E, K = LPR * E, GPB = kBlock / LPR, NB = 8;
     __shared__ double red[kBlock / 32][2 * K];
-    const int g = blockIdx.x;
+    const int g = blockIdx.x / kSegSlices, q = blockIdx.x % kSegSlices;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane % LPR;
-    const int64_t r0 = node_off[g], r1 = node_off[g + 1];
+    const int64_t g0 = node_off[g], rows = node_off[g + 1] - g0;
+    const int64_t r0 = g0 + rows * q / kSegSlices, r1 = g0 + rows * (q + 1) / kSegSlices;
     double d1[E], d2[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) d1[e] = d2[e] = 0.0;
@@ -845,20 +853,28 @@ __global__ void __launch_bounds__(kBlock) k_seg_stats(const T* __restrict__ X,
         float f1[E], f2[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) f1[e] = f2[e] = 0.f;
-        for (int i = 0; i < 64; ++i) {
-            const int64_t r = base + (int64_t)i * GPB;
-            if (r >= r1) break;
-            float x[E];
-            Vec<T>::load(X + r * K + sub * E, x);
-            const float d = deg ? (float)deg[r] : 0.f;
+        for (int i0 = 0; i0 < 64; i0 += NB) {
+            if (base + (int64_t)i0 * GPB >= r1) break;
+            float x[NB][E], d[NB];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if (deg) {
-                    f1[e] = fmaf(d, x[e], f1[e]);
-                    f2[e] += d;
-                } else {
-                    f1[e] += x[e];
-                    f2[e] = fmaf(x[e], x[e], f2[e]);
+            for (int b = 0; b < NB; ++b) {  // all loads of the batch before any use
+                const int64_t r = base + (int64_t)(i0 + b) * GPB;
+                const bool ok = r < r1;
+                if (ok) Vec<T>::load(X + r * K + sub * E, x[b]);
+                d[b] = ok && deg ? (float)deg[r] : 0.f;
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (base + (int64_t)(i0 + b) * GPB >= r1) break;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (deg) {
+                        f1[e] = fmaf(d[b], x[b][e], f1[e]);
+                        f2[e] += d[b];
+                    } else {
+                        f1[e] += x[b][e];
+                        f2[e] = fmaf(x[b][e], x[b][e], f2[e]);
+                    }
                 }
             }
         }
@@ -886,8 +902,19 @@ __global__ void __launch_bounds__(kBlock) k_seg_stats(const T* __restrict__ X,
         double acc = 0.0;
 #pragma unroll
         for (int w = 0; w < kBlock / 32; ++w) acc += red[w][t];
-        stats[(size_t)g * 2 * K + t] = acc;
+        part[(size_t)blockIdx.x * 2 * K + t] = acc;
     }
+}
+
+// stats[g][t] = sum over the slices of graph g, in slice order, of their partials
+__global__ void k_seg_reduce(int ng, int K2, const double* __restrict__ part,
+                             double* __restrict__ stats) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ng * K2) return;
+    const int64_t g = i / K2, t = i % K2;
+    double acc = 0.0;
+    for (int q = 0; q < kSegSlices; ++q) acc += part[((size_t)g * kSegSlices + q) * K2 + t];
+    stats[i] = acc;
 }
 
 // mean[g][k], scale[g][k] (scale = 1 / RMS of the centred column, 1 if zero) from the stats.
@@ -1212,6 +1239,7 @@ struct Smoother {
     // ng + 1 entries): per-graph seeded blocks, means and projection scales; one launch per sweep
     // for all graphs.
     static sfg_status filter_score_batched(sfg_ctx* ctx, const sfg_graph* U, const sfg_graph* PU,
+                                           const int32_t* orig_local,
                                            int ng, const int32_t* node_off, int steps,
                                            double omega, uint64_t seed, const int32_t* ids,
                                            int64_t ne, sfg_score_mode mode, float* scores) {
@@ -1231,15 +1259,22 @@ struct Smoother {
         SFG_TRY(s.get(&sg, (size_t)ng * K));
         SFG_TRY(s.get(&sp, (size_t)ng * K));
         SFG_TRY(s.get(&stats, (size_t)ng * 2 * K));
+        double* spart;
+        SFG_TRY(s.get(&spart, (size_t)ng * kSegSlices * 2 * K));
         const unsigned fin_grid = ceil_div_u((int64_t)ng * K, kBlock);
-        k_init_batched<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, seed, node_off, ng, x0);
+        const unsigned red_grid = ceil_div_u((int64_t)ng * 2 * K, kBlock);
+        auto seg_stats = [&](const T* X, const double* deg) {
+            k_seg_stats<T, LPR><<<ng * kSegSlices, kBlock, 0, ctx->stream>>>(X, node_off, deg, spart);
+            k_seg_reduce<<<red_grid, kBlock, 0, ctx->stream>>>(ng, 2 * K, spart, stats);
+            ctx->launches += 2;
+        };
+        k_init_batched<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, seed, node_off, ng, orig_local, x0);
         const bool weighted = steps > 0;
-        k_seg_stats<T, LPR><<<ng, kBlock, 0, ctx->stream>>>(x0, node_off, weighted ? U->deg : nullptr,
-                                                             stats);
+        seg_stats(x0, weighted ? U->deg : nullptr);
         k_seg_finalize<<<fin_grid, kBlock, 0, ctx->stream>>>(stats, node_off, ng, K, weighted ? 1 : 0,
                                                              mean, nullptr);
         k_center_batched<T, LPR><<<grid, kBlock, 0, ctx->stream>>>(n, node_off, ng, mean, x0);
-        ctx->launches += 4;
+        ctx->launches += 3;
         SFG_LAUNCH_CHECK(ctx, "k_init_batched");
         const T* xr[2] = {x0, x0};
         const sfg_graph* L[2] = {U, PU};
@@ -1259,9 +1294,9 @@ struct Smoother {
                 nxt = (nxt == buf[w][0]) ? buf[w][1] : buf[w][0];
             }
             xr[w] = cur;
-            k_seg_stats<T, LPR><<<ng, kBlock, 0, ctx->stream>>>(cur, node_off, nullptr, stats);
+            seg_stats(cur, nullptr);
             k_seg_finalize<<<fin_grid, kBlock, 0, ctx->stream>>>(stats, node_off, ng, K, 0, mean, sc[w]);
-            ctx->launches += 2;
+            ++ctx->launches;
             SFG_LAUNCH_CHECK(ctx, "k_seg_stats");
         }
         return sfg_score_batched_impl(ctx, U, xr[0], xr[1], K, Vec<T>::E == 4 ? SFG_F32 : SFG_BF16,
@@ -1410,14 +1445,15 @@ sfg_status sfg_filter_score_impl(sfg_ctx* ctx, const sfg_graph* LG, const sfg_gr
 }
 
 sfg_status sfg_filter_score_batched_impl(sfg_ctx* ctx, const sfg_graph* U, const sfg_graph* PU,
+                                         const int32_t* orig_local,
                                          int ng, const int32_t* node_off, int K, int steps,
                                          double omega, uint64_t seed, sfg_dtype storage,
                                          const int32_t* ids, int64_t ne, sfg_score_mode mode,
                                          float* scores) {
     return dispatch(K, storage, [&](auto S) {
         using Sm = decltype(S);
-        return Sm::filter_score_batched(ctx, U, PU, ng, node_off, steps, omega, seed, ids, ne,
-                                        mode, scores);
+        return Sm::filter_score_batched(ctx, U, PU, orig_local, ng, node_off, steps, omega, seed,
+                                        ids, ne, mode, scores);
     });
 }
 

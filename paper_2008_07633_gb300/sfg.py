@@ -619,14 +619,16 @@ class Batch:
     """Owner of an sfg_batch plan (see include/sfg.h): build once, run many times."""
 
     def __init__(self, ctx, graphs, K=16, steps=15, omega=0.7, mode=SFG_SCORE_RATIO,
-                 budget_frac=0.05, budget_unit=0, storage=torch.float32, autotune=False):
+                 budget_frac=0.05, budget_unit=0, storage=torch.float32, autotune=False,
+                 locality=False):
         self.ctx = ctx
         p = sfg_params(K, steps, 0, omega, 0, mode, budget_frac, budget_unit, _dt(storage),
                        SFG_SMOOTH_JACOBI)
         arr = (_vp * len(graphs))(*[g.h for g in graphs])
         h = _vp()
-        ctx.check(lib().sfg_batch_create(ctx.h, len(graphs), arr, ctypes.byref(p),
-                                         1 if autotune else 0, ctypes.byref(h)))
+        flags = (1 if autotune else 0) | (2 if locality else 0)   # SFG_BATCH_AUTOTUNE, _LOCALITY
+        ctx.check(lib().sfg_batch_create(ctx.h, len(graphs), arr, ctypes.byref(p), flags,
+                                         ctypes.byref(h)))
         self.h = h
         ng, m = _int(), _i64()
         offs = (ctypes.c_int64 * (len(graphs) + 1))()

@@ -72,6 +72,66 @@ def test_batch_run_captured_in_a_cuda_graph(S):
         assert torch.equal(out, ref)
 
 
+def _locality_specs():
+    specs = _specs()
+    # integer weights: many weight ties, which the forest breaks by original edge id
+    n, u, v, w = gen.random_graph(1500, 6000, seed=44, lo=1, hi=4)
+    specs.append((n, u, v, np.floor(w).astype(np.float32)))
+    specs.append(gen.random_graph(900, 1000, seed=45, connected=False))   # several components
+    return specs
+
+
+def test_locality_order_keeps_forest_and_sizes(S):
+    """With the nodes renumbered by breadth-first level, the spanning forests (budget 0) equal the
+    input-order plan's bit for bit -- weight ties are broken by the original edge ids -- and the
+    masks come out in the original edge order."""
+    ctx = S.sfg_ctx_create(0)
+    gs = [S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w)) for n, u, v, w in _locality_specs()]
+    kw = dict(K=16, steps=15, budget_frac=0.0)
+    plain = S.Batch(ctx, gs, **kw)
+    loc = S.Batch(ctx, gs, locality=True, **kw)
+    assert loc.counts == plain.counts and loc.offsets == plain.offsets
+    assert torch.equal(loc.run(3), plain.run(3))
+
+
+def test_locality_order_sparsifiers(S):
+    """With a budget, the sparsifiers differ from the input-order plan's only through FP32
+    summation order: same sizes, at least 95% of every graph's selected edges shared, kappa
+    within 5%; runs are deterministic and replay from a CUDA graph bit for bit."""
+    stream = torch.cuda.Stream()
+    ctx = S.sfg_ctx_create(0, stream)
+    with torch.cuda.stream(stream):
+        gs = [S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w)) for n, u, v, w in _locality_specs()]
+        kw = dict(K=16, steps=15, budget_frac=0.05)
+        plain = S.Batch(ctx, gs, **kw)
+        loc = S.Batch(ctx, gs, locality=True, autotune=True, **kw)
+        a, b = plain.run(7), loc.run(7)
+        again = loc.run(7)
+        forest = plain.split(S.Batch(ctx, gs, K=16, steps=15, budget_frac=0.0).run(7))
+    stream.synchronize()
+    assert loc.counts == plain.counts
+    assert torch.equal(b, again)
+    for g, pa, pb, f in zip(gs, plain.split(a), loc.split(b), forest):
+        assert int(pa.sum()) == int(pb.sum())
+        assert torch.equal(pb & f, f)                       # the forest is kept
+        sel_a, sel_b = pa & ~f.bool(), pb & ~f.bool()
+        k = int(sel_a.sum())
+        if k == 0:
+            continue
+        assert int((sel_a & sel_b).sum()) >= 0.95 * k
+        if g.n >= 1000:
+            ka = S.sfg_kappa(ctx, g, pa)[0]
+            kb = S.sfg_kappa(ctx, g, pb)[0]
+            assert abs(kb / ka - 1.0) <= 0.05
+    out = torch.empty_like(b)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        loc.run(7, out=out)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, b)
+
+
 def test_batch_plan_rejects_bad_arguments(S):
     ctx = S.sfg_ctx_create(0)
     n, u, v, w = gen.grid2d(8, 8)
