@@ -13,7 +13,7 @@ Metric: filter+score algorithmic GB/s = bytes / step time with
   B_score     = 16 E_off + 2 N K s                    (per edge 16 bytes, both blocks once)
   B_step      = T (B_sweep(G) + B_sweep(P)) + B_score
 B_score counts 16 bytes per scored edge: its id, its two endpoint ids and its score (the weight
-lookup is not counted, as in the survey's byte model). The timed region uses inputs larger than
+lookup is left out of the byte model). The timed region uses inputs larger than
 L2 (each vector block is 268 MB), so no L2 flush is done.
 
 Also in the line (rank 0, outside the headline's timed region, each timed with CUDA events over
