@@ -343,7 +343,8 @@ SFG_API sfg_status sfg_sparsify_batched(sfg_ctx* ctx, int ng, const sfg_graph* c
  *    (sfg_autotune);
  *  - SFG_BATCH_LOCALITY: renumber each graph's nodes internally by breadth-first level from a
  *    pseudo-peripheral root (not in the paper; a memory-locality device for graphs whose input
- *    order scatters neighbours, e.g. k-NN graphs of unsorted points). Seeded rows are drawn from
+ *    order scatters neighbours, e.g. k-NN graphs of unsorted points; at most 4096 levels, nodes
+ *    further out and other components keep their input order after the labelled ones). Seeded rows are drawn from
  *    the original node ids, forest ties and the selection use the original edge ids, and masks
  *    come out in the original edge order, so the result is the plan's without the flag up to FP32
  *    summation order in the sweeps and column statistics.

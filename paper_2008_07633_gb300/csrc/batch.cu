@@ -312,6 +312,7 @@ static sfg_status check_batch_params(sfg_ctx* ctx, const sfg_params* P) {
 
 // Breadth-first renumbering of the union (see the file comment): b->U is replaced by its
 // relabelled copy; f2c receives the new id of every original union edge.
+constexpr int32_t kMaxLevels = 4096;
 static sfg_status batch_reorder(sfg_ctx* ctx, sfg_batch* b, int32_t* f2c) {
     const int32_t n = b->n;
     const int64_t m = b->m;
@@ -343,8 +344,9 @@ static sfg_status batch_reorder(sfg_ctx* ctx, sfg_batch* b, int32_t* f2c) {
         SFG_CUDA(ctx, cudaMemsetAsync(level, 0xff, 4 * (size_t)n, ctx->stream));
         k_bfs_seed<<<gg, kBlock, 0, ctx->stream>>>(ng, b->d_noff, pass ? roots : nullptr, level);
         ++ctx->launches;
-        for (depth = 0;; ++depth) {
-            if (depth >= n) return sfg_fail(ctx, SFG_ETIMEOUT, "breadth-first search did not end");
+        // one launch and one synchronisation per level: the search stops after kMaxLevels levels
+        // (nodes further out keep their input order, after the labelled ones)
+        for (depth = 0; depth + 1 < kMaxLevels; ++depth) {
             SFG_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
             k_bfs_step<<<gn, kBlock, 0, ctx->stream>>>(n, U->row_ptr, U->colval, depth, level, flag);
             ++ctx->launches;

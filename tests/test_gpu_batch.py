@@ -78,6 +78,15 @@ def _locality_specs():
     n, u, v, w = gen.random_graph(1500, 6000, seed=44, lo=1, hi=4)
     specs.append((n, u, v, np.floor(w).astype(np.float32)))
     specs.append(gen.random_graph(900, 1000, seed=45, connected=False))   # several components
+    # a long chain with short chords: more breadth-first levels than the search labels (4096), so
+    # its far end keeps the input order
+    n, u, v, w = gen.path(9000, weights="uniform")
+    rng = np.random.default_rng(46)
+    a = rng.integers(0, n - 3, 300)
+    u = np.concatenate([u, a]).astype(np.int32)
+    v = np.concatenate([v, a + 2 + rng.integers(0, 2, a.size)]).astype(np.int32)
+    w = np.concatenate([w, rng.uniform(1.0, 10.0, a.size)]).astype(np.float32)
+    specs.append((n, u, v, w))
     return specs
 
 
