@@ -685,6 +685,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(pg, values, device):
+    """Element-wise maximum of `values` over all ranks (a replica job takes as long as its
+    slowest rank); `values` unchanged without a process group."""
+    if pg is None:
+        return [float(x) for x in values]
+    import torch
+
+    t_ = torch.tensor([float(x) for x in values], device=device, dtype=torch.float64)
+    pg.all_reduce(t_, op=pg.ReduceOp.MAX)
+    return [float(x) for x in t_.tolist()]
+
+
+def whole_job_gbps(world, bytes_per_step, ms):
+    """Whole-job throughput of `world` replicas that each move bytes_per_step per step."""
+    return world * bytes_per_step / (ms * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------------------------------------
 # reference arm / CPU baseline: the oracle on a bounded sample of the workload
 # ------------------------------------------------------------------------------------------------
@@ -830,11 +847,8 @@ def run_ours(args):
     nj, ms_j = S.sfg_ctx_kernel_time(ctx, "jacobi")
     ns_, ms_s = S.sfg_ctx_kernel_time(ctx, "score")
     S.sfg_ctx_timing(ctx, False)
-    if pg:
-        t_ = torch.tensor([ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t_, op=pg.ReduceOp.MAX)
-        ms = float(t_.item())
-    value = world * b_step / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(pg, [ms], dev)[0]
+    value = whole_job_gbps(world, b_step, ms)
 
     # roofline of the dominant kernel (the Jacobi sweep), from its live CUDA-event durations
     peak, peak_kind = load_peaks()
@@ -891,10 +905,7 @@ def run_ours(args):
         e2e_step()
     barrier()
     e2e_ms = (time.perf_counter() - t0) / e2e_iters * 1e3
-    if pg:
-        t_ = torch.tensor([e2e_ms, sparsify_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t_, op=pg.ReduceOp.MAX)
-        e2e_ms, sparsify_ms = (float(x) for x in t_.tolist())
+    e2e_ms, sparsify_ms = max_over_ranks(pg, [e2e_ms, sparsify_ms], dev)
     if rank != 0:
         return 0
 
@@ -945,7 +956,7 @@ def run_ours(args):
                       "tuned_tile_shape": {k_: v_[0] for k_, v_ in tuned.items()}},
            "roofline": roof,
            "clocks": clk.summary(),
-           "e2e": {"value": world * b_step / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+           "e2e": {"value": whole_job_gbps(world, b_step, e2e_ms), "unit": UNIT,
                    "h2d_bytes_per_step": int(u.nbytes + v.nbytes + w.nbytes),
                    "d2h_bytes_per_step": int(G.m), "ms_per_step": e2e_ms,
                    "what": "pinned host edge list -> H2D -> sfg_laplacian -> sfg_sparsify (flat) -> D2H mask"},
