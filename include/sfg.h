@@ -168,8 +168,8 @@ SFG_API sfg_status sfg_jacobi(sfg_ctx* ctx, const sfg_graph* L, int K, int steps
  * sweep: a warp sweeps TPI = {1, 2, 4, 1, 2, 4}[v] consecutive row tiles before its grid-stride
  * jump, with {4, 4, 4, 3, 3, 3}[v] CTAs per SM requested from the compiler; default v = 1. Shape s
  * of the scorer (sfg_score_edges, sfg_filter_score and the batched forms): a warp scores
- * {1, 2}[s] edge tiles per iteration with {4, 2}[s] CTAs per SM; default s = 0 below an average
- * degree of 8, else 1. sfg_autotune times all sweep variants on L (three sweeps each) and both
+ * {1, 2, 1}[s] edge tiles per iteration with {4, 2, 4}[s] CTAs per SM, shape 2 reading rows with
+ * loads cached in L2 only; default s = 0 below an average degree of 8, else 1. sfg_autotune times all sweep variants on L (three sweeps each) and both
  * scorer shapes on every edge of L (three launches each), synchronises, and records the fastest of
  * each in ctx's table under (K, storage, degree bucket b: 2^b <= 2m/n < 2^(b+1)); later calls on
  * graphs of that key use them (for the scorer, the key of L_G). Every variant and shape computes
@@ -177,7 +177,7 @@ SFG_API sfg_status sfg_jacobi(sfg_ctx* ctx, const sfg_graph* L, int K, int steps
  * sfg_tune_table writes the table as JSON text, one object per key with its sweep variant and
  * scorer shape (-1: none recorded; len_host: its length; SFG_ECAPACITY if cap is too small). */
 #define SFG_SWEEP_VARIANTS 6
-#define SFG_SCORE_SHAPES 2
+#define SFG_SCORE_SHAPES 3
 SFG_API sfg_status sfg_autotune(sfg_ctx* ctx, const sfg_graph* L, int K, sfg_dtype storage,
                                 int* variant_host, double* us_per_sweep_host);
 SFG_API sfg_status sfg_tune_set(sfg_ctx* ctx, int K, sfg_dtype storage, int degree_bucket,

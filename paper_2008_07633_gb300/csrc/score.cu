@@ -13,12 +13,27 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// One 32-byte read-only global load (sm_100 and later) into two 16-byte vectors; p must be 32-byte
-// aligned.
+// One 32-byte global load (sm_100 and later) into two 16-byte vectors; p must be 32-byte aligned.
+template <int CG>
 __device__ __forceinline__ void load_raw32(const void* p, uint4& a, uint4& b) {
-    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
-                 : "l"(p));
+    if (CG)  // cached in L2 only
+        asm volatile("ld.global.cg.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                     : "l"(p));
+    else
+        asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                     : "l"(p));
+}
+
+// One 16-byte row vector; CG: cached in L2 only.
+template <typename T, int CG>
+__device__ __forceinline__ uint4 load_row16(const T* p) {
+    if (!CG) return Vec<T>::load_raw(p);
+    uint4 r;
+    asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
 }
 
 template <int LPR>
@@ -38,13 +53,13 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
 // gathered rows stay packed until they are used. The two squared distances are folded together:
 // at the first step the even lane of each pair keeps the G partial and the odd lane the P partial,
 // so one shuffle per level moves both, and one more hands the P sum to the group's first lane.
-// The score formula is fixed at compile time (MODE); U and MINB (CTAs per SM) are the launch
-// shape.
+// The score formula is fixed at compile time (MODE); U, MINB (CTAs per SM) and CG (row loads
+// cached in L2 only, not in L1) are the launch shape.
 // SCALED: the blocks are raw smoothed blocks and column k of each is multiplied by its projection
 // scale (sg, sp) on the fly; the projection's mean removal cancels in X_p - X_q.
 // SCALED = 2: the scales are per graph of a disjoint union (graph g's rows start at node_off[g]),
 // looked up from each edge's first endpoint.
-template <typename T, int LPR, int V, bool WIDE, int SCALED, int U, int MINB, int MODE>
+template <typename T, int LPR, int V, bool WIDE, int SCALED, int U, int MINB, int CG, int MODE>
 __global__ void __launch_bounds__(kBlock, MINB)
     k_score(int64_t ne, const int32_t* __restrict__ ids, const int32_t* __restrict__ eu,
              const int32_t* __restrict__ ev, const float* __restrict__ ew,
@@ -101,17 +116,17 @@ __global__ void __launch_bounds__(kBlock, MINB)
         for (int u = 0; u < U; ++u) {
             const int64_t p = cur[u].p, q = cur[u].q;
             if constexpr (V == 2 && WIDE) {
-                load_raw32(Xg + p * K, rgp[u][0], rgp[u][V - 1]);
-                load_raw32(Xg + q * K, rgq[u][0], rgq[u][V - 1]);
-                load_raw32(Xp + p * K, rpp[u][0], rpp[u][V - 1]);
-                load_raw32(Xp + q * K, rpq[u][0], rpq[u][V - 1]);
+                load_raw32<CG>(Xg + p * K, rgp[u][0], rgp[u][V - 1]);
+                load_raw32<CG>(Xg + q * K, rgq[u][0], rgq[u][V - 1]);
+                load_raw32<CG>(Xp + p * K, rpp[u][0], rpp[u][V - 1]);
+                load_raw32<CG>(Xp + q * K, rpq[u][0], rpq[u][V - 1]);
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    rgp[u][v] = Vec<T>::load_raw(Xg + p * K + v * E);
-                    rgq[u][v] = Vec<T>::load_raw(Xg + q * K + v * E);
-                    rpp[u][v] = Vec<T>::load_raw(Xp + p * K + v * E);
-                    rpq[u][v] = Vec<T>::load_raw(Xp + q * K + v * E);
+                    rgp[u][v] = load_row16<T, CG>(Xg + p * K + v * E);
+                    rgq[u][v] = load_row16<T, CG>(Xg + q * K + v * E);
+                    rpp[u][v] = load_row16<T, CG>(Xp + p * K + v * E);
+                    rpq[u][v] = load_row16<T, CG>(Xp + q * K + v * E);
                 }
             }
         }
@@ -211,7 +226,8 @@ __global__ void k_affinity(int64_t m, const int32_t* __restrict__ eu, const int3
 
 // NV: 16-byte vectors per row; each lane takes two of them (one when a row is one vector).
 // Launch shape 0: one tile per warp iteration, four CTAs per SM; shape 1: two tiles, two CTAs per
-// SM (sfg_score_shape). Both compute the same values bit for bit.
+// SM; shape 2: shape 0 with row loads cached in L2 only (sfg_score_shape). All compute the same
+// values bit for bit.
 template <typename T, int NV>
 sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const void* XP,
                         const int32_t* ids, int64_t ne, int mode, const float* sg,
@@ -225,17 +241,18 @@ sfg_status launch_score(sfg_ctx* ctx, const sfg_graph* LG, const void* XG, const
     const int sc = node_off ? 2 : (sg ? 1 : 0);
     const int shape = sfg_score_shape(ctx, K, sizeof(T) == 2 ? SFG_BF16 : SFG_F32, LG);
     constexpr bool W2 = V == 2;  // 32-byte loads exist only for two vectors per lane
-#define SFG_SCORE_ROW(WD, SC, U, MB)                                                                \
-    {(void*)k_score<T, LPR, V, WD, SC, U, MB, 0>, (void*)k_score<T, LPR, V, WD, SC, U, MB, 1>,   \
-     (void*)k_score<T, LPR, V, WD, SC, U, MB, 2>}
-    static void* const tab[2][2][3][3] = {
-        {{SFG_SCORE_ROW(false, 0, 1, 4), SFG_SCORE_ROW(false, 1, 1, 4), SFG_SCORE_ROW(false, 2, 1, 4)},
-         {SFG_SCORE_ROW(false, 0, 2, 2), SFG_SCORE_ROW(false, 1, 2, 2), SFG_SCORE_ROW(false, 2, 2, 2)}},
-        {{SFG_SCORE_ROW(W2, 0, 1, 4), SFG_SCORE_ROW(W2, 1, 1, 4), SFG_SCORE_ROW(W2, 2, 1, 4)},
-         {SFG_SCORE_ROW(W2, 0, 2, 2), SFG_SCORE_ROW(W2, 1, 2, 2), SFG_SCORE_ROW(W2, 2, 2, 2)}}};
+#define SFG_SCORE_ROW(WD, SC, U, MB, CG)                                                            \
+    {(void*)k_score<T, LPR, V, WD, SC, U, MB, CG, 0>, (void*)k_score<T, LPR, V, WD, SC, U, MB, CG, 1>, \
+     (void*)k_score<T, LPR, V, WD, SC, U, MB, CG, 2>}
+#define SFG_SCORE_SHAPE(WD, U, MB, CG)                                                              \
+    {SFG_SCORE_ROW(WD, 0, U, MB, CG), SFG_SCORE_ROW(WD, 1, U, MB, CG), SFG_SCORE_ROW(WD, 2, U, MB, CG)}
+    static void* const tab[2][SFG_SCORE_SHAPES][3][3] = {
+        {SFG_SCORE_SHAPE(false, 1, 4, 0), SFG_SCORE_SHAPE(false, 2, 2, 0), SFG_SCORE_SHAPE(false, 1, 4, 1)},
+        {SFG_SCORE_SHAPE(W2, 1, 4, 0), SFG_SCORE_SHAPE(W2, 2, 2, 0), SFG_SCORE_SHAPE(W2, 1, 4, 1)}};
+#undef SFG_SCORE_SHAPE
 #undef SFG_SCORE_ROW
     const void* k = tab[wide][shape][sc][mode];
-    const int U = shape == 0 ? 1 : 2;
+    const int U = shape == 1 ? 2 : 1;
     void* args[] = {(void*)&ne, (void*)&ids, (void*)&LG->eu, (void*)&LG->ev, (void*)&LG->ew,
                     (void*)&xg, (void*)&xp, (void*)&eta, (void*)&sg, (void*)&sp,
                     (void*)&node_off, (void*)&ngraphs, (void*)&out};

@@ -42,7 +42,7 @@ def test_autotune_variants_agree_bit_for_bit(S):
     best, us = S.sfg_autotune(ctx, g, 32)
     assert 0 <= best < 6 and us > 0
     table = S.sfg_tune_table(ctx)
-    assert len(table) == 1 and table[0]["score_shape"] in (0, 1)
+    assert len(table) == 1 and table[0]["score_shape"] in (0, 1, 2)
     assert table == [{"K": 32, "dtype": 0, "degree_bucket": 2, "variant": best,
                       "tiles_per_warp": [1, 2, 4, 1, 2, 4][best],
                       "ctas_per_sm": [4, 4, 4, 3, 3, 3][best],
@@ -53,7 +53,7 @@ def test_autotune_variants_agree_bit_for_bit(S):
 @pytest.mark.parametrize("K,dt", [(4, torch.float32), (32, torch.float32), (64, torch.float32),
                                   (8, torch.bfloat16), (64, torch.bfloat16)])
 def test_score_shapes_agree_bit_for_bit(S, K, dt):
-    # both launch shapes of the scorer, on a mesh (degree bucket 2) and a denser graph (bucket 3)
+    # every launch shape of the scorer, on a mesh (degree bucket 2) and a denser graph (bucket 3)
     ctx = S.sfg_ctx_create(0)
     for n, u, v, w in (gen.grid3d(24, seed=2), gen.knn3d(6000, k=10, seed=3)):
         g = S.sfg_laplacian(ctx, n, dev(u), dev(v), dev(w))
@@ -62,14 +62,16 @@ def test_score_shapes_agree_bit_for_bit(S, K, dt):
         xp = torch.from_numpy(gen.gaussian_block(g.n, K, seed=6)).to(DEV).to(dt)
         ids = dev(np.arange(g.m, dtype=np.int32)[::-1].copy())
         outs = []
-        for shape in (0, 1, -1):
+        shapes = (0, 1, 2, -1)
+        for shape in shapes:
             S.sfg_tune_set_score(ctx, K, dt, bucket, shape)
             for mode in (0, 1, 2):
                 outs.append(S.sfg_score_edges(ctx, g, xg, xp, ids, mode=mode))
-        for i in range(3):
-            assert torch.equal(outs[i], outs[3 + i]) and torch.equal(outs[i], outs[6 + i])
+        for j in range(1, len(shapes)):
+            for i in range(3):
+                assert torch.equal(outs[i], outs[3 * j + i])
     with pytest.raises(S.SfgError):
-        S.sfg_tune_set_score(ctx, K, dt, 2, 2)
+        S.sfg_tune_set_score(ctx, K, dt, 2, 3)
 
 
 def test_filter_score_and_select_capture_in_a_cuda_graph(S):
